@@ -1,0 +1,350 @@
+"""Benchmark: FMM matvecs/s (and GMRES solves/s) of the Helmholtz single-layer operator.
+
+Default workload: unit sphere, icosphere level 7 + longest-edge bisection
+(655,360 triangles x 3 points, N = 1,966,080), k = 20, expansion order
+p_l = ceil(k a_l + 6 log10(k a_l + pi)) per level with floor p_min, leaf <= 64,
+FP32 P2P/M2L, FP64 GMRES(50) to 1e-4.  One step = one FMM matvec (density prep,
+P2P, P2M, M2M, M2L, L2L, L2P, correction, output) with inputs resident in HBM;
+the solve (GMRES) is timed in its own region and reported under "solve".
+
+python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--impl reference]
+Prints ONE JSON line on rank 0.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "FMM matvecs/s and solves/s at 1e-4 residual vs plain FP32 form; p50/p99 latency"
+
+WORKLOADS = {
+    # name: (mesh, k, config overrides, GMRES restart)
+    "sphere_655360": ("sphere_655360", 20.0, {}, 50),
+    "sphere_1280": ("sphere_1280", 1.0, {"p_fixed": 8}, 30),
+    "sphere_163840": ("sphere_163840", 10.0, {}, 50),
+}
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return d.get("hbm_gbs", 6800.0), "measured", d.get("sm_max_mhz", 2070.0)
+    except Exception:
+        return 6800.0, "fallback", 2070.0
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index=0):
+        self.rows = []
+        self.proc = None
+        self.gpu = gpu_index
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm = [float(r[1]) for r in self.rows if len(r) >= 9 and r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if len(r) >= 9 and r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in self.rows:
+            if len(r) < 9:
+                continue
+            for q, nm in enumerate(names):
+                if r[5 + q].lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def cpu_baseline(V, F, k, near_factor, sigma, budget_s=12.0, rows=None):
+    """Oracle direct summation on a bounded sample of rows (FP64, all host cores)."""
+    import numpy as np
+
+    import oracle
+
+    N = 3 * F.shape[0]
+    r = oracle.near_radius(V, F, near_factor)
+    rng = np.random.default_rng(1)
+    if rows is None:
+        probe = rng.choice(N, size=16, replace=False)
+        t0 = time.perf_counter()
+        oracle.direct_rows(V, F, k, r, probe, sigma)
+        dt = time.perf_counter() - t0
+        nrow = int(max(16, min(4096, 16 * budget_s / max(dt, 1e-3))))
+        rows = np.sort(rng.choice(N, size=nrow, replace=False))
+    t0 = time.perf_counter()
+    vals = oracle.direct_rows(V, F, k, r, rows, sigma)
+    dt = time.perf_counter() - t0
+    return rows, vals, dt
+
+
+def run_reference(args):
+    """Reference arm: the FP64 oracle on the host cores, a bounded sample per step."""
+    import numpy as np
+
+    import synthetic
+
+    world, rank, _ = _dist()
+    if rank != 0:
+        return
+    mesh, k, over, _ = WORKLOADS[args.workload]
+    V, F = synthetic.workload_mesh(mesh)
+    N = 3 * F.shape[0]
+    sigma = synthetic.random_density(N, seed=0)
+    # size each step so the whole run stays within a few minutes
+    rows, _, dt = cpu_baseline(V, F, k, 1.0, sigma, budget_s=min(20.0, 120.0 / max(1, args.steps + args.warmup)))
+    for _ in range(args.warmup):
+        cpu_baseline(V, F, k, 1.0, sigma, rows=rows)
+    times = []
+    for _ in range(args.steps):
+        _, _, dt = cpu_baseline(V, F, k, 1.0, sigma, rows=rows)
+        times.append(dt)
+    tot = sum(times)
+    value = args.steps * len(rows) / N / tot
+    sample = f"{len(rows)} sampled rows of the direct sum (point part + exact self/near integrals) per step"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "matvec/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "N": N, "k": k},
+        "cpu_baseline": {"value": value, "unit": "matvec/s", "cores": os.cpu_count(), "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "matvec/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--workload", default="sphere_655360", choices=sorted(WORKLOADS))
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--p-min", type=int, default=None)
+    ap.add_argument("--solves", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    import paper_1803_09948_gb300 as pkg
+    import synthetic
+
+    world, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    __graft_entry__.build()
+    mesh, k, over, restart = WORKLOADS[args.workload]
+    cfg = dict(over)
+    if args.p_min is not None:
+        cfg["p_min"] = args.p_min
+    cfg["restart"] = restart
+    V, F = synthetic.workload_mesh(mesh)
+    N = 3 * F.shape[0]
+    stream = torch.cuda.current_stream()
+    t0 = time.perf_counter()
+    plan = pkg.Plan(V, F, k, **cfg)
+    plan_s = time.perf_counter() - t0
+    info = plan.info()
+    costs = plan.costs()
+    sigma = synthetic.random_density(N, seed=0)
+    dens = torch.from_numpy(sigma.astype(np.complex64)).cuda()
+    pot = torch.empty_like(dens)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    # ------------------------------------------------------------ device-resident matvecs
+    for _ in range(args.warmup):
+        plan.matvec(dens, pot)
+    barrier()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    clocks = ClockSampler(local)
+    clocks.start()
+    launches0 = plan.launch_count()
+    barrier()
+    ev[0].record(stream)
+    for s in range(args.steps):
+        plan.matvec(dens, pot)
+        ev[s + 1].record(stream)
+    barrier()
+    launches = plan.launch_count() - launches0
+    step_ms = [ev[s].elapsed_time(ev[s + 1]) for s in range(args.steps)]
+    total_ms = ev[0].elapsed_time(ev[args.steps])
+    if world > 1:
+        t = torch.tensor([total_ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    clk = clocks.stop()
+    value = world * args.steps / (total_ms / 1e3)
+
+    # ------------------------------------------------------------ per-stage breakdown (same stream)
+    stages = None
+    reps = 3
+    for r in range(reps):
+        st = plan.matvec_timed(dens, pot)
+        stages = st if stages is None else {q: stages[q] + st[q] for q in st}
+    stages = {q: v / reps for q, v in stages.items()}
+
+    # ------------------------------------------------------------ end to end through the ABI (host buffers)
+    h_in = torch.from_numpy(sigma.astype(np.complex64)).pin_memory()
+    h_out = torch.empty_like(h_in).pin_memory()
+    for _ in range(2):
+        dens.copy_(h_in, non_blocking=True)
+        plan.matvec(dens, pot)
+        h_out.copy_(pot, non_blocking=True)
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        dens.copy_(h_in, non_blocking=True)
+        plan.matvec(dens, pot)
+        h_out.copy_(pot, non_blocking=True)
+    e1.record(stream)
+    barrier()
+    e2e_ms = e0.elapsed_time(e1)
+    got = h_out.numpy().astype(np.complex128)
+
+    # ------------------------------------------------------------ GMRES solves (own region)
+    solve = None
+    if args.solves > 0:
+        b = torch.empty_like(dens)
+        plan.rhs_planewave([0.0, 0.0, 1.0], b)
+        x = torch.empty_like(dens)
+        plan.solve(b, x)  # warm-up solve (allocates the Krylov basis)
+        lat = []
+        its = []
+        rrs = []
+        for _ in range(args.solves):
+            barrier()
+            t1 = time.perf_counter()
+            stt, it, rr = plan.solve(b, x)
+            torch.cuda.synchronize()
+            lat.append(time.perf_counter() - t1)
+            its.append(it[0])
+            rrs.append(rr[0])
+        solve = {"solves_per_s": len(lat) / sum(lat), "ms_per_solve": 1e3 * statistics.mean(lat),
+                 "p50_ms": 1e3 * float(np.percentile(lat, 50)), "p99_ms": 1e3 * float(np.percentile(lat, 99)),
+                 "iterations": its[-1], "true_relres": rrs[-1], "restart": restart, "tol": 1e-4,
+                 "status": "converged" if stt == 0 else "not converged", "rhs": "plane wave along +z"}
+
+    # ------------------------------------------------------------ roofline of the dominant stage
+    hbm, peak_src, smax = _peaks()
+    props = torch.cuda.get_device_properties(local)
+    fp32_peak = props.multi_processor_count * 128 * 2 * smax * 1e6 / 1e12  # TFLOP/s
+    dom = max(stages, key=stages.get)
+    work = {
+        "p2p": ("alu", costs["p2p_pairs"] * 24 / 1e12, "TFLOP/s", fp32_peak, "24 flop per source-target pair"),
+        "m2l": ("alu", costs["m2l_cmacs"] * 8 / 1e12, "TFLOP/s", fp32_peak, "8 flop per complex multiply-add"),
+        "m2m": ("alu", costs["m2m_l2l_cmacs"] * 4 / 1e12, "TFLOP/s", fp32_peak, "M2M half of the M2M+L2L work"),
+        "l2l": ("alu", costs["m2m_l2l_cmacs"] * 4 / 1e12, "TFLOP/s", fp32_peak, "L2L half of the M2M+L2L work"),
+        "corr": ("hbm", (costs["corr_nnz"] * 12 + costs["n_points"] * 16) / 1e9, "GB/s", hbm,
+                 "12 B per nonzero + 16 B per row"),
+    }
+    rl = None
+    if dom in work:
+        bound, amount, unit, peak, note = work[dom]
+        achieved = amount / (stages[dom] / 1e3)
+        rl = {"kernel": dom, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
+              "frac": achieved / peak, "traffic": None,
+              "peak_source": (f"FP32: {props.multi_processor_count} SMs x 128 lanes x 2 flop x {smax:.0f} MHz"
+                              if bound == "alu" else f"HBM {peak_src} copy bandwidth"),
+              "work_per_launch": note}
+
+    # ------------------------------------------------------------ accuracy and CPU baseline (rank 0)
+    cpu = None
+    acc = None
+    if rank == 0 and not args.no_cpu_baseline:
+        rows, ref, dt = cpu_baseline(V, F, k, plan.cfg.near_factor, sigma)
+        acc = {"sampled_rows": int(len(rows)),
+               "rel_err_vs_oracle": float(np.linalg.norm(got[rows] - ref) / np.linalg.norm(ref))}
+        cpu = {"value": len(rows) / N / dt, "unit": "matvec/s", "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"{len(rows)} sampled rows of the FP64 direct sum (point part + exact self/near "
+                         f"integrals), {dt:.1f} s, scaled to whole matvecs"}
+
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": value, "unit": "matvec/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "fp32 (P2P, M2L, tree passes); fp64 GMRES",
+            "data": "synthetic",
+            "config": {"workload": f"{args.workload}: {synthetic.WORKLOADS[mesh][0]}", "N": N, "k": k,
+                       "leaf_max": plan.cfg.leaf_max, "depth": info["depth"], "orders": info["orders"],
+                       "near_factor": plan.cfg.near_factor, "corr_nnz": info["corr_nnz"],
+                       "m2l_translations": info["m2l_translations"], "device_bytes": info["device_bytes"],
+                       "parallelism": "replicas" if world > 1 else "single GPU",
+                       "l2": f"inputs larger than L2 (plan holds {info['device_bytes'] / 1e9:.2f} GB)"},
+            "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99)),
+                           "mean": statistics.mean(step_ms),
+                           "std": statistics.pstdev(step_ms) if len(step_ms) > 1 else 0.0},
+            "stages_ms": stages,
+            "plan_s": plan_s,
+            "solve": solve,
+            "e2e": {"value": args.steps / (e2e_ms / 1e3), "unit": "matvec/s", "h2d_bytes_per_step": 8 * N,
+                    "d2h_bytes_per_step": 8 * N},
+            "roofline": rl,
+            "cpu_baseline": cpu,
+            "accuracy": acc,
+            "clocks": clk,
+            "gpu_launches": launches,
+        }
+        print(json.dumps(out))
+    plan.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,189 @@
+/*
+ * hfmm.h - C ABI of the GB300 FMM-accelerated Helmholtz boundary-integral library.
+ *
+ * The operator follows the problem statement of "Extreme Scale FMM-Accelerated
+ * Boundary Integral Equation Solver for Wave Scattering" (arXiv:1803.09948):
+ *
+ *   Green's function        G(x,y) = exp(i k R) / (4 pi R), R = |x - y|      (Eq. 6)
+ *   sound-soft scattering   int_S G(r,r') q(r') dS' = p_inc(r) on S          (Eq. 7)
+ *   Nystrom discretisation  Z I = V_inc, [V_inc]_i = p_inc(x_i)              (Eq. 9, 10)
+ *
+ * Discretisation used by every call (flat triangles, three points each):
+ *   point 3n+a (a = 0,1,2) of triangle n sits at barycentric (2/3,1/6,1/6)
+ *   rotated to vertex a; its weight is area_n/3 and its basis function the
+ *   linear Lagrange function L_(n,a) = 2 lambda_a - 1/3 (1 at the point, 0 at
+ *   the other two).  For target x_i the singular set S(i) holds its own
+ *   triangle and every triangle with a point within near_factor * (mean edge
+ *   length) of x_i; those triangles are integrated exactly (Sec. 2.2, the
+ *   self- and near-singularity treatment of Listing 1 and Sec. 6.4), every
+ *   other source point enters with the point rule w_j G(x_i, x_j):
+ *
+ *     (Z s)_i = sum_{n not in S(i)} sum_a w_(n,a) G(x_i, x_(n,a)) s_(n,a)
+ *             + sum_{n in S(i)}     sum_a s_(n,a) int_{T_n} G(x_i,y) L_(n,a)(y) dS_y
+ *
+ * The point part is evaluated by the FMM (Sec. 2.3, Eq. 11-14: P2M, M2M, M2L,
+ * L2L, L2P on a uniform octree, P2P between neighbouring leaves) and the
+ * exact-minus-point correction on S(i) is a sparse matrix built once per plan.
+ *
+ * Conventions
+ *   - Status: 0 success, negative error (HFMM_E_*), HFMM_NOT_CONVERGED (+1)
+ *     from hfmm_solve when max_iter is reached.  No C++ exception crosses the ABI.
+ *   - Vectors ("density", "potential", "rhs", "x") are DEVICE pointers to
+ *     complex64 (interleaved float re, im) of length N = 3 * n_tri in user
+ *     point order (point 3n+a as above), nrhs of them stored one after another
+ *     (column-major N x nrhs).  The caller owns them; the library never frees
+ *     or keeps them beyond the call.
+ *   - Mesh arrays passed to hfmm_plan_create are HOST pointers; they are
+ *     copied and need not outlive the call.
+ *   - Streams are cudaStream_t passed as void* (NULL: the legacy default
+ *     stream).  hfmm_matvec and hfmm_direct are stream-ordered and return
+ *     before the work completes; hfmm_solve returns after the solve completes.
+ *   - A plan is not thread-safe: calls on one plan must not overlap in time or
+ *     on the device (it owns one set of scratch buffers).
+ *   - Only real wavenumbers are supported (k_im must be 0).
+ */
+#ifndef HFMM_H
+#define HFMM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define HFMM_OK 0
+#define HFMM_NOT_CONVERGED 1
+#define HFMM_E_INVALID (-1)   /* bad argument (null pointer, size, value out of range) */
+#define HFMM_E_MESH (-2)      /* degenerate mesh: zero-area triangle, non-finite vertex, bad index */
+#define HFMM_E_NOMEM (-3)     /* device allocation failed or over the configured memory budget */
+#define HFMM_E_CUDA (-4)      /* a CUDA runtime call failed */
+#define HFMM_E_TIMEOUT (-5)   /* reserved: a bounded device wait gave up */
+#define HFMM_E_OVERFLOW (-6)  /* a fixed-capacity table overflowed (e.g. near set too large) */
+
+typedef struct hfmm_plan hfmm_plan; /* opaque; owns all device state of one mesh and wavenumber */
+
+typedef struct {
+    int leaf_max;       /* max points per leaf; the octree depth is the smallest meeting it (64) */
+    int depth;          /* >0: force this octree depth instead (0: automatic) */
+    int p_fixed;        /* >0: expansion order on every level; 0: per-level formula below */
+    int p_min;          /* floor for the formula p_l = ceil(k a_l + 6 log10(k a_l + pi)),
+                           a_l = circumradius of a level-l box */
+    double near_factor; /* near radius = near_factor * mean edge length (1.0) */
+    int quad_order;     /* Gauss-Legendre points per direction of the Duffy-type
+                           self/near quadrature (10) */
+    int restart;        /* GMRES restart length m (30) */
+    int max_iter;       /* GMRES iteration cap (1000) */
+    double tol;         /* GMRES relative residual ||b - Z x|| / ||b|| target (1e-4) */
+    double mem_budget_bytes; /* refuse a plan whose device footprint exceeds this (0: no limit) */
+} hfmm_config;
+
+/* Fills *cfg with the defaults shown in parentheses above (p_min = 7). */
+void hfmm_default_config(hfmm_config* cfg);
+
+/*
+ * Builds a plan for the surface (vertices: n_vert x 3 doubles, tris: n_tri x 3
+ * vertex indices, counter-clockwise) and wavenumber k = k_re + i k_im (Eq. 3,
+ * 6).  Computes quadrature points and weights, the octree and interaction
+ * lists, the translation operators and the sparse near/self correction
+ * (Sec. 2.2-2.3).  Work is issued on `stream` and the call returns after it
+ * completes.  On failure *out is NULL and nothing is leaked.
+ */
+int hfmm_plan_create(const hfmm_config* cfg, const double* vertices, int64_t n_vert,
+                     const int32_t* tris, int64_t n_tri, double k_re, double k_im,
+                     void* stream, hfmm_plan** out);
+
+void hfmm_plan_destroy(hfmm_plan* plan); /* NULL is a no-op */
+
+int64_t hfmm_num_points(const hfmm_plan* plan); /* N = 3 * n_tri, or -1 for NULL */
+
+/*
+ * Copies the quadrature points (xyz: N x 3), weights (w: N) and triangle ids
+ * (tri: N) to HOST arrays in user order; any of the three may be NULL.
+ */
+int hfmm_points(const hfmm_plan* plan, double* xyz, double* w, int32_t* tri);
+
+/*
+ * Plan facts for reporting: depth (octree leaf level), order per level
+ * (orders[l] for l = 0..depth; levels 0 and 1 carry no expansions and report 0,
+ * orders must hold 32 ints), number of leaves, near/self correction nonzeros,
+ * M2L translations, and device bytes held by the plan.  Any pointer may be NULL.
+ */
+int hfmm_plan_info(const hfmm_plan* plan, int* depth, int* orders, int64_t* n_leaves,
+                   int64_t* corr_nnz, int64_t* m2l_translations, int64_t* device_bytes);
+
+/*
+ * potential = Z density (Eq. 9-10) with the FMM for the point part, nrhs
+ * right-hand sides.  density and potential are device complex64 vectors,
+ * N x nrhs, user point order; they may not overlap.  Stream-ordered.
+ */
+int hfmm_matvec(hfmm_plan* plan, const void* density, void* potential, int nrhs, void* stream);
+
+/*
+ * Like hfmm_matvec but evaluates only part of the operator (for tests and
+ * breakdowns): parts bit 0 = near field (P2P between neighbouring leaves),
+ * bit 1 = far field (P2M..L2P), bit 2 = near/self correction.  parts = 7 is
+ * hfmm_matvec.
+ */
+int hfmm_matvec_parts(hfmm_plan* plan, const void* density, void* potential, int nrhs,
+                      int parts, void* stream);
+
+/*
+ * potential = Z density by direct O(N^2) summation of the point part plus the
+ * same correction (a reference for tests and small problems).  Same argument
+ * conventions as hfmm_matvec.
+ */
+int hfmm_direct(hfmm_plan* plan, const void* density, void* potential, int nrhs, void* stream);
+
+/*
+ * rhs_out (device complex64, N x nrhs) = incident plane waves
+ * p_inc(x) = exp(i k d.x) at the quadrature points (Eq. 9's V_inc);
+ * dirs: HOST array of nrhs unit vectors (3 doubles each).  Stream-ordered.
+ */
+int hfmm_rhs_planewave(hfmm_plan* plan, const double* dirs, int nrhs, void* rhs_out, void* stream);
+
+/*
+ * Solves Z x = rhs by restarted GMRES(m) (the paper's solver, Sec. 5.1 and
+ * 6.4) with FP64 Krylov basis, Gram-Schmidt (two classical passes), Givens
+ * rotations and residual tests, and the FP32 FMM matvec.  x0 = 0.  Stops when
+ * the relative residual reaches cfg->tol (checked on the true residual at
+ * exit).  rhs, x_out: device complex64, N x nrhs (right-hand sides solved one
+ * after another).  iters_out / relres_out (HOST, nrhs entries each, may be
+ * NULL) receive the iteration count and final true relative residual.
+ * Returns HFMM_NOT_CONVERGED if any right-hand side hit max_iter (x_out then
+ * holds the last iterate).  Returns after completion.
+ */
+int hfmm_solve(hfmm_plan* plan, const void* rhs, void* x_out, int nrhs, int* iters_out,
+               double* relres_out, void* stream);
+
+/*
+ * hfmm_matvec for one right-hand side with CUDA events recorded on `stream`
+ * between the stages; returns after completion.  stage_ms (HOST, 9 floats)
+ * receives the device time of: 0 density prep, 1 near field (P2P), 2 P2M,
+ * 3 M2M, 4 M2L, 5 L2L, 6 L2P, 7 correction, 8 output permutation.
+ */
+int hfmm_matvec_timed(hfmm_plan* plan, const void* density, void* potential, float* stage_ms,
+                      void* stream);
+
+/*
+ * Algorithmic work of one matvec (HOST, 6 doubles): 0 near-field source-target
+ * pairs (j != i), 1 M2L complex multiply-adds (sum over translations of
+ * P_l^2), 2 M2M + L2L complex multiply-adds, 3 correction nonzeros,
+ * 4 points N, 5 expansion coefficients (all levels, multipoles + locals).
+ */
+int hfmm_plan_costs(const hfmm_plan* plan, double* costs);
+
+/* Number of kernels this plan has launched on the device since it was created. */
+int64_t hfmm_launch_count(const hfmm_plan* plan);
+
+/* Static description of a status code (never NULL). */
+const char* hfmm_status_string(int status);
+
+/* Detail of the last error raised on the calling thread ("" if none); the
+   string is owned by the library and valid until the next call on the thread. */
+const char* hfmm_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HFMM_H */

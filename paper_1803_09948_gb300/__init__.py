@@ -1,0 +1,310 @@
+"""Python binding of the GB300 Helmholtz FMM library (libhfmm.so, C ABI in include/hfmm.h).
+
+Argument marshalling only: every step of the matvec and the solve runs in the
+library's CUDA kernels.  Device vectors are torch complex64 CUDA tensors (or
+raw device pointers); PyTorch provides device memory and streams.  There is no
+CPU fallback: if the library is not built, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libhfmm.so")
+_lib = None
+
+HFMM_OK = 0
+HFMM_NOT_CONVERGED = 1
+HFMM_E_INVALID = -1
+HFMM_E_MESH = -2
+HFMM_E_NOMEM = -3
+HFMM_E_CUDA = -4
+HFMM_E_TIMEOUT = -5
+HFMM_E_OVERFLOW = -6
+
+EXPORTED = [
+    "hfmm_default_config", "hfmm_plan_create", "hfmm_plan_destroy", "hfmm_num_points", "hfmm_points",
+    "hfmm_plan_info", "hfmm_matvec", "hfmm_matvec_parts", "hfmm_direct", "hfmm_rhs_planewave",
+    "hfmm_solve", "hfmm_status_string", "hfmm_last_error", "hfmm_matvec_timed", "hfmm_launch_count",
+    "hfmm_plan_costs",
+]
+STAGES = ["prep", "p2p", "p2m", "m2m", "m2l", "l2l", "l2p", "corr", "output"]
+
+
+class hfmm_config(ctypes.Structure):
+    _fields_ = [
+        ("leaf_max", ctypes.c_int),
+        ("depth", ctypes.c_int),
+        ("p_fixed", ctypes.c_int),
+        ("p_min", ctypes.c_int),
+        ("near_factor", ctypes.c_double),
+        ("quad_order", ctypes.c_int),
+        ("restart", ctypes.c_int),
+        ("max_iter", ctypes.c_int),
+        ("tol", ctypes.c_double),
+        ("mem_budget_bytes", ctypes.c_double),
+    ]
+
+
+class HfmmError(RuntimeError):
+    def __init__(self, status, where):
+        self.status = status
+        detail = hfmm_last_error() if _lib is not None else ""
+        super().__init__(f"{where}: {hfmm_status_string(status)} ({status}) {detail}".strip())
+
+
+def lib():
+    """Loads libhfmm.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with __graft_entry__.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i64, dp = ctypes.c_void_p, ctypes.c_int64, ctypes.POINTER(ctypes.c_double)
+        L.hfmm_default_config.argtypes = [ctypes.POINTER(hfmm_config)]
+        L.hfmm_default_config.restype = None
+        L.hfmm_plan_create.argtypes = [ctypes.POINTER(hfmm_config), dp, i64, ctypes.POINTER(ctypes.c_int32), i64,
+                                       ctypes.c_double, ctypes.c_double, vp, ctypes.POINTER(vp)]
+        L.hfmm_plan_destroy.argtypes = [vp]
+        L.hfmm_plan_destroy.restype = None
+        L.hfmm_num_points.argtypes = [vp]
+        L.hfmm_num_points.restype = i64
+        L.hfmm_points.argtypes = [vp, dp, dp, ctypes.POINTER(ctypes.c_int32)]
+        L.hfmm_plan_info.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                     ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(i64),
+                                     ctypes.POINTER(i64)]
+        L.hfmm_matvec.argtypes = [vp, vp, vp, ctypes.c_int, vp]
+        L.hfmm_matvec_parts.argtypes = [vp, vp, vp, ctypes.c_int, ctypes.c_int, vp]
+        L.hfmm_direct.argtypes = [vp, vp, vp, ctypes.c_int, vp]
+        L.hfmm_rhs_planewave.argtypes = [vp, dp, ctypes.c_int, vp, vp]
+        L.hfmm_solve.argtypes = [vp, vp, vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), dp, vp]
+        L.hfmm_status_string.argtypes = [ctypes.c_int]
+        L.hfmm_status_string.restype = ctypes.c_char_p
+        L.hfmm_matvec_timed.argtypes = [vp, vp, vp, ctypes.POINTER(ctypes.c_float), vp]
+        L.hfmm_plan_costs.argtypes = [vp, dp]
+        L.hfmm_launch_count.argtypes = [vp]
+        L.hfmm_launch_count.restype = i64
+        L.hfmm_last_error.argtypes = []
+        L.hfmm_last_error.restype = ctypes.c_char_p
+        _lib = L
+    return _lib
+
+
+def _check(status, where):
+    if status < 0:
+        raise HfmmError(status, where)
+    return status
+
+
+def _ptr(x):
+    """Device (or host) address of a torch tensor / int / None."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return ctypes.c_void_p(x)
+    return ctypes.c_void_p(x.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _vec(t, n, nrhs, name):
+    import torch
+
+    if isinstance(t, int):
+        return
+    if not (t.is_cuda and t.dtype == torch.complex64 and t.is_contiguous() and t.numel() == n * nrhs):
+        raise ValueError(f"{name}: expected a contiguous complex64 CUDA tensor of {n * nrhs} elements")
+
+
+# ---------------------------------------------------------------- ABI mirrors
+def hfmm_default_config(**overrides):
+    c = hfmm_config()
+    lib().hfmm_default_config(ctypes.byref(c))
+    for k, v in overrides.items():
+        if not hasattr(c, k):
+            raise KeyError(k)
+        setattr(c, k, v)
+    return c
+
+
+def hfmm_status_string(status):
+    return lib().hfmm_status_string(int(status)).decode()
+
+
+def hfmm_last_error():
+    return lib().hfmm_last_error().decode()
+
+
+def hfmm_plan_create(cfg, vertices, tris, k_re, k_im=0.0, stream=None):
+    V = np.ascontiguousarray(vertices, dtype=np.float64)
+    F = np.ascontiguousarray(tris, dtype=np.int32)
+    out = ctypes.c_void_p()
+    st = hfmm_plan_create_raw(cfg, V, F, k_re, k_im, stream, out)
+    _check(st, "hfmm_plan_create")
+    return out
+
+
+def hfmm_plan_create_raw(cfg, V, F, k_re, k_im, stream, out):
+    return lib().hfmm_plan_create(
+        ctypes.byref(cfg), V.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), V.shape[0] if V.ndim else 0,
+        F.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), F.shape[0] if F.ndim else 0, float(k_re), float(k_im),
+        _stream(stream), ctypes.byref(out))
+
+
+def hfmm_plan_destroy(plan):
+    lib().hfmm_plan_destroy(plan)
+
+
+def hfmm_num_points(plan):
+    return int(lib().hfmm_num_points(plan))
+
+
+def hfmm_points(plan):
+    n = hfmm_num_points(plan)
+    xyz = np.empty((n, 3))
+    w = np.empty(n)
+    tri = np.empty(n, dtype=np.int32)
+    _check(lib().hfmm_points(plan, xyz.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                             w.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                             tri.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))), "hfmm_points")
+    return xyz, w, tri
+
+
+def hfmm_plan_info(plan):
+    depth = ctypes.c_int()
+    orders = (ctypes.c_int * 32)()
+    nl, nnz, m2l, by = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    _check(lib().hfmm_plan_info(plan, ctypes.byref(depth), orders, ctypes.byref(nl), ctypes.byref(nnz),
+                                ctypes.byref(m2l), ctypes.byref(by)), "hfmm_plan_info")
+    return {"depth": depth.value, "orders": [orders[l] for l in range(depth.value + 1)], "n_leaves": nl.value,
+            "corr_nnz": nnz.value, "m2l_translations": m2l.value, "device_bytes": by.value}
+
+
+def hfmm_matvec(plan, density, potential, nrhs=1, stream=None):
+    n = hfmm_num_points(plan)
+    _vec(density, n, nrhs, "density")
+    _vec(potential, n, nrhs, "potential")
+    _check(lib().hfmm_matvec(plan, _ptr(density), _ptr(potential), int(nrhs), _stream(stream)), "hfmm_matvec")
+
+
+def hfmm_matvec_parts(plan, density, potential, parts, nrhs=1, stream=None):
+    n = hfmm_num_points(plan)
+    _vec(density, n, nrhs, "density")
+    _vec(potential, n, nrhs, "potential")
+    _check(lib().hfmm_matvec_parts(plan, _ptr(density), _ptr(potential), int(nrhs), int(parts), _stream(stream)),
+           "hfmm_matvec_parts")
+
+
+def hfmm_matvec_timed(plan, density, potential, stream=None):
+    """One matvec with per-stage device times (ms), keyed by STAGES."""
+    n = hfmm_num_points(plan)
+    _vec(density, n, 1, "density")
+    _vec(potential, n, 1, "potential")
+    ms = (ctypes.c_float * 9)()
+    _check(lib().hfmm_matvec_timed(plan, _ptr(density), _ptr(potential), ms, _stream(stream)), "hfmm_matvec_timed")
+    return dict(zip(STAGES, [float(v) for v in ms]))
+
+
+def hfmm_plan_costs(plan):
+    c = (ctypes.c_double * 6)()
+    _check(lib().hfmm_plan_costs(plan, c), "hfmm_plan_costs")
+    keys = ["p2p_pairs", "m2l_cmacs", "m2m_l2l_cmacs", "corr_nnz", "n_points", "coefficients"]
+    return dict(zip(keys, [float(v) for v in c]))
+
+
+def hfmm_launch_count(plan):
+    return int(lib().hfmm_launch_count(plan))
+
+
+def hfmm_direct(plan, density, potential, nrhs=1, stream=None):
+    n = hfmm_num_points(plan)
+    _vec(density, n, nrhs, "density")
+    _vec(potential, n, nrhs, "potential")
+    _check(lib().hfmm_direct(plan, _ptr(density), _ptr(potential), int(nrhs), _stream(stream)), "hfmm_direct")
+
+
+def hfmm_rhs_planewave(plan, dirs, rhs_out, stream=None):
+    d = np.ascontiguousarray(np.atleast_2d(dirs), dtype=np.float64)
+    n = hfmm_num_points(plan)
+    _vec(rhs_out, n, d.shape[0], "rhs_out")
+    _check(lib().hfmm_rhs_planewave(plan, d.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), d.shape[0],
+                                    _ptr(rhs_out), _stream(stream)), "hfmm_rhs_planewave")
+
+
+def hfmm_solve(plan, rhs, x_out, nrhs=1, stream=None):
+    """Returns (status, iterations[nrhs], relative residuals[nrhs])."""
+    n = hfmm_num_points(plan)
+    _vec(rhs, n, nrhs, "rhs")
+    _vec(x_out, n, nrhs, "x_out")
+    its = (ctypes.c_int * nrhs)()
+    rr = (ctypes.c_double * nrhs)()
+    st = _check(lib().hfmm_solve(plan, _ptr(rhs), _ptr(x_out), int(nrhs), its, rr, _stream(stream)), "hfmm_solve")
+    return st, list(its), list(rr)
+
+
+class Plan:
+    """Owning wrapper: Plan(vertices, tris, k, **config) ... plan.close()."""
+
+    def __init__(self, vertices, tris, k, stream=None, **cfg):
+        self.cfg = hfmm_default_config(**cfg)
+        self.handle = hfmm_plan_create(self.cfg, vertices, tris, k, 0.0, stream)
+        self.n = hfmm_num_points(self.handle)
+        self.k = float(k)
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            hfmm_plan_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def info(self):
+        return hfmm_plan_info(self.handle)
+
+    def points(self):
+        return hfmm_points(self.handle)
+
+    def matvec(self, density, potential, nrhs=1, stream=None):
+        hfmm_matvec(self.handle, density, potential, nrhs, stream)
+
+    def matvec_parts(self, density, potential, parts, nrhs=1, stream=None):
+        hfmm_matvec_parts(self.handle, density, potential, parts, nrhs, stream)
+
+    def matvec_timed(self, density, potential, stream=None):
+        return hfmm_matvec_timed(self.handle, density, potential, stream)
+
+    def costs(self):
+        return hfmm_plan_costs(self.handle)
+
+    def launch_count(self):
+        return hfmm_launch_count(self.handle)
+
+    def direct(self, density, potential, nrhs=1, stream=None):
+        hfmm_direct(self.handle, density, potential, nrhs, stream)
+
+    def rhs_planewave(self, dirs, rhs_out, stream=None):
+        hfmm_rhs_planewave(self.handle, dirs, rhs_out, stream)
+
+    def solve(self, rhs, x_out, nrhs=1, stream=None):
+        return hfmm_solve(self.handle, rhs, x_out, nrhs, stream)

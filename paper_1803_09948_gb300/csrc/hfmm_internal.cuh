@@ -1,0 +1,195 @@
+// Internal declarations of the GB300 Helmholtz FMM library (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/hfmm.h"
+
+#define HFMM_MAXLEV 21
+#define HFMM_PMAX 40          // largest expansion order a plan accepts
+#define HFMM_NEAR_CAP 128     // largest near/self triangle set per target
+#define HFMM_TRANS_NB 64      // columns per translation work item
+
+// ---------------------------------------------------------------- errors
+struct HfmmError {
+    int code;
+    std::string what;
+};
+
+#define HFMM_CUDA(call)                                                              \
+    do {                                                                             \
+        cudaError_t e_ = (call);                                                     \
+        if (e_ != cudaSuccess)                                                       \
+            throw HfmmError{e_ == cudaErrorMemoryAllocation ? HFMM_E_NOMEM : HFMM_E_CUDA, \
+                            std::string(#call) + ": " + cudaGetErrorString(e_)};     \
+    } while (0)
+
+// ---------------------------------------------------------------- device buffers
+template <typename T>
+struct DBuf {
+    T* p = nullptr;
+    size_t n = 0;
+    DBuf() = default;
+    DBuf(const DBuf&) = delete;
+    DBuf& operator=(const DBuf&) = delete;
+    ~DBuf() { release(); }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        n = 0;
+    }
+    void alloc(size_t count, size_t* counter) {
+        release();
+        if (count == 0) count = 1;
+        HFMM_CUDA(cudaMalloc((void**)&p, count * sizeof(T)));
+        n = count;
+        if (counter) *counter += count * sizeof(T);
+    }
+    void upload(const std::vector<T>& h, size_t* counter, cudaStream_t st) {
+        alloc(h.size(), counter);
+        if (!h.empty())
+            HFMM_CUDA(cudaMemcpyAsync(p, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice, st));
+    }
+};
+
+// ---------------------------------------------------------------- translation work
+// One work item: Out[:, dst_c] += T * In[:, src_c] for up to HFMM_TRANS_NB column
+// pairs.  T is row-major [Pout][Pin] complex64; column c of a coefficient
+// array at base offset b is coef[b + c * P .. b + c * P + P).
+struct TransItem {
+    int64_t op;    // offset (complex elements) of T in the operator buffer
+    int64_t src;   // base offset of the source coefficient array
+    int64_t dst;   // base offset of the destination coefficient array
+    int32_t cols;  // first entry in the column-pair list
+    int16_t ncol;  // number of column pairs (<= HFMM_TRANS_NB)
+    int16_t pin, pout;  // Pin = (p_in+1)^2, Pout = (p_out+1)^2
+    int16_t atomic;     // 1: accumulate with atomics (destinations shared across items)
+    int16_t pad[2];
+};
+
+struct LevelInfo {
+    int p = 0, P = 0;       // order and (p+1)^2
+    double s = 1.0;         // scale min(1, k a)
+    double side = 0.0;      // box side
+    int64_t nbox = 0;
+    int64_t box0 = 0;       // first box of this level in the all-level box arrays
+    int64_t mofs = 0;       // offset of this level's multipoles in coef
+    int64_t lofs = 0;       // offset of this level's locals in coef
+    int64_t m2l_op = 0;     // offset of 343 M2L operators (316 used) [343][P][P]
+    int64_t pc_op = 0;      // offset of 8 L2L operators [8][P][P_parent] (levels >= 3)
+    int64_t m2m_op = 0;     // offset of 8 M2M operators [8][P_parent][P] (levels >= 3)
+};
+
+struct hfmm_plan {
+    hfmm_config cfg;
+    double k = 0.0;
+    int64_t N = 0, nt = 0;
+    int L = 0;
+    double D = 0.0, lo[3] = {0, 0, 0};
+    double r_near = 0.0, mean_edge = 0.0;
+    LevelInfo lev[HFMM_MAXLEV + 1];
+    int64_t nleaf = 0, ntiles = 0;
+    int64_t corr_nnz = 0, m2l_count = 0;
+    size_t dev_bytes = 0;
+    bool poly_p2p = true;   // near field fits the polynomial kernel range
+    float p2p_shift = 0.f;  // k * side of a leaf
+
+    // sorted point data
+    DBuf<float4> pts;        // k * (x - leaf centre), sorted
+    DBuf<int32_t> perm;      // sorted -> user
+    DBuf<int32_t> iperm;     // user -> sorted
+    DBuf<float> wscale;      // k w / (4 pi), sorted
+    DBuf<int32_t> pt_leaf;   // leaf of each sorted point
+    DBuf<double> x64;        // user-order FP64 points (N x 3)
+    std::vector<double> host_x, host_w;  // user-order points and weights (host copies)
+    std::vector<int32_t> host_t;         // triangle of each point
+    // leaves
+    DBuf<int32_t> leaf_start;  // nleaf + 1
+    DBuf<int4> leaf_ijk;       // integer coordinates at level L
+    DBuf<int32_t> nbr_ptr, nbr;
+    DBuf<int4> tiles;          // (leaf, first point, count, 0)
+    // far field
+    DBuf<float2> coef;         // all multipoles and locals
+    int64_t coef_m_total = 0, coef_total = 0;
+    DBuf<float2> ops;          // all translation operators
+    DBuf<TransItem> items;
+    DBuf<int2> item_cols;
+    std::vector<int64_t> m2m_items_begin, m2m_items_end;  // per level l (parents at l)
+    std::vector<int64_t> l2l_items_begin, l2l_items_end;  // per level l (children at l)
+    int64_t m2l_items_begin = 0, m2l_items_end = 0;
+    // correction
+    DBuf<int64_t> corr_ptr;
+    DBuf<int32_t> corr_col;
+    DBuf<float2> corr_val;
+    // scratch (one matvec at a time per plan)
+    DBuf<float2> sig, phi;
+    // GMRES workspace (allocated on first solve, kept resident)
+    DBuf<double2> kry;         // (restart + 1) x N
+    DBuf<double2> gw, gx, gb;  // work vector, iterate, right-hand side
+    DBuf<double> gred;         // reduction scratch
+    int kry_m = 0;
+    int64_t launches = 0;       // kernels launched by this plan
+    double cost[6] = {0, 0, 0, 0, 0, 0};  // see hfmm_plan_costs
+    cudaEvent_t* stage_ev = nullptr;  // set by hfmm_matvec_timed: events after each stage
+};
+
+// ---------------------------------------------------------------- kernels: FMM matvec
+namespace hfmm {
+
+// sig_sorted = k w / (4 pi) * density[perm]  (one right-hand side)
+void launch_density_prep(hfmm_plan* P, const void* density, bool fp64, float2* sig, cudaStream_t st);
+// out[perm[i]] = phi[i]
+void launch_output(hfmm_plan* P, const float2* phi, void* out, bool fp64, cudaStream_t st);
+// parts bit 0 near, 1 far, 2 correction; writes P->phi
+void run_matvec_sorted(hfmm_plan* P, int parts, cudaStream_t st);
+// records stage event q (if timing is active)
+void mark_stage(hfmm_plan* P, int q, cudaStream_t st);
+void run_direct_sorted(hfmm_plan* P, cudaStream_t st);
+void launch_planewave(hfmm_plan* P, double dx, double dy, double dz, float2* out, cudaStream_t st);
+
+// ---------------------------------------------------------------- kernels: plan build (FP64)
+struct ProjectionJob {
+    int type;          // 0: regular functions, 1: outgoing functions
+    int pf, pb;        // orders of the functions and of the projection basis
+    double sf, sb;     // scales
+    double rho;        // projection radius
+    int nth, nph;      // quadrature
+    int nops;          // number of operators
+    const double* d0;  // host: nops x 3 vectors (function centre - sphere centre)
+    float2* out;       // device: nops x [Pb][Pf]
+    bool conj_transpose_copy;  // also write T^H to out2
+    float2* out2;      // device: nops x [Pf][Pb]
+};
+void build_projection_ops(const ProjectionJob& job, double k, cudaStream_t st);
+
+struct CorrInputs {
+    const double* x64s;     // sorted FP64 points (N x 3)
+    const int32_t* tri_s;   // triangle of each sorted point
+    const double* V;        // vertices (device)
+    const int32_t* F;       // triangles (device)
+    const int32_t* iperm;   // user -> sorted
+    const double* w64s;     // sorted FP64 weights
+    const uint64_t* skey;   // sorted keys of the search-level boxes
+    const int32_t* sstart;  // point ranges of the search-level boxes (nsbox + 1)
+    int64_t nsbox;
+    int search_level, L;
+    const int4* pt_ijk;     // level-L integer coordinates of each sorted point
+    int64_t N;
+    double k, r_near;
+    int quad_order;
+};
+// Returns nnz; fills P->corr_ptr / corr_col / corr_val.
+int64_t build_correction(hfmm_plan* P, const CorrInputs& in, cudaStream_t st);
+
+// ---------------------------------------------------------------- GMRES
+int run_gmres(hfmm_plan* P, const void* rhs, void* x, int* iters, double* relres, cudaStream_t st);
+
+// host special functions (plan building only)
+void host_jn_scaled(int nmax, double z, double s, double* out);
+void host_hn_scaled(int nmax, double z, double s, double* re, double* im);
+
+}  // namespace hfmm

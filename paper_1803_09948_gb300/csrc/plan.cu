@@ -1,0 +1,698 @@
+// Plan construction (host orchestration) and the C ABI entry points.
+//
+// A plan holds, on the device: Morton-sorted points and weights, the uniform
+// octree (leaves, neighbour lists, interaction lists grouped by translation
+// offset), all translation operators, and the sparse self/near correction.
+// Sec. 2.2 (discretisation, singular treatment), Sec. 2.3 (octree, sweeps),
+// Sec. 3.1-3.2 (Morton order, cell = index + count).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "hfmm_internal.cuh"
+#include "kernel_poly.h"
+
+using namespace hfmm;
+
+static thread_local std::string g_last_error;
+
+static inline uint64_t spread3_h(uint64_t v) {
+    v &= 0x1fffff;
+    v = (v | v << 32) & 0x1f00000000ffffull;
+    v = (v | v << 16) & 0x1f0000ff0000ffull;
+    v = (v | v << 8) & 0x100f00f00f00f00full;
+    v = (v | v << 4) & 0x10c30c30c30c30c3ull;
+    v = (v | v << 2) & 0x1249249249249249ull;
+    return v;
+}
+static inline uint64_t morton_h(uint64_t x, uint64_t y, uint64_t z) {
+    return (spread3_h(x) << 2) | (spread3_h(y) << 1) | spread3_h(z);
+}
+static inline uint64_t compact3_h(uint64_t v) {
+    v &= 0x1249249249249249ull;
+    v = (v ^ (v >> 2)) & 0x10c30c30c30c30c3ull;
+    v = (v ^ (v >> 4)) & 0x100f00f00f00f00full;
+    v = (v ^ (v >> 8)) & 0x1f0000ff0000ffull;
+    v = (v ^ (v >> 16)) & 0x1f00000000ffffull;
+    v = (v ^ (v >> 32)) & 0x1fffff;
+    return v;
+}
+static inline void demorton_h(uint64_t k, int64_t* c) {
+    c[0] = (int64_t)compact3_h(k >> 2);
+    c[1] = (int64_t)compact3_h(k >> 1);
+    c[2] = (int64_t)compact3_h(k);
+}
+
+static int64_t find_sorted(const std::vector<uint64_t>& keys, uint64_t key) {
+    auto it = std::lower_bound(keys.begin(), keys.end(), key);
+    if (it == keys.end() || *it != key) return -1;
+    return (int64_t)(it - keys.begin());
+}
+
+// projection radius in [0.55 a, a] keeping every j_n(k rho), n <= p, away from a zero
+static double choose_rho(double k, double a, int p) {
+    std::vector<double> re(p + 1), im(p + 1);
+    double best = a, best_score = -1.0;
+    for (int t = 0; t <= 32; ++t) {
+        double rho = a * (1.0 - 0.45 * t / 32.0);
+        host_hn_scaled(p, k * rho, 1.0, re.data(), im.data());
+        double sc = 1e300;
+        for (int n = 0; n <= p; ++n) sc = std::min(sc, std::fabs(re[n]) / std::hypot(re[n], im[n]));
+        if (sc > best_score * 1.0000001) {
+            best_score = sc;
+            best = rho;
+        }
+    }
+    return best;
+}
+
+static int level_order(const hfmm_config& c, double k, double side) {
+    if (c.p_fixed > 0) return c.p_fixed;
+    double ka = k * 0.5 * std::sqrt(3.0) * side;
+    int p = (int)std::ceil(ka + 6.0 * std::log10(ka + 3.14159265358979323846));
+    return std::max(p, c.p_min);
+}
+
+namespace {
+struct HostLevel {
+    std::vector<uint64_t> key;
+    std::vector<int32_t> start;  // nbox + 1
+};
+
+struct PairBuckets {
+    std::vector<std::vector<int2>> b;
+    explicit PairBuckets(int n) : b(n) {}
+};
+
+void emit_items(const PairBuckets& pb, const std::vector<int64_t>& op_of_bucket, int64_t src, int64_t dst, int pin,
+                int pout, int atomic, std::vector<TransItem>& items, std::vector<int2>& cols) {
+    for (size_t g = 0; g < pb.b.size(); ++g) {
+        const auto& v = pb.b[g];
+        for (size_t c0 = 0; c0 < v.size(); c0 += HFMM_TRANS_NB) {
+            TransItem it{};
+            it.op = op_of_bucket[g];
+            it.src = src;
+            it.dst = dst;
+            it.cols = (int32_t)cols.size();
+            it.ncol = (int16_t)std::min<size_t>(HFMM_TRANS_NB, v.size() - c0);
+            it.pin = (int16_t)pin;
+            it.pout = (int16_t)pout;
+            it.atomic = (int16_t)atomic;
+            for (int q = 0; q < it.ncol; ++q) cols.push_back(v[c0 + q]);
+            items.push_back(it);
+        }
+    }
+}
+}  // namespace
+
+static void build_plan(hfmm_plan* P, const double* V, int64_t nv, const int32_t* F, int64_t nt, cudaStream_t st) {
+    const hfmm_config& cfg = P->cfg;
+    const double k = P->k;
+    const int64_t N = 3 * nt;
+    P->nt = nt;
+    P->N = N;
+    // ---------------------------------------------------------- points (Sec. 2.2)
+    std::vector<double> X(3 * N), W(N);
+    std::vector<int32_t> T(N);
+    double edge_sum = 0.0;
+    for (int64_t n = 0; n < nt; ++n) {
+        const double* v[3];
+        for (int a = 0; a < 3; ++a) {
+            int32_t id = F[3 * n + a];
+            if (id < 0 || id >= nv) throw HfmmError{HFMM_E_MESH, "triangle vertex index out of range"};
+            v[a] = V + 3 * (int64_t)id;
+            for (int d = 0; d < 3; ++d)
+                if (!std::isfinite(v[a][d])) throw HfmmError{HFMM_E_MESH, "non-finite vertex coordinate"};
+        }
+        double e1[3], e2[3];
+        for (int d = 0; d < 3; ++d) {
+            e1[d] = v[1][d] - v[0][d];
+            e2[d] = v[2][d] - v[0][d];
+        }
+        double c[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2], e1[0] * e2[1] - e1[1] * e2[0]};
+        double area = 0.5 * std::sqrt(c[0] * c[0] + c[1] * c[1] + c[2] * c[2]);
+        double l2 = e1[0] * e1[0] + e1[1] * e1[1] + e1[2] * e1[2];
+        if (!(area > 1e-14 * l2) || !(area > 0.0)) throw HfmmError{HFMM_E_MESH, "degenerate (zero-area) triangle"};
+        for (int a = 0; a < 3; ++a) {
+            double e[3];
+            for (int d = 0; d < 3; ++d) e[d] = v[(a + 1) % 3][d] - v[a][d];
+            edge_sum += std::sqrt(e[0] * e[0] + e[1] * e[1] + e[2] * e[2]);
+            int64_t i = 3 * n + a;
+            for (int d = 0; d < 3; ++d)
+                X[3 * i + d] = (2.0 / 3.0) * v[a][d] + (1.0 / 6.0) * v[(a + 1) % 3][d] + (1.0 / 6.0) * v[(a + 2) % 3][d];
+            W[i] = area / 3.0;
+            T[i] = (int32_t)n;
+        }
+    }
+    P->mean_edge = edge_sum / (3.0 * (double)nt);
+    P->r_near = cfg.near_factor * P->mean_edge;
+    // ---------------------------------------------------------- octree
+    double mn[3] = {1e300, 1e300, 1e300}, mx[3] = {-1e300, -1e300, -1e300};
+    for (int64_t i = 0; i < N; ++i)
+        for (int d = 0; d < 3; ++d) {
+            mn[d] = std::min(mn[d], X[3 * i + d]);
+            mx[d] = std::max(mx[d], X[3 * i + d]);
+        }
+    double ext = std::max(mx[0] - mn[0], std::max(mx[1] - mn[1], mx[2] - mn[2]));
+    double D = 1.0;
+    if (ext > 0.0) {
+        while (D < ext) D *= 2.0;
+        while (D * 0.5 >= ext) D *= 0.5;
+    }
+    P->D = D;
+    for (int d = 0; d < 3; ++d) P->lo[d] = 0.5 * (mn[d] + mx[d]) - 0.5 * D;
+    const int LMAX = 20;
+    const double scale20 = std::ldexp(1.0, LMAX) / D;
+    std::vector<std::pair<uint64_t, int32_t>> kv(N);
+    for (int64_t i = 0; i < N; ++i) {
+        uint64_t c[3];
+        for (int d = 0; d < 3; ++d) {
+            int64_t q = (int64_t)std::floor((X[3 * i + d] - P->lo[d]) * scale20);
+            q = std::max<int64_t>(0, std::min<int64_t>(q, ((int64_t)1 << LMAX) - 1));
+            c[d] = (uint64_t)q;
+        }
+        kv[i] = {morton_h(c[0], c[1], c[2]), (int32_t)i};
+    }
+    std::sort(kv.begin(), kv.end());
+    int L = cfg.depth;
+    if (L <= 0) {
+        for (L = 0; L < LMAX; ++L) {
+            int sh = 3 * (LMAX - L);
+            int64_t run = 0, best = 0;
+            for (int64_t i = 0; i < N; ++i) {
+                run = (i > 0 && (kv[i].first >> sh) == (kv[i - 1].first >> sh)) ? run + 1 : 1;
+                best = std::max(best, run);
+            }
+            if (best <= cfg.leaf_max) break;
+        }
+    }
+    L = std::min(L, LMAX);
+    P->L = L;
+    std::vector<HostLevel> lv(L + 1);
+    for (int l = 0; l <= L; ++l) {
+        int sh = 3 * (LMAX - l);
+        for (int64_t i = 0; i < N; ++i) {
+            uint64_t key = kv[i].first >> sh;
+            if (i == 0 || key != (kv[i - 1].first >> sh)) {
+                lv[l].key.push_back(key);
+                lv[l].start.push_back((int32_t)i);
+            }
+        }
+        lv[l].start.push_back((int32_t)N);
+        P->lev[l].nbox = (int64_t)lv[l].key.size();
+        P->lev[l].side = D / std::ldexp(1.0, l);
+        if (l >= 2) {
+            P->lev[l].p = level_order(cfg, k, P->lev[l].side);
+            if (P->lev[l].p > HFMM_PMAX) throw HfmmError{HFMM_E_INVALID, "expansion order above HFMM_PMAX"};
+            P->lev[l].P = (P->lev[l].p + 1) * (P->lev[l].p + 1);
+        }
+        P->lev[l].s = std::min(1.0, k * 0.5 * std::sqrt(3.0) * P->lev[l].side);
+    }
+    // ---------------------------------------------------------- sorted point data
+    std::vector<int32_t> perm(N), iperm(N), pt_leaf(N);
+    for (int64_t i = 0; i < N; ++i) {
+        perm[i] = kv[i].second;
+        iperm[kv[i].second] = (int32_t)i;
+    }
+    const HostLevel& leaves = lv[L];
+    int64_t nleaf = (int64_t)leaves.key.size();
+    P->nleaf = nleaf;
+    const double sideL = P->lev[L].side;
+    std::vector<float4> pts(N);
+    std::vector<float> wscale(N);
+    std::vector<int4> leaf_ijk(nleaf), pt_ijk(N);
+    std::vector<double> x64s(3 * N), w64s(N);
+    std::vector<int32_t> tri_s(N);
+    const double kPi = 3.14159265358979323846;
+    for (int64_t b = 0; b < nleaf; ++b) {
+        int64_t c[3];
+        demorton_h(leaves.key[b], c);
+        leaf_ijk[b] = make_int4((int)c[0], (int)c[1], (int)c[2], 0);
+        double ctr[3];
+        for (int d = 0; d < 3; ++d) ctr[d] = P->lo[d] + ((double)c[d] + 0.5) * sideL;
+        for (int32_t i = leaves.start[b]; i < leaves.start[b + 1]; ++i) {
+            int32_t u = perm[i];
+            pts[i] = make_float4((float)(k * (X[3 * u] - ctr[0])), (float)(k * (X[3 * u + 1] - ctr[1])),
+                                 (float)(k * (X[3 * u + 2] - ctr[2])), 0.f);
+            wscale[i] = (float)(k * W[u] / (4.0 * kPi));
+            pt_leaf[i] = (int32_t)b;
+            pt_ijk[i] = leaf_ijk[b];
+            for (int d = 0; d < 3; ++d) x64s[3 * i + d] = X[3 * u + d];
+            w64s[i] = W[u];
+            tri_s[i] = T[u];
+        }
+    }
+    // neighbour lists (27 boxes, self included) and target tiles
+    std::vector<int32_t> nbr_ptr(nleaf + 1, 0), nbr;
+    std::vector<int4> tiles;
+    int64_t nl = (int64_t)1 << L;
+    for (int64_t b = 0; b < nleaf; ++b) {
+        int4 c = leaf_ijk[b];
+        for (int dx = -1; dx <= 1; ++dx)
+            for (int dy = -1; dy <= 1; ++dy)
+                for (int dz = -1; dz <= 1; ++dz) {
+                    int64_t x = c.x + dx, y = c.y + dy, z = c.z + dz;
+                    if (x < 0 || y < 0 || z < 0 || x >= nl || y >= nl || z >= nl) continue;
+                    int64_t s = find_sorted(leaves.key, morton_h(x, y, z));
+                    if (s >= 0) nbr.push_back((int32_t)s);
+                }
+        nbr_ptr[b + 1] = (int32_t)nbr.size();
+        for (int32_t i0 = leaves.start[b]; i0 < leaves.start[b + 1]; i0 += 32)
+            tiles.push_back(make_int4((int)b, i0, std::min(32, leaves.start[b + 1] - i0), 0));
+    }
+    P->ntiles = (int64_t)tiles.size();
+    double pairs = 0.0;
+    for (int64_t b = 0; b < nleaf; ++b) {
+        double nt_b = leaves.start[b + 1] - leaves.start[b];
+        for (int32_t q = nbr_ptr[b]; q < nbr_ptr[b + 1]; ++q)
+            pairs += nt_b * (double)(leaves.start[nbr[q] + 1] - leaves.start[nbr[q]]);
+    }
+    P->cost[0] = pairs - (double)N;
+    P->cost[4] = (double)N;
+    P->p2p_shift = (float)(k * sideL);
+    P->poly_p2p = 12.0 * (k * sideL) * (k * sideL) * 1.001 <= (double)HFMM_POLY_UMAX;
+
+    size_t* cnt = &P->dev_bytes;
+    P->pts.upload(pts, cnt, st);
+    P->perm.upload(perm, cnt, st);
+    P->iperm.upload(iperm, cnt, st);
+    P->wscale.upload(wscale, cnt, st);
+    P->pt_leaf.upload(pt_leaf, cnt, st);
+    P->x64.upload(X, cnt, st);
+    P->leaf_start.upload(leaves.start, cnt, st);
+    P->leaf_ijk.upload(leaf_ijk, cnt, st);
+    P->nbr_ptr.upload(nbr_ptr, cnt, st);
+    P->nbr.upload(nbr, cnt, st);
+    P->tiles.upload(tiles, cnt, st);
+    P->sig.alloc(N, cnt);
+    P->phi.alloc(N, cnt);
+    P->host_x = X;
+    P->host_w = W;
+    P->host_t = T;
+
+    // ---------------------------------------------------------- far field (Sec. 2.3)
+    P->m2m_items_begin.assign(L + 2, 0);
+    P->m2m_items_end.assign(L + 2, 0);
+    P->l2l_items_begin.assign(L + 2, 0);
+    P->l2l_items_end.assign(L + 2, 0);
+    if (L >= 2) {
+        int64_t off = 0;
+        for (int l = 2; l <= L; ++l) {
+            P->lev[l].mofs = off;
+            off += P->lev[l].nbox * P->lev[l].P;
+        }
+        P->coef_m_total = off;
+        for (int l = 2; l <= L; ++l) {
+            P->lev[l].lofs = off;
+            off += P->lev[l].nbox * P->lev[l].P;
+        }
+        P->coef_total = off;
+        P->cost[5] = (double)off;
+        int64_t ooff = 0;
+        for (int l = 2; l <= L; ++l) {
+            int Pl = P->lev[l].P;
+            P->lev[l].m2l_op = ooff;
+            ooff += 316ll * Pl * Pl;
+            if (l >= 3) {
+                int Pp = P->lev[l - 1].P;
+                P->lev[l].pc_op = ooff;
+                ooff += 8ll * Pl * Pp;
+                P->lev[l].m2m_op = ooff;
+                ooff += 8ll * Pl * Pp;
+            }
+        }
+        if (cfg.mem_budget_bytes > 0 &&
+            (double)P->dev_bytes + 8.0 * (double)(ooff + P->coef_total) > cfg.mem_budget_bytes)
+            throw HfmmError{HFMM_E_NOMEM, "plan exceeds the configured device memory budget"};
+        P->coef.alloc(P->coef_total, cnt);
+        P->ops.alloc(ooff, cnt);
+        // offset table: 343 offsets in [-3,3]^3 minus the 27 neighbours -> 316 slots
+        int slot[343];
+        std::vector<double> d0_unit;
+        int ns = 0;
+        for (int o = 0; o < 343; ++o) {
+            int dx = o / 49 - 3, dy = (o / 7) % 7 - 3, dz = o % 7 - 3;
+            if (std::abs(dx) <= 1 && std::abs(dy) <= 1 && std::abs(dz) <= 1) {
+                slot[o] = -1;
+                continue;
+            }
+            slot[o] = ns++;
+            d0_unit.push_back(dx);
+            d0_unit.push_back(dy);
+            d0_unit.push_back(dz);
+        }
+        for (int l = 2; l <= L; ++l) {
+            const LevelInfo& li = P->lev[l];
+            double a = 0.5 * std::sqrt(3.0) * li.side;
+            ProjectionJob job{};
+            job.type = 1;
+            job.pf = job.pb = li.p;
+            job.sf = job.sb = li.s;
+            job.rho = choose_rho(k, a, li.p);
+            job.nth = job.pb + (job.pf + 1) / 2 + 16;
+            job.nph = 2 * job.nth + 2;
+            job.nops = 316;
+            std::vector<double> d0(d0_unit);
+            for (double& v : d0) v *= li.side;  // c_source - c_target
+            job.d0 = d0.data();
+            job.out = P->ops.p + li.m2l_op;
+            job.out2 = nullptr;
+            build_projection_ops(job, k, st);
+            if (l >= 3) {
+                const LevelInfo& lp = P->lev[l - 1];
+                ProjectionJob pj{};
+                pj.type = 0;
+                pj.pf = lp.p;
+                pj.sf = lp.s;
+                pj.pb = li.p;
+                pj.sb = li.s;
+                pj.rho = choose_rho(k, a, li.p);
+                pj.nth = pj.pb + (pj.pf + 1) / 2 + 16;
+                pj.nph = 2 * pj.nth + 2;
+                pj.nops = 8;
+                std::vector<double> dd(24);
+                for (int o = 0; o < 8; ++o) {
+                    int bits[3] = {(o >> 2) & 1, (o >> 1) & 1, o & 1};
+                    for (int d = 0; d < 3; ++d) dd[3 * o + d] = -0.25 * lp.side * (2.0 * bits[d] - 1.0);  // c_parent - c_child
+                }
+                pj.d0 = dd.data();
+                pj.out = P->ops.p + li.pc_op;
+                pj.out2 = P->ops.p + li.m2m_op;
+                build_projection_ops(pj, k, st);
+            }
+        }
+        // work items
+        std::vector<TransItem> items;
+        std::vector<int2> cols;
+        for (int l = L - 1; l >= 2; --l) {  // M2M: children at l+1 -> parents at l
+            PairBuckets pb(8);
+            const HostLevel& ch = lv[l + 1];
+            for (int64_t c = 0; c < (int64_t)ch.key.size(); ++c) {
+                int64_t par = find_sorted(lv[l].key, ch.key[c] >> 3);
+                pb.b[ch.key[c] & 7].push_back(make_int2((int)c, (int)par));
+            }
+            std::vector<int64_t> ops(8);
+            for (int o = 0; o < 8; ++o) ops[o] = P->lev[l + 1].m2m_op + (int64_t)o * P->lev[l].P * P->lev[l + 1].P;
+            P->m2m_items_begin[l] = (int64_t)items.size();
+            emit_items(pb, ops, P->lev[l + 1].mofs, P->lev[l].mofs, P->lev[l + 1].P, P->lev[l].P, 1, items, cols);
+            P->m2m_items_end[l] = (int64_t)items.size();
+            P->cost[2] += (double)ch.key.size() * P->lev[l].P * P->lev[l + 1].P;
+        }
+        P->m2l_items_begin = (int64_t)items.size();
+        int64_t m2l_count = 0;
+        for (int l = 2; l <= L; ++l) {
+            PairBuckets pb(316);
+            const HostLevel& H = lv[l];
+            int64_t nlv = (int64_t)1 << l;
+            for (int64_t t = 0; t < (int64_t)H.key.size(); ++t) {
+                int64_t c[3];
+                demorton_h(H.key[t], c);
+                int64_t px = c[0] >> 1, py = c[1] >> 1, pz = c[2] >> 1;
+                for (int ex = -1; ex <= 1; ++ex)
+                    for (int ey = -1; ey <= 1; ++ey)
+                        for (int ez = -1; ez <= 1; ++ez) {
+                            int64_t qx = px + ex, qy = py + ey, qz = pz + ez;
+                            if (qx < 0 || qy < 0 || qz < 0 || 2 * qx >= nlv || 2 * qy >= nlv || 2 * qz >= nlv) continue;
+                            for (int o = 0; o < 8; ++o) {
+                                int64_t sx = 2 * qx + ((o >> 2) & 1), sy = 2 * qy + ((o >> 1) & 1), sz = 2 * qz + (o & 1);
+                                int64_t dx = sx - c[0], dy = sy - c[1], dz = sz - c[2];
+                                if (std::llabs(dx) <= 1 && std::llabs(dy) <= 1 && std::llabs(dz) <= 1) continue;
+                                int64_t s = find_sorted(H.key, morton_h(sx, sy, sz));
+                                if (s < 0) continue;
+                                int sl = slot[(dx + 3) * 49 + (dy + 3) * 7 + (dz + 3)];
+                                pb.b[sl].push_back(make_int2((int)s, (int)t));
+                                ++m2l_count;
+                                P->cost[1] += (double)P->lev[l].P * P->lev[l].P;
+                            }
+                        }
+            }
+            std::vector<int64_t> ops(316);
+            for (int o = 0; o < 316; ++o) ops[o] = P->lev[l].m2l_op + (int64_t)o * P->lev[l].P * P->lev[l].P;
+            emit_items(pb, ops, P->lev[l].mofs, P->lev[l].lofs, P->lev[l].P, P->lev[l].P, 1, items, cols);
+        }
+        P->m2l_items_end = (int64_t)items.size();
+        P->m2l_count = m2l_count;
+        for (int l = 3; l <= L; ++l) {  // L2L: parents at l-1 -> children at l
+            PairBuckets pb(8);
+            const HostLevel& ch = lv[l];
+            for (int64_t c = 0; c < (int64_t)ch.key.size(); ++c) {
+                int64_t par = find_sorted(lv[l - 1].key, ch.key[c] >> 3);
+                pb.b[ch.key[c] & 7].push_back(make_int2((int)par, (int)c));
+            }
+            std::vector<int64_t> ops(8);
+            for (int o = 0; o < 8; ++o) ops[o] = P->lev[l].pc_op + (int64_t)o * P->lev[l].P * P->lev[l - 1].P;
+            P->l2l_items_begin[l] = (int64_t)items.size();
+            emit_items(pb, ops, P->lev[l - 1].lofs, P->lev[l].lofs, P->lev[l - 1].P, P->lev[l].P, 0, items, cols);
+            P->l2l_items_end[l] = (int64_t)items.size();
+            P->cost[2] += (double)ch.key.size() * P->lev[l].P * P->lev[l - 1].P;
+        }
+        P->items.upload(items, cnt, st);
+        P->item_cols.upload(cols, cnt, st);
+    }
+
+    // ---------------------------------------------------------- self / near correction (Sec. 2.2)
+    int ls = L;
+    while (ls > 0 && P->lev[ls].side < P->r_near) --ls;
+    const HostLevel& S = lv[ls];
+    DBuf<double> d_x64s, d_w64s, d_V;
+    DBuf<int32_t> d_tri, d_F, d_sstart;
+    DBuf<uint64_t> d_skey;
+    DBuf<int4> d_pt_ijk;
+    d_x64s.upload(x64s, nullptr, st);
+    d_w64s.upload(w64s, nullptr, st);
+    std::vector<double> Vh(V, V + 3 * nv);
+    std::vector<int32_t> Fh(F, F + 3 * nt);
+    d_V.upload(Vh, nullptr, st);
+    d_F.upload(Fh, nullptr, st);
+    d_tri.upload(tri_s, nullptr, st);
+    d_skey.upload(S.key, nullptr, st);
+    d_sstart.upload(S.start, nullptr, st);
+    d_pt_ijk.upload(pt_ijk, nullptr, st);
+    CorrInputs ci{};
+    ci.x64s = d_x64s.p;
+    ci.tri_s = d_tri.p;
+    ci.V = d_V.p;
+    ci.F = d_F.p;
+    ci.iperm = P->iperm.p;
+    ci.w64s = d_w64s.p;
+    ci.skey = d_skey.p;
+    ci.sstart = d_sstart.p;
+    ci.nsbox = (int64_t)S.key.size();
+    ci.search_level = ls;
+    ci.L = L;
+    ci.pt_ijk = d_pt_ijk.p;
+    ci.N = N;
+    ci.k = k;
+    ci.r_near = P->r_near;
+    ci.quad_order = cfg.quad_order;
+    P->corr_nnz = build_correction(P, ci, st);
+    P->cost[3] = (double)P->corr_nnz;
+    HFMM_CUDA(cudaStreamSynchronize(st));
+    if (cfg.mem_budget_bytes > 0 && (double)P->dev_bytes > cfg.mem_budget_bytes)
+        throw HfmmError{HFMM_E_NOMEM, "plan exceeds the configured device memory budget"};
+}
+
+// =================================================================== C ABI
+#define HFMM_GUARD_BEGIN try {
+#define HFMM_GUARD_END                               \
+    }                                                \
+    catch (const HfmmError& e) {                     \
+        g_last_error = e.what;                       \
+        return e.code;                               \
+    }                                                \
+    catch (const std::bad_alloc&) {                  \
+        g_last_error = "host allocation failed";     \
+        return HFMM_E_NOMEM;                         \
+    }                                                \
+    catch (...) {                                    \
+        g_last_error = "unexpected exception";       \
+        return HFMM_E_CUDA;                          \
+    }
+
+extern "C" {
+
+void hfmm_default_config(hfmm_config* c) {
+    if (!c) return;
+    c->leaf_max = 64;
+    c->depth = 0;
+    c->p_fixed = 0;
+    c->p_min = 7;
+    c->near_factor = 1.0;
+    c->quad_order = 10;
+    c->restart = 30;
+    c->max_iter = 1000;
+    c->tol = 1e-4;
+    c->mem_budget_bytes = 0.0;
+}
+
+const char* hfmm_last_error(void) { return g_last_error.c_str(); }
+
+const char* hfmm_status_string(int s) {
+    switch (s) {
+        case HFMM_OK: return "ok";
+        case HFMM_NOT_CONVERGED: return "GMRES did not reach the tolerance within max_iter";
+        case HFMM_E_INVALID: return "invalid argument";
+        case HFMM_E_MESH: return "degenerate or invalid mesh";
+        case HFMM_E_NOMEM: return "out of device memory or over the memory budget";
+        case HFMM_E_CUDA: return "CUDA runtime error";
+        case HFMM_E_TIMEOUT: return "device wait timed out";
+        case HFMM_E_OVERFLOW: return "fixed-capacity table overflowed";
+        default: return "unknown status";
+    }
+}
+
+int hfmm_plan_create(const hfmm_config* cfg, const double* vertices, int64_t n_vert, const int32_t* tris,
+                     int64_t n_tri, double k_re, double k_im, void* stream, hfmm_plan** out) {
+    if (out) *out = nullptr;
+    if (!cfg || !vertices || !tris || !out || n_vert <= 0 || n_tri <= 0) return HFMM_E_INVALID;
+    if (!(k_re > 0.0) || !std::isfinite(k_re) || k_im != 0.0) return HFMM_E_INVALID;
+    if (cfg->leaf_max < 1 || cfg->depth < 0 || cfg->depth > 20 || cfg->p_fixed < 0 || cfg->p_fixed > HFMM_PMAX ||
+        cfg->p_min < 0 || cfg->p_min > HFMM_PMAX || !(cfg->near_factor >= 0.0) || cfg->quad_order < 2 ||
+        cfg->quad_order > 64 || cfg->restart < 1 || cfg->max_iter < 1 || !(cfg->tol > 0.0))
+        return HFMM_E_INVALID;
+    if (3 * n_tri > (int64_t)INT32_MAX / 2) return HFMM_E_INVALID;
+    HFMM_GUARD_BEGIN
+    std::unique_ptr<hfmm_plan> P(new hfmm_plan());
+    P->cfg = *cfg;
+    P->k = k_re;
+    build_plan(P.get(), vertices, n_vert, tris, n_tri, (cudaStream_t)stream);
+    *out = P.release();
+    return HFMM_OK;
+    HFMM_GUARD_END
+}
+
+void hfmm_plan_destroy(hfmm_plan* P) {
+    if (!P) return;
+    cudaDeviceSynchronize();
+    delete P;
+}
+
+int64_t hfmm_num_points(const hfmm_plan* P) { return P ? P->N : -1; }
+
+int hfmm_points(const hfmm_plan* P, double* xyz, double* w, int32_t* tri) {
+    if (!P) return HFMM_E_INVALID;
+    if (xyz) std::memcpy(xyz, P->host_x.data(), sizeof(double) * 3 * P->N);
+    if (w) std::memcpy(w, P->host_w.data(), sizeof(double) * P->N);
+    if (tri) std::memcpy(tri, P->host_t.data(), sizeof(int32_t) * P->N);
+    return HFMM_OK;
+}
+
+int hfmm_plan_info(const hfmm_plan* P, int* depth, int* orders, int64_t* n_leaves, int64_t* corr_nnz,
+                   int64_t* m2l_translations, int64_t* device_bytes) {
+    if (!P) return HFMM_E_INVALID;
+    if (depth) *depth = P->L;
+    if (orders)
+        for (int l = 0; l < 32; ++l) orders[l] = (l <= P->L) ? P->lev[l].p : 0;
+    if (n_leaves) *n_leaves = P->nleaf;
+    if (corr_nnz) *corr_nnz = P->corr_nnz;
+    if (m2l_translations) *m2l_translations = P->m2l_count;
+    if (device_bytes) *device_bytes = (int64_t)P->dev_bytes;
+    return HFMM_OK;
+}
+
+int hfmm_matvec_parts(hfmm_plan* P, const void* density, void* potential, int nrhs, int parts, void* stream) {
+    if (!P || !density || !potential || nrhs < 1 || parts < 0 || parts > 7) return HFMM_E_INVALID;
+    HFMM_GUARD_BEGIN
+    cudaStream_t st = (cudaStream_t)stream;
+    for (int r = 0; r < nrhs; ++r) {
+        const float2* d = (const float2*)density + (int64_t)r * P->N;
+        float2* o = (float2*)potential + (int64_t)r * P->N;
+        launch_density_prep(P, d, false, P->sig.p, st);
+        run_matvec_sorted(P, parts, st);
+        launch_output(P, P->phi.p, o, false, st);
+    }
+    HFMM_CUDA(cudaGetLastError());
+    return HFMM_OK;
+    HFMM_GUARD_END
+}
+
+int hfmm_matvec(hfmm_plan* P, const void* density, void* potential, int nrhs, void* stream) {
+    return hfmm_matvec_parts(P, density, potential, nrhs, 7, stream);
+}
+
+int hfmm_matvec_timed(hfmm_plan* P, const void* density, void* potential, float* stage_ms, void* stream) {
+    if (!P || !density || !potential || !stage_ms) return HFMM_E_INVALID;
+    cudaEvent_t ev[10] = {};
+    HFMM_GUARD_BEGIN
+    cudaStream_t st = (cudaStream_t)stream;
+    struct Cleanup {
+        hfmm_plan* P;
+        cudaEvent_t* ev;
+        ~Cleanup() {
+            P->stage_ev = nullptr;
+            for (int q = 0; q < 10; ++q)
+                if (ev[q]) cudaEventDestroy(ev[q]);
+        }
+    } cleanup{P, ev};
+    for (int q = 0; q < 10; ++q) HFMM_CUDA(cudaEventCreate(&ev[q]));
+    P->stage_ev = ev;
+    mark_stage(P, 0, st);
+    launch_density_prep(P, density, false, P->sig.p, st);
+    run_matvec_sorted(P, 7, st);
+    launch_output(P, P->phi.p, potential, false, st);
+    mark_stage(P, 9, st);
+    HFMM_CUDA(cudaEventSynchronize(ev[9]));
+    for (int q = 0; q < 9; ++q) HFMM_CUDA(cudaEventElapsedTime(&stage_ms[q], ev[q], ev[q + 1]));
+    return HFMM_OK;
+    HFMM_GUARD_END
+}
+
+int64_t hfmm_launch_count(const hfmm_plan* P) { return P ? P->launches : -1; }
+
+int hfmm_plan_costs(const hfmm_plan* P, double* costs) {
+    if (!P || !costs) return HFMM_E_INVALID;
+    for (int q = 0; q < 6; ++q) costs[q] = P->cost[q];
+    return HFMM_OK;
+}
+
+int hfmm_direct(hfmm_plan* P, const void* density, void* potential, int nrhs, void* stream) {
+    if (!P || !density || !potential || nrhs < 1) return HFMM_E_INVALID;
+    HFMM_GUARD_BEGIN
+    cudaStream_t st = (cudaStream_t)stream;
+    for (int r = 0; r < nrhs; ++r) {
+        launch_density_prep(P, (const float2*)density + (int64_t)r * P->N, false, P->sig.p, st);
+        run_direct_sorted(P, st);
+        launch_output(P, P->phi.p, (float2*)potential + (int64_t)r * P->N, false, st);
+    }
+    HFMM_CUDA(cudaGetLastError());
+    return HFMM_OK;
+    HFMM_GUARD_END
+}
+
+int hfmm_rhs_planewave(hfmm_plan* P, const double* dirs, int nrhs, void* rhs_out, void* stream) {
+    if (!P || !dirs || !rhs_out || nrhs < 1) return HFMM_E_INVALID;
+    for (int r = 0; r < nrhs; ++r)
+        for (int d = 0; d < 3; ++d)
+            if (!std::isfinite(dirs[3 * r + d])) return HFMM_E_INVALID;
+    HFMM_GUARD_BEGIN
+    cudaStream_t st = (cudaStream_t)stream;
+    for (int r = 0; r < nrhs; ++r)
+        launch_planewave(P, dirs[3 * r], dirs[3 * r + 1], dirs[3 * r + 2], (float2*)rhs_out + (int64_t)r * P->N, st);
+    HFMM_CUDA(cudaGetLastError());
+    return HFMM_OK;
+    HFMM_GUARD_END
+}
+
+int hfmm_solve(hfmm_plan* P, const void* rhs, void* x_out, int nrhs, int* iters_out, double* relres_out,
+               void* stream) {
+    if (!P || !rhs || !x_out || nrhs < 1) return HFMM_E_INVALID;
+    HFMM_GUARD_BEGIN
+    cudaStream_t st = (cudaStream_t)stream;
+    int status = HFMM_OK;
+    for (int r = 0; r < nrhs; ++r) {
+        int it = 0;
+        double rr = 0.0;
+        int s = run_gmres(P, (const float2*)rhs + (int64_t)r * P->N, (float2*)x_out + (int64_t)r * P->N, &it, &rr, st);
+        if (s != HFMM_OK) status = s;
+        if (iters_out) iters_out[r] = it;
+        if (relres_out) relres_out[r] = rr;
+    }
+    return status;
+    HFMM_GUARD_END
+}
+
+}  // extern "C"
