@@ -59,7 +59,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
         except Exception:
@@ -109,11 +109,11 @@ def cpu_baseline(V, F, k, near_factor, sigma, budget_s=12.0, rows=None):
     r = oracle.near_radius(V, F, near_factor)
     rng = np.random.default_rng(1)
     if rows is None:
-        probe = rng.choice(N, size=16, replace=False)
+        probe = rng.choice(N, size=min(16, N), replace=False)
         t0 = time.perf_counter()
         oracle.direct_rows(V, F, k, r, probe, sigma)
         dt = time.perf_counter() - t0
-        nrow = int(max(16, min(4096, 16 * budget_s / max(dt, 1e-3))))
+        nrow = int(max(16, min(4096, N, 16 * budget_s / max(dt, 1e-3))))
         rows = np.sort(rng.choice(N, size=nrow, replace=False))
     t0 = time.perf_counter()
     vals = oracle.direct_rows(V, F, k, r, rows, sigma)
@@ -159,7 +159,7 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--workload", default="sphere_655360", choices=sorted(WORKLOADS))
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
