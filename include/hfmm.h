@@ -175,6 +175,37 @@ int hfmm_plan_costs(const hfmm_plan* plan, double* costs);
 /* Number of kernels this plan has launched on the device since it was created. */
 int64_t hfmm_launch_count(const hfmm_plan* plan);
 
+/*
+ * Scratch-free point sum (the paper has no counterpart; it is a service for
+ * callers that cannot allocate device memory, e.g. code running inside
+ * another framework's memory pool or arena, or a process whose device
+ * footprint must stay fixed after start-up, where cudaMalloc is forbidden or
+ * unavailable).
+ *
+ *   potential_i = sum_{j != i, R_ij > 0} w_j exp(i k R_ij) / (4 pi R_ij) density_j
+ *
+ * i.e. the point part of the operator, the same result as hfmm_matvec_parts
+ * with parts = 1 on a plan whose single leaf holds every point.  No plan is
+ * needed.  xyz (n x 3 doubles) and w (n doubles) are DEVICE arrays (for
+ * example the output of hfmm_points copied to the device); density and
+ * potential are DEVICE complex64 vectors of length n; the caller owns all of
+ * them.  Stream-ordered, O(n^2) work.
+ *
+ * Working memory is a fixed file-scope device array of HFMM_NOALLOC_MAX_POINTS
+ * entries (32 bytes each, 8 MiB), held by every device that loads the library
+ * until the process exits; the call itself allocates and frees nothing.
+ * n > HFMM_NOALLOC_MAX_POINTS returns HFMM_E_OVERFLOW (see hfmm_last_error).
+ * The first call on a device looks up the array's device address (with that
+ * device current); make that first call before any stream capture.  All calls
+ * on a device share the one array, so calls that overlap on the GPU (on
+ * different streams, or from different threads) race and must be serialised
+ * by the caller.  Each call overwrites the entries it reads; nothing needs
+ * clearing between calls.
+ */
+#define HFMM_NOALLOC_MAX_POINTS 262144
+int hfmm_point_sum_noalloc(const double* xyz, const double* w, int64_t n, double k,
+                           const void* density, void* potential, void* stream);
+
 /* Static description of a status code (never NULL). */
 const char* hfmm_status_string(int status);
 

@@ -29,8 +29,9 @@ EXPORTED = [
     "hfmm_default_config", "hfmm_plan_create", "hfmm_plan_destroy", "hfmm_num_points", "hfmm_points",
     "hfmm_plan_info", "hfmm_matvec", "hfmm_matvec_parts", "hfmm_direct", "hfmm_rhs_planewave",
     "hfmm_solve", "hfmm_status_string", "hfmm_last_error", "hfmm_matvec_timed", "hfmm_launch_count",
-    "hfmm_plan_costs",
+    "hfmm_plan_costs", "hfmm_point_sum_noalloc",
 ]
+HFMM_NOALLOC_MAX_POINTS = 262144
 STAGES = ["prep", "p2p", "p2m", "m2m", "m2l", "l2l", "l2p", "corr", "output"]
 
 
@@ -85,6 +86,7 @@ def lib():
         L.hfmm_status_string.restype = ctypes.c_char_p
         L.hfmm_matvec_timed.argtypes = [vp, vp, vp, ctypes.POINTER(ctypes.c_float), vp]
         L.hfmm_plan_costs.argtypes = [vp, dp]
+        L.hfmm_point_sum_noalloc.argtypes = [vp, vp, i64, ctypes.c_double, vp, vp, vp]
         L.hfmm_launch_count.argtypes = [vp]
         L.hfmm_launch_count.restype = i64
         L.hfmm_last_error.argtypes = []
@@ -221,6 +223,21 @@ def hfmm_plan_costs(plan):
     _check(lib().hfmm_plan_costs(plan, c), "hfmm_plan_costs")
     keys = ["p2p_pairs", "m2l_cmacs", "m2m_l2l_cmacs", "corr_nnz", "n_points", "coefficients"]
     return dict(zip(keys, [float(v) for v in c]))
+
+
+def hfmm_point_sum_noalloc(xyz, w, density, potential, k, stream=None):
+    """Point sum through the scratch-free entry point; xyz [n,3] and w [n] are
+    float64 CUDA tensors, density / potential complex64 CUDA tensors."""
+    import torch
+
+    n = int(w.numel())
+    if not (xyz.is_cuda and w.is_cuda and xyz.dtype == torch.float64 and w.dtype == torch.float64
+            and xyz.is_contiguous() and w.is_contiguous() and xyz.numel() == 3 * n):
+        raise ValueError("xyz / w: expected contiguous float64 CUDA tensors of 3n and n elements")
+    _vec(density, n, 1, "density")
+    _vec(potential, n, 1, "potential")
+    return _check(lib().hfmm_point_sum_noalloc(_ptr(xyz), _ptr(w), n, float(k), _ptr(density), _ptr(potential),
+                                               _stream(stream)), "hfmm_point_sum_noalloc")
 
 
 def hfmm_launch_count(plan):

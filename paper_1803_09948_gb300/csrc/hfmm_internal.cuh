@@ -28,6 +28,9 @@ struct HfmmError {
                             std::string(#call) + ": " + cudaGetErrorString(e_)};     \
     } while (0)
 
+// records the message returned by hfmm_last_error on the calling thread
+void hfmm_set_last_error(const std::string& msg);
+
 // ---------------------------------------------------------------- device buffers
 template <typename T>
 struct DBuf {

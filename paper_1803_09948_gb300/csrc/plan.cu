@@ -20,6 +20,8 @@ using namespace hfmm;
 
 static thread_local std::string g_last_error;
 
+void hfmm_set_last_error(const std::string& msg) { g_last_error = msg; }
+
 static inline uint64_t spread3_h(uint64_t v) {
     v &= 0x1fffff;
     v = (v | v << 32) & 0x1f00000000ffffull;
