@@ -166,6 +166,7 @@ def main():
     ap.add_argument("--p-min", type=int, default=None)
     ap.add_argument("--solves", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--simt", action="store_true", help="M2L on FP32 SIMT cores only (the plain form)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -189,6 +190,8 @@ def main():
     if args.p_min is not None:
         cfg["p_min"] = args.p_min
     cfg["restart"] = restart
+    if args.simt:
+        cfg["m2l_tensor"] = 0
     V, F = synthetic.workload_mesh(mesh)
     N = 3 * F.shape[0]
     stream = torch.cuda.current_stream()
@@ -282,12 +285,20 @@ def main():
 
     # ------------------------------------------------------------ roofline of the dominant stage
     hbm, peak_src, smax = _peaks()
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            bf16_peak = json.load(f).get("bf16_tflops", 1936.2)
+    except Exception:
+        bf16_peak = 1900.0
     props = torch.cuda.get_device_properties(local)
     fp32_peak = props.multi_processor_count * 128 * 2 * smax * 1e6 / 1e12  # TFLOP/s
     dom = max(stages, key=stages.get)
     work = {
         "p2p": ("alu", costs["p2p_pairs"] * 24 / 1e12, "TFLOP/s", fp32_peak, "24 flop per source-target pair"),
-        "m2l": ("alu", costs["m2l_cmacs"] * 8 / 1e12, "TFLOP/s", fp32_peak, "8 flop per complex multiply-add"),
+        "m2l": ("alu", costs["m2l_cmacs"] * 8 / 1e12, "TFLOP/s", fp32_peak, "8 flop per complex multiply-add")
+        if args.simt else
+        ("tensor", costs["m2l_cmacs"] * 8 * 3 / 1e12, "TFLOP/s", bf16_peak,
+         "8 flop per complex multiply-add x 3 BF16 products (hi*hi, hi*lo, lo*hi)"),
         "m2m": ("alu", costs["m2m_l2l_cmacs"] * 4 / 1e12, "TFLOP/s", fp32_peak, "M2M half of the M2M+L2L work"),
         "l2l": ("alu", costs["m2m_l2l_cmacs"] * 4 / 1e12, "TFLOP/s", fp32_peak, "L2L half of the M2M+L2L work"),
         "corr": ("hbm", (costs["corr_nnz"] * 12 + costs["n_points"] * 16) / 1e9, "GB/s", hbm,
@@ -300,7 +311,9 @@ def main():
         rl = {"kernel": dom, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
               "frac": achieved / peak, "traffic": None,
               "peak_source": (f"FP32: {props.multi_processor_count} SMs x 128 lanes x 2 flop x {smax:.0f} MHz"
-                              if bound == "alu" else f"HBM {peak_src} copy bandwidth"),
+                              if bound == "alu" else
+                              (f"dense BF16 cuBLAS burst, {peak_src}" if bound == "tensor"
+                               else f"HBM {peak_src} copy bandwidth")),
               "work_per_launch": note}
 
     # ------------------------------------------------------------ accuracy and CPU baseline (rank 0)
@@ -323,6 +336,7 @@ def main():
             "config": {"workload": f"{args.workload}: {synthetic.WORKLOADS[mesh][0]}", "N": N, "k": k,
                        "leaf_max": plan.cfg.leaf_max, "depth": info["depth"], "orders": info["orders"],
                        "near_factor": plan.cfg.near_factor, "corr_nnz": info["corr_nnz"],
+                       "m2l": "FP32 SIMT" if args.simt else "tcgen05 BF16x3 (levels with (p+1)^2 <= 64), FP32 SIMT above",
                        "m2l_translations": info["m2l_translations"], "device_bytes": info["device_bytes"],
                        "parallelism": "replicas" if world > 1 else "single GPU",
                        "l2": f"inputs larger than L2 (plan holds {info['device_bytes'] / 1e9:.2f} GB)"},

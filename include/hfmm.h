@@ -75,6 +75,8 @@ typedef struct {
     int max_iter;       /* GMRES iteration cap (1000) */
     double tol;         /* GMRES relative residual ||b - Z x|| / ||b|| target (1e-4) */
     double mem_budget_bytes; /* refuse a plan whose device footprint exceeds this (0: no limit) */
+    int m2l_tensor;     /* 1: M2L of levels with (p+1)^2 <= 64 on the tensor cores (BF16 split in
+                           three products, FP32 accumulation); 0: FP32 SIMT everywhere (1) */
 } hfmm_config;
 
 /* Fills *cfg with the defaults shown in parentheses above (p_min = 7). */
@@ -171,6 +173,13 @@ int hfmm_matvec_timed(hfmm_plan* plan, const void* density, void* potential, flo
  * 4 points N, 5 expansion coefficients (all levels, multipoles + locals).
  */
 int hfmm_plan_costs(const hfmm_plan* plan, double* costs);
+
+/*
+ * Reads and clears the plan's device error flag, set by a kernel whose bounded
+ * wait gave up (it then skips its remaining work).  Synchronises `stream`.
+ * Returns HFMM_OK or HFMM_E_TIMEOUT.
+ */
+int hfmm_device_status(hfmm_plan* plan, void* stream);
 
 /* Number of kernels this plan has launched on the device since it was created. */
 int64_t hfmm_launch_count(const hfmm_plan* plan);

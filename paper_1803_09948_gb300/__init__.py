@@ -29,7 +29,7 @@ EXPORTED = [
     "hfmm_default_config", "hfmm_plan_create", "hfmm_plan_destroy", "hfmm_num_points", "hfmm_points",
     "hfmm_plan_info", "hfmm_matvec", "hfmm_matvec_parts", "hfmm_direct", "hfmm_rhs_planewave",
     "hfmm_solve", "hfmm_status_string", "hfmm_last_error", "hfmm_matvec_timed", "hfmm_launch_count",
-    "hfmm_plan_costs", "hfmm_point_sum_noalloc",
+    "hfmm_plan_costs", "hfmm_point_sum_noalloc", "hfmm_device_status",
 ]
 HFMM_NOALLOC_MAX_POINTS = 262144
 STAGES = ["prep", "p2p", "p2m", "m2m", "m2l", "l2l", "l2p", "corr", "output"]
@@ -47,6 +47,7 @@ class hfmm_config(ctypes.Structure):
         ("max_iter", ctypes.c_int),
         ("tol", ctypes.c_double),
         ("mem_budget_bytes", ctypes.c_double),
+        ("m2l_tensor", ctypes.c_int),
     ]
 
 
@@ -86,6 +87,7 @@ def lib():
         L.hfmm_status_string.restype = ctypes.c_char_p
         L.hfmm_matvec_timed.argtypes = [vp, vp, vp, ctypes.POINTER(ctypes.c_float), vp]
         L.hfmm_plan_costs.argtypes = [vp, dp]
+        L.hfmm_device_status.argtypes = [vp, vp]
         L.hfmm_point_sum_noalloc.argtypes = [vp, vp, i64, ctypes.c_double, vp, vp, vp]
         L.hfmm_launch_count.argtypes = [vp]
         L.hfmm_launch_count.restype = i64
@@ -240,6 +242,11 @@ def hfmm_point_sum_noalloc(xyz, w, density, potential, k, stream=None):
                                                _stream(stream)), "hfmm_point_sum_noalloc")
 
 
+def hfmm_device_status(plan, stream=None):
+    """HFMM_OK, or HFMM_E_TIMEOUT if a kernel's bounded wait gave up since the last call."""
+    return int(lib().hfmm_device_status(plan, _stream(stream)))
+
+
 def hfmm_launch_count(plan):
     return int(lib().hfmm_launch_count(plan))
 
@@ -313,6 +320,9 @@ class Plan:
 
     def costs(self):
         return hfmm_plan_costs(self.handle)
+
+    def device_status(self, stream=None):
+        return hfmm_device_status(self.handle, stream)
 
     def launch_count(self):
         return hfmm_launch_count(self.handle)

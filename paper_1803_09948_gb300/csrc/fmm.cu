@@ -386,8 +386,7 @@ __global__ void __launch_bounds__(128) k_translate(const TransItem* __restrict__
                 if (cc >= ncol) continue;
                 float2* o = coef + it.dst + (int64_t)sc[cc].y * Pout + r;
                 if (it.atomic) {
-                    atomicAdd(&o->x, accr[qa][qb]);
-                    atomicAdd(&o->y, acci[qa][qb]);
+                    red_add(o, make_float2(accr[qa][qb], acci[qa][qb]));
                 } else {
                     float2 v = *o;
                     *o = make_float2(v.x + accr[qa][qb], v.y + acci[qa][qb]);
@@ -526,7 +525,14 @@ void run_matvec_sorted(hfmm_plan* P, int parts, cudaStream_t st) {
     if (far)
         for (int l = L - 1; l >= 2; --l) launch_translate(P, P->m2m_items_begin[l], P->m2m_items_end[l], st);
     mark_stage(P, 4, st);
-    if (far) launch_translate(P, P->m2l_items_begin, P->m2l_items_end, st);
+    if (far) {
+        for (const auto& r : P->m2l_simt_ranges) launch_translate(P, r.first, r.second, st);
+        if (P->n_tc_groups > 0) {
+            m2l_tc_launch(P->tc_groups.p, P->n_tc_groups, P->items.p, P->item_cols.p, P->aops.p, P->coef.p,
+                          P->dev_err.p, st);
+            ++P->launches;
+        }
+    }
     mark_stage(P, 5, st);
     if (far)
         for (int l = 3; l <= L; ++l) launch_translate(P, P->l2l_items_begin[l], P->l2l_items_end[l], st);

@@ -124,6 +124,11 @@ struct hfmm_plan {
     std::vector<int64_t> m2m_items_begin, m2m_items_end;  // per level l (parents at l)
     std::vector<int64_t> l2l_items_begin, l2l_items_end;  // per level l (children at l)
     int64_t m2l_items_begin = 0, m2l_items_end = 0;
+    std::vector<std::pair<int64_t, int64_t>> m2l_simt_ranges;  // M2L item ranges on the SIMT kernel
+    DBuf<uint16_t> aops;       // tensor-core M2L operators (BF16 hi/lo, packed)
+    DBuf<int4> tc_groups;      // (first item, item count, operator, P) per tensor-core block
+    int64_t n_tc_groups = 0;
+    DBuf<int> dev_err;         // set by kernels whose bounded waits gave up
     // correction
     DBuf<int64_t> corr_ptr;
     DBuf<int32_t> corr_col;
@@ -142,6 +147,11 @@ struct hfmm_plan {
 
 // ---------------------------------------------------------------- kernels: FMM matvec
 namespace hfmm {
+
+// *p += v without returning the old value (a reduction, not an atomic exchange)
+__device__ __forceinline__ void red_add(float2* p, float2 v) {
+    asm volatile("red.global.add.v2.f32 [%0], {%1, %2};" ::"l"(p), "f"(v.x), "f"(v.y) : "memory");
+}
 
 // sig_sorted = k w / (4 pi) * density[perm]  (one right-hand side)
 void launch_density_prep(hfmm_plan* P, const void* density, bool fp64, float2* sig, cudaStream_t st);
@@ -187,6 +197,13 @@ struct CorrInputs {
 };
 // Returns nnz; fills P->corr_ptr / corr_col / corr_val.
 int64_t build_correction(hfmm_plan* P, const CorrInputs& in, cudaStream_t st);
+
+// ---------------------------------------------------------------- tensor-core M2L
+size_t m2l_tc_op_elems();  // BF16 elements per packed operator (hi + lo)
+int m2l_tc_max_group();    // work items per tensor-core block
+void m2l_tc_pack(const float2* T, int P, int nops, uint16_t* out, cudaStream_t st);
+void m2l_tc_launch(const int4* groups, int64_t ngroups, const TransItem* items, const int2* cols,
+                   const uint16_t* aops, float2* coef, int* err, cudaStream_t st);
 
 // ---------------------------------------------------------------- GMRES
 int run_gmres(hfmm_plan* P, const void* rhs, void* x, int* iters, double* relres, cudaStream_t st);

@@ -1,0 +1,448 @@
+// M2L on the fifth-generation tensor cores (tcgen05, TMEM accumulators), BF16x3.
+//
+// One work item applies the translation matrix T of one offset (Sec. 2.3's M2L,
+// Eq. 11-14 read as the local/multipole addition theorem) to up to 64 gathered
+// multipole columns X and accumulates into the targets' local expansions:
+//     L[:, dst_c] += T X[:, src_c].
+// In real arithmetic with interleaved rows
+//     A = rows 2i: [Re T_i, Im T_i],  rows 2i+1: [Im T_i, -Re T_i]   (128 x 2P)
+//     B = [Re X ; -Im X]                                           (2P x 64)
+//     D = A B:  row 2i = Re (T X)_i,  row 2i+1 = Im (T X)_i.
+// A and B are split into BF16 high and low parts (x = hi + lo, 16 significant
+// bits), and D = A_hi B_hi + A_hi B_lo + A_lo B_hi is accumulated in FP32 in
+// tensor memory: tcgen05.mma kind::f16, M = 128, N = 64, K = 16 per
+// instruction, operands in shared memory in the K-major no-swizzle
+// (core-matrix) layout.  A is split once at plan time; B is gathered from the
+// multipole array and split on the fly.  A block keeps one T in shared memory
+// for a group of work items of the same offset.
+#include <cuda_bf16.h>
+
+#include "hfmm_internal.cuh"
+
+namespace hfmm {
+
+namespace {
+
+constexpr int kM = 128;        // rows of A (2P <= 128)
+constexpr int kK = 128;        // K (2P rounded up; P <= 64)
+constexpr int kN = 64;         // columns per work item
+constexpr int kKc = kK / 8;    // core matrices along K
+constexpr uint32_t kCoreBytes = 128;                 // 8 rows x 16 bytes
+constexpr uint32_t kSBO = kKc * kCoreBytes;          // next 8-row group
+constexpr uint32_t kLBO = kCoreBytes;                // next 8-element K group
+constexpr uint32_t kABytes = kM * kK * 2;            // 32 KiB per BF16 part
+constexpr uint32_t kBBytes = kN * kK * 2;            // 16 KiB per BF16 part
+constexpr uint32_t kTmemCols = 64;
+constexpr long long kWaitLimit = 1ll << 26;          // try_wait polls before giving up
+
+// element (r, k) of a K-major core-matrix tile with kKc core matrices per 8-row group
+__host__ __device__ constexpr uint32_t core_index(uint32_t r, uint32_t k) {
+    return ((r >> 3) * kKc + (k >> 3)) * 64 + (r & 7) * 8 + (k & 7);
+}
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ uint64_t umma_desc(uint32_t addr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((addr >> 4) & 0x3FFF);
+    d |= (uint64_t)((kLBO >> 4) & 0x3FFF) << 16;
+    d |= (uint64_t)((kSBO >> 4) & 0x3FFF) << 32;
+    d |= (uint64_t)1 << 46;  // descriptor version for this architecture; no swizzle, base offset 0
+    return d;
+}
+
+// kind::f16 instruction descriptor: D f32, A/B bf16, both K-major, N = 64, M = 128
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kN >> 3) << 17) |
+                            ((uint32_t)(kM >> 4) << 24);
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n"
+        :
+        : "r"(tmem_d), "l"(a), "l"(b), "r"(kIdesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t addr, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(addr), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int q = 0; q < 16; ++q) v[q] = __uint_as_float(r[q]);
+}
+
+// 64 consecutive columns of this thread's lane: four loads in flight, one wait
+__device__ __forceinline__ void tmem_ld64(uint32_t taddr, float (&v)[64]) {
+    uint32_t r[64];
+#pragma unroll
+    for (int b = 0; b < 4; ++b)
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+            "%14, %15}, [%16];"
+            : "=r"(r[16 * b + 0]), "=r"(r[16 * b + 1]), "=r"(r[16 * b + 2]), "=r"(r[16 * b + 3]),
+              "=r"(r[16 * b + 4]), "=r"(r[16 * b + 5]), "=r"(r[16 * b + 6]), "=r"(r[16 * b + 7]),
+              "=r"(r[16 * b + 8]), "=r"(r[16 * b + 9]), "=r"(r[16 * b + 10]), "=r"(r[16 * b + 11]),
+              "=r"(r[16 * b + 12]), "=r"(r[16 * b + 13]), "=r"(r[16 * b + 14]), "=r"(r[16 * b + 15])
+            : "r"(taddr + (uint32_t)(16 * b)));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int q = 0; q < 64; ++q) v[q] = __uint_as_float(r[q]);
+}
+
+__device__ __forceinline__ void split_bf16(float x, __nv_bfloat16& hi, __nv_bfloat16& lo) {
+    hi = __float2bfloat16_rn(x);
+    lo = __float2bfloat16_rn(x - __bfloat162float(hi));
+}
+
+// Operator conversion (plan time): FP32 complex T [P][P] -> A_hi, A_lo (core-matrix layout).
+__global__ void k_m2l_tc_pack(const float2* __restrict__ T, int P, int nops, __nv_bfloat16* __restrict__ out) {
+    int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)nops * kM * kK) return;
+    int op = (int)(idx / (kM * kK));
+    int rk = (int)(idx % (kM * kK));
+    int r = rk / kK, k = rk % kK;
+    int i = r >> 1;
+    bool odd = r & 1;
+    float v = 0.f;
+    if (i < P) {
+        const float2* row = T + (int64_t)op * P * P + (int64_t)i * P;
+        if (k < P) v = odd ? row[k].y : row[k].x;
+        else if (k < 2 * P) v = odd ? -row[k - P].x : row[k - P].y;
+    }
+    __nv_bfloat16 hi, lo;
+    split_bf16(v, hi, lo);
+    __nv_bfloat16* o = out + (int64_t)op * 2 * kM * kK;
+    o[core_index(r, k)] = hi;
+    o[kM * kK + core_index(r, k)] = lo;
+}
+
+constexpr int kStages = 2;         // B stages and TMEM accumulators in flight
+constexpr int kMaxGroup = 32;      // work items per block (one operator)
+constexpr int kProducers = 256;    // threads gathering B (warps 4..11)
+constexpr int kEpilogue = 128;     // threads draining TMEM (warps 0..3, one per TMEM lane quarter)
+constexpr int kMmaWarp = (kEpilogue + kProducers) / 32;  // TMEM owner and MMA issuer
+constexpr int kThreads = kEpilogue + kProducers + 32;
+
+struct TcSmem {
+    __nv_bfloat16 a[2][kM * kK];            // operator T of the group: hi, lo
+    __nv_bfloat16 b[kStages][2][kN * kK];   // gathered multipoles: hi, lo per stage
+    uint64_t full[kStages];                 // producers -> MMA: stage written
+    uint64_t empty[kStages];                // MMA done reading the stage
+    uint64_t tfull[kStages];                // accumulator ready
+    uint64_t tempty[kStages];               // epilogue done reading the accumulator
+    float stage[kStages][kN][kM];           // accumulator columns = target expansions (Re/Im interleaved)
+    TransItem items[kMaxGroup];             // the group's work items
+    int2 cols[kMaxGroup][kN];               // their (source, destination) columns
+    uint32_t tmem;
+    int abort;
+};
+
+__device__ __forceinline__ void mbar_arrive(uint32_t addr) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(addr) : "memory");
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t addr, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(addr), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void tc_commit(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+                 : "memory");
+}
+
+// Bounded wait that also gives up when another role has aborted; on a timeout
+// it raises the block's abort flag and the device error flag.
+__device__ __forceinline__ bool wait_or_abort(uint32_t bar, uint32_t parity, volatile int* abort, int* err) {
+    for (long long it = 0; it < kWaitLimit; ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((it & 255) == 255 && *abort) return false;
+    }
+    *abort = 1;
+    atomicExch(err, 1);
+    return false;
+}
+
+// AND of v over the 128 epilogue threads (named barrier 1); every epilogue thread
+// takes the same branch afterwards, so no later barrier can be left waiting.
+__device__ __forceinline__ bool epilogue_all(bool v) {
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.u32 q, %1, 0;\n\t"
+        "bar.red.and.pred p, 1, 128, q;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(r)
+        : "r"((uint32_t)v)
+        : "memory");
+    return r != 0;
+}
+
+__global__ void __launch_bounds__(kThreads, 1)
+    k_m2l_tc(const int4* __restrict__ groups, const TransItem* __restrict__ items, const int2* __restrict__ cols,
+             const __nv_bfloat16* __restrict__ aops, float2* __restrict__ coef, int* __restrict__ err) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    TcSmem& S = *reinterpret_cast<TcSmem*>(smem_raw);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int4 g = groups[blockIdx.x];  // (first item, item count, operator index, P)
+    const int P = g.w, nitems = g.y;
+    volatile int* abort = &S.abort;
+
+    if (warp == kMmaWarp) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&S.tmem)),
+                     "r"(kStages * kTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        for (int q = 0; q < kStages; ++q) {
+            mbar_init(smem_u32(&S.full[q]), kProducers);
+            mbar_init(smem_u32(&S.empty[q]), 1);
+            mbar_init(smem_u32(&S.tfull[q]), 1);
+            mbar_init(smem_u32(&S.tempty[q]), kEpilogue);
+        }
+        S.abort = 0;
+    }
+    {
+        // the group's work items and column lists: one coalesced pass instead of a
+        // dependent load per item later
+        for (int q = tid; q < nitems; q += kThreads) S.items[q] = items[g.x + q];
+        __syncthreads();
+        for (int q = tid; q < nitems * kN; q += kThreads) {
+            const int w = q / kN, c = q % kN;
+            S.cols[w][c] = c < S.items[w].ncol ? cols[S.items[w].cols + c] : make_int2(0, 0);
+        }
+        // the group's operator (hi and lo), a straight copy of the packed layout
+        const uint4* src = reinterpret_cast<const uint4*>(aops + (int64_t)g.z * 2 * kM * kK);
+        uint4* dst = reinterpret_cast<uint4*>(&S.a[0][0]);
+        for (int q = tid; q < (int)(2 * kABytes / 16); q += kThreads) dst[q] = __ldg(src + q);
+        // K beyond 2P stays zero in B (A is zero there too), so no stale NaN enters a product
+        uint4* bz = reinterpret_cast<uint4*>(&S.b[0][0][0]);
+        for (int q = tid; q < (int)(kStages * 2 * kBBytes / 16); q += kThreads) bz[q] = make_uint4(0, 0, 0, 0);
+    }
+    fence_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = S.tmem;
+
+    if (warp >= 4 && warp < kMmaWarp) {
+        // ---------------------------------------------------------------- producers
+        const int pt = tid - kEpilogue;
+        const int nchunk = (P + 7) >> 3;
+        for (int w = 0; w < nitems; ++w) {
+            const int s = w & 1;
+            const uint32_t ph = (uint32_t)(w >> 1) & 1u;
+            if (!wait_or_abort(smem_u32(&S.empty[s]), ph ^ 1u, abort, err)) break;
+            const TransItem& it = S.items[w];
+            const int ncol = it.ncol;
+            __nv_bfloat16* bh = &S.b[s][0][0];
+            __nv_bfloat16* bl = &S.b[s][1][0];
+            if ((P & 7) == 0 && nchunk * kN == 2 * kProducers) {
+                // P = 64: two (column, chunk) tasks per thread, lanes on consecutive columns;
+                // all loads in flight before any use, split with packed BF16 pairs
+                const int c = pt & (kN - 1);
+                const bool valid = c < ncol;
+                const int cidx = valid ? S.cols[w][c].x : 0;
+                float4 v[2][4];
+#pragma unroll
+                for (int q = 0; q < 2; ++q) {
+                    const int j = (pt >> 6) + 4 * q;
+                    const float4* x4 = reinterpret_cast<const float4*>(coef + it.src + (int64_t)cidx * P + 8 * j);
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) v[q][e] = valid ? __ldg(x4 + e) : make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+                if (valid) {
+#pragma unroll
+                    for (int q = 0; q < 2; ++q) {
+                        const int j = (pt >> 6) + 4 * q;
+                        uint4 rh, rl, ih, il;
+                        uint32_t* prh = &rh.x;
+                        uint32_t* prl = &rl.x;
+                        uint32_t* pih = &ih.x;
+                        uint32_t* pil = &il.x;
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            const __nv_bfloat162 hr = __floats2bfloat162_rn(v[q][e].x, v[q][e].z);
+                            const __nv_bfloat162 hi = __floats2bfloat162_rn(-v[q][e].y, -v[q][e].w);
+                            const float2 br = __bfloat1622float2(hr), bi = __bfloat1622float2(hi);
+                            const __nv_bfloat162 lr = __floats2bfloat162_rn(v[q][e].x - br.x, v[q][e].z - br.y);
+                            const __nv_bfloat162 li = __floats2bfloat162_rn(-v[q][e].y - bi.x, -v[q][e].w - bi.y);
+                            prh[e] = *reinterpret_cast<const uint32_t*>(&hr);
+                            prl[e] = *reinterpret_cast<const uint32_t*>(&lr);
+                            pih[e] = *reinterpret_cast<const uint32_t*>(&hi);
+                            pil[e] = *reinterpret_cast<const uint32_t*>(&li);
+                        }
+                        const uint32_t o_re = core_index(c, 8 * j), o_im = core_index(c, P + 8 * j);
+                        *reinterpret_cast<uint4*>(bh + o_re) = rh;
+                        *reinterpret_cast<uint4*>(bl + o_re) = rl;
+                        *reinterpret_cast<uint4*>(bh + o_im) = ih;
+                        *reinterpret_cast<uint4*>(bl + o_im) = il;
+                    }
+                }
+            } else {
+                for (int task = pt; task < kN * nchunk; task += kProducers) {
+                    const int c = task / nchunk, j = task % nchunk;
+                    if (c >= ncol) continue;
+                    const float2* x = coef + it.src + (int64_t)S.cols[w][c].x * P + 8 * j;
+                    __align__(16) __nv_bfloat16 rh[8], rl[8], ih[8], il[8];
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) {
+                        const float2 v = (8 * j + q < P) ? __ldg(x + q) : make_float2(0.f, 0.f);
+                        split_bf16(v.x, rh[q], rl[q]);
+                        split_bf16(-v.y, ih[q], il[q]);
+                    }
+#pragma unroll
+                    for (int q = 0; q < 8; ++q)
+                        if (8 * j + q < P) {
+                            bh[core_index(c, 8 * j + q)] = rh[q];
+                            bl[core_index(c, 8 * j + q)] = rl[q];
+                            bh[core_index(c, P + 8 * j + q)] = ih[q];
+                            bl[core_index(c, P + 8 * j + q)] = il[q];
+                        }
+                }
+            }
+            fence_async_smem();  // this thread's stores -> visible to the tensor core
+            mbar_arrive(smem_u32(&S.full[s]));
+        }
+    } else if (warp == kMmaWarp) {
+        // ---------------------------------------------------------------- MMA issuer
+        int issued = -1;
+        if (lane == 0) {
+            const uint32_t a_hi = smem_u32(&S.a[0][0]), a_lo = smem_u32(&S.a[1][0]);
+            for (int w = 0; w < nitems; ++w) {
+                const int s = w & 1;
+                const uint32_t ph = (uint32_t)(w >> 1) & 1u;
+                if (!wait_or_abort(smem_u32(&S.full[s]), ph, abort, err)) break;
+                if (!wait_or_abort(smem_u32(&S.tempty[s]), ph ^ 1u, abort, err)) break;
+                tc_fence_after();
+                const uint32_t b_hi = smem_u32(&S.b[s][0][0]), b_lo = smem_u32(&S.b[s][1][0]);
+                const uint32_t d = tmem + (uint32_t)(s * kTmemCols);
+#pragma unroll 1
+                for (int k = 0; k < kK / 16; ++k) {
+                    const uint32_t ko = (uint32_t)k * 2 * kLBO;
+                    mma_bf16(d, umma_desc(a_hi + ko), umma_desc(b_hi + ko), k > 0);
+                    mma_bf16(d, umma_desc(a_hi + ko), umma_desc(b_lo + ko), 1);
+                    mma_bf16(d, umma_desc(a_lo + ko), umma_desc(b_hi + ko), 1);
+                }
+                tc_commit(smem_u32(&S.empty[s]));
+                tc_commit(smem_u32(&S.tfull[s]));
+                issued = w;
+            }
+            if (*abort && issued >= 0) {
+                // drain this thread's MMAs before the tensor memory is released (bounded)
+                const int s = issued & 1;
+                const uint32_t ph = (uint32_t)(issued >> 1) & 1u;
+                for (long long it = 0; it < kWaitLimit; ++it)
+                    if (mbar_try_wait(smem_u32(&S.tfull[s]), ph)) break;
+            }
+        }
+        __syncwarp();
+    } else {
+        // ---------------------------------------------------------------- epilogue (warps 0..3)
+        const int r = tid;  // TMEM lane = row of D
+        const int i = r >> 1;
+        const bool odd = r & 1;
+        for (int w = 0; w < nitems; ++w) {
+            const int s = w & 1;
+            const uint32_t ph = (uint32_t)(w >> 1) & 1u;
+            const bool ok = wait_or_abort(smem_u32(&S.tfull[s]), ph, abort, err);
+            if (!epilogue_all(ok)) break;
+            tc_fence_after();
+            const TransItem& it = S.items[w];
+            const int ncol = it.ncol;
+            const uint32_t base = tmem + (uint32_t)(s * kTmemCols) + ((uint32_t)(warp * 32) << 16);
+            float v[kN];
+            tmem_ld64(base, v);
+            if ((P & 1) == 0) {
+                // Column c of D, rows 0..2P-1, is the 8P-byte image of the target expansion
+                // L[dst_c] (Re, Im interleaved): stage it and let the bulk-copy engine add it.
+                if (r < kN) asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");  // stage[s] free
+                asm volatile("bar.sync 2, 128;" ::: "memory");
+#pragma unroll
+                for (int c = 0; c < kN; ++c) S.stage[s][c][r] = v[c];
+                fence_async_smem();
+                tc_fence_before();
+                mbar_arrive(smem_u32(&S.tempty[s]));  // accumulator drained
+                asm volatile("bar.sync 2, 128;" ::: "memory");
+                if (r < ncol) {
+                    float2* dst = coef + it.dst + (int64_t)S.cols[w][r].y * P;
+                    asm volatile("cp.reduce.async.bulk.global.shared::cta.bulk_group.add.f32 [%0], [%1], %2;" ::"l"(dst),
+                                 "r"(smem_u32(&S.stage[s][r][0])), "r"(8 * P)
+                                 : "memory");
+                }
+                if (r < kN) asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+                continue;
+            }
+            // odd P: per-lane reductions.  Column pairs (c, c+1): the even lane (Re row) sends
+            // its c+1 value and takes column c, the odd lane (Im row) the reverse; every lane
+            // issues one reduction, no divergent branch
+            const bool row_ok = i < P;
+#pragma unroll
+            for (int c = 0; c < kN; c += 2) {
+                const float send = odd ? v[c] : v[c + 1];
+                const float recv = __shfl_xor_sync(0xffffffffu, send, 1);
+                const int col = c + (odd ? 1 : 0);
+                const float re = odd ? recv : v[c];
+                const float imv = odd ? v[c + 1] : recv;
+                if (row_ok && col < ncol) red_add(coef + it.dst + (int64_t)S.cols[w][col].y * P + i, make_float2(re, imv));
+            }
+            tc_fence_before();
+            mbar_arrive(smem_u32(&S.tempty[s]));
+        }
+        if (r < kN) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");  // bulk reductions landed
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == kMmaWarp)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kStages * kTmemCols)
+                     : "memory");
+}
+
+}  // namespace
+
+size_t m2l_tc_op_elems() { return (size_t)2 * kM * kK; }
+int m2l_tc_max_group() { return kMaxGroup; }
+
+void m2l_tc_pack(const float2* T, int P, int nops, uint16_t* out, cudaStream_t st) {
+    int64_t n = (int64_t)nops * kM * kK;
+    k_m2l_tc_pack<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(T, P, nops, reinterpret_cast<__nv_bfloat16*>(out));
+    HFMM_CUDA(cudaGetLastError());
+}
+
+void m2l_tc_launch(const int4* groups, int64_t ngroups, const TransItem* items, const int2* cols,
+                   const uint16_t* aops, float2* coef, int* err, cudaStream_t st) {
+    if (ngroups <= 0) return;
+    size_t smem = sizeof(TcSmem);
+    HFMM_CUDA(cudaFuncSetAttribute(k_m2l_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_m2l_tc<<<(unsigned)ngroups, kThreads, smem, st>>>(groups, items, cols,
+                                                   reinterpret_cast<const __nv_bfloat16*>(aops), coef, err);
+    HFMM_CUDA(cudaGetLastError());
+}
+
+}  // namespace hfmm

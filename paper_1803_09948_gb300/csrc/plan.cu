@@ -292,6 +292,8 @@ static void build_plan(hfmm_plan* P, const double* V, int64_t nv, const int32_t*
     P->tiles.upload(tiles, cnt, st);
     P->sig.alloc(N, cnt);
     P->phi.alloc(N, cnt);
+    P->dev_err.alloc(1, cnt);
+    HFMM_CUDA(cudaMemsetAsync(P->dev_err.p, 0, sizeof(int), st));
     P->host_x = X;
     P->host_w = W;
     P->host_t = T;
@@ -305,12 +307,12 @@ static void build_plan(hfmm_plan* P, const double* V, int64_t nv, const int32_t*
         int64_t off = 0;
         for (int l = 2; l <= L; ++l) {
             P->lev[l].mofs = off;
-            off += P->lev[l].nbox * P->lev[l].P;
+            off += (P->lev[l].nbox * P->lev[l].P + 15) & ~15ll;  // 128-byte aligned level blocks
         }
         P->coef_m_total = off;
         for (int l = 2; l <= L; ++l) {
             P->lev[l].lofs = off;
-            off += P->lev[l].nbox * P->lev[l].P;
+            off += (P->lev[l].nbox * P->lev[l].P + 15) & ~15ll;
         }
         P->coef_total = off;
         P->cost[5] = (double)off;
@@ -406,7 +408,9 @@ static void build_plan(hfmm_plan* P, const double* V, int64_t nv, const int32_t*
         }
         P->m2l_items_begin = (int64_t)items.size();
         int64_t m2l_count = 0;
+        std::vector<int64_t> lev_item_b(L + 1, 0), lev_item_e(L + 1, 0);
         for (int l = 2; l <= L; ++l) {
+            lev_item_b[l] = (int64_t)items.size();
             PairBuckets pb(316);
             const HostLevel& H = lv[l];
             int64_t nlv = (int64_t)1 << l;
@@ -435,8 +439,45 @@ static void build_plan(hfmm_plan* P, const double* V, int64_t nv, const int32_t*
             std::vector<int64_t> ops(316);
             for (int o = 0; o < 316; ++o) ops[o] = P->lev[l].m2l_op + (int64_t)o * P->lev[l].P * P->lev[l].P;
             emit_items(pb, ops, P->lev[l].mofs, P->lev[l].lofs, P->lev[l].P, P->lev[l].P, 1, items, cols);
+            lev_item_e[l] = (int64_t)items.size();
         }
         P->m2l_items_end = (int64_t)items.size();
+        // tensor-core M2L for levels with (p+1)^2 <= 64: pack operators, group items by operator
+        std::vector<int4> groups;
+        int64_t tc_ops = 0;
+        std::vector<int64_t> tc_base(L + 1, -1);
+        for (int l = 2; l <= L; ++l)
+            if (cfg.m2l_tensor && P->lev[l].P <= 64) {
+                tc_base[l] = tc_ops;
+                tc_ops += 316;
+            }
+        if (tc_ops > 0) {
+            P->aops.alloc((size_t)tc_ops * m2l_tc_op_elems(), cnt);
+            for (int l = 2; l <= L; ++l)
+                if (tc_base[l] >= 0)
+                    m2l_tc_pack(P->ops.p + P->lev[l].m2l_op, P->lev[l].P, 316,
+                                P->aops.p + (size_t)tc_base[l] * m2l_tc_op_elems(), st);
+        }
+        const int kGroupItems = m2l_tc_max_group();
+        for (int l = 2; l <= L; ++l) {
+            if (tc_base[l] < 0) {
+                if (!P->m2l_simt_ranges.empty() && P->m2l_simt_ranges.back().second == lev_item_b[l])
+                    P->m2l_simt_ranges.back().second = lev_item_e[l];
+                else
+                    P->m2l_simt_ranges.push_back({lev_item_b[l], lev_item_e[l]});
+                continue;
+            }
+            int64_t PP = (int64_t)P->lev[l].P * P->lev[l].P;
+            for (int64_t b = lev_item_b[l]; b < lev_item_e[l];) {
+                int64_t e = b;
+                while (e < lev_item_e[l] && e - b < kGroupItems && items[e].op == items[b].op) ++e;
+                int slot = (int)((items[b].op - P->lev[l].m2l_op) / PP);
+                groups.push_back(make_int4((int)b, (int)(e - b), (int)(tc_base[l] + slot), P->lev[l].P));
+                b = e;
+            }
+        }
+        P->n_tc_groups = (int64_t)groups.size();
+        P->tc_groups.upload(groups, cnt, st);
         P->m2l_count = m2l_count;
         for (int l = 3; l <= L; ++l) {  // L2L: parents at l-1 -> children at l
             PairBuckets pb(8);
@@ -529,6 +570,7 @@ void hfmm_default_config(hfmm_config* c) {
     c->max_iter = 1000;
     c->tol = 1e-4;
     c->mem_budget_bytes = 0.0;
+    c->m2l_tensor = 1;
 }
 
 const char* hfmm_last_error(void) { return g_last_error.c_str(); }
@@ -554,7 +596,8 @@ int hfmm_plan_create(const hfmm_config* cfg, const double* vertices, int64_t n_v
     if (!(k_re > 0.0) || !std::isfinite(k_re) || k_im != 0.0) return HFMM_E_INVALID;
     if (cfg->leaf_max < 1 || cfg->depth < 0 || cfg->depth > 20 || cfg->p_fixed < 0 || cfg->p_fixed > HFMM_PMAX ||
         cfg->p_min < 0 || cfg->p_min > HFMM_PMAX || !(cfg->near_factor >= 0.0) || cfg->quad_order < 2 ||
-        cfg->quad_order > 64 || cfg->restart < 1 || cfg->max_iter < 1 || !(cfg->tol > 0.0))
+        cfg->quad_order > 64 || cfg->restart < 1 || cfg->max_iter < 1 || !(cfg->tol > 0.0) ||
+        (cfg->m2l_tensor != 0 && cfg->m2l_tensor != 1))
         return HFMM_E_INVALID;
     if (3 * n_tri > (int64_t)INT32_MAX / 2) return HFMM_E_INVALID;
     HFMM_GUARD_BEGIN
@@ -644,6 +687,22 @@ int hfmm_matvec_timed(hfmm_plan* P, const void* density, void* potential, float*
 }
 
 int64_t hfmm_launch_count(const hfmm_plan* P) { return P ? P->launches : -1; }
+
+int hfmm_device_status(hfmm_plan* P, void* stream) {
+    if (!P) return HFMM_E_INVALID;
+    HFMM_GUARD_BEGIN
+    cudaStream_t st = (cudaStream_t)stream;
+    int flag = 0;
+    HFMM_CUDA(cudaMemcpyAsync(&flag, P->dev_err.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+    HFMM_CUDA(cudaMemsetAsync(P->dev_err.p, 0, sizeof(int), st));
+    HFMM_CUDA(cudaStreamSynchronize(st));
+    if (flag) {
+        g_last_error = "a device wait gave up (tensor-core M2L)";
+        return HFMM_E_TIMEOUT;
+    }
+    return HFMM_OK;
+    HFMM_GUARD_END
+}
 
 int hfmm_plan_costs(const hfmm_plan* P, double* costs) {
     if (!P || !costs) return HFMM_E_INVALID;

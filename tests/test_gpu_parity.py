@@ -220,3 +220,26 @@ def test_zero_rhs_gives_zero_solution(c1):
     x = _dev(np.ones(c1["plan"].n))
     st, its, rr = c1["plan"].solve(b, x)
     assert st == pkg.HFMM_OK and its[0] == 0 and np.all(_host(x) == 0)
+
+
+@pytest.mark.parametrize("p", [3, 5, 7])
+def test_tensor_core_m2l_against_simt_and_oracle(c1, p):
+    """BF16x3 tcgen05 M2L ((p+1)^2 <= 64) against the FP32 SIMT form of the same
+    plan and against the oracle's direct sum; p = 5 has (p+1)^2 = 36, not a
+    multiple of 8 (element-wise operand staging)."""
+    tc = pkg.Plan(c1["V"], c1["F"], 1.0, p_fixed=p, m2l_tensor=1)
+    simt = pkg.Plan(c1["V"], c1["F"], 1.0, p_fixed=p, m2l_tensor=0)
+    try:
+        far_tc = _apply(tc, c1["s"], parts=2)
+        far_simt = _apply(simt, c1["s"], parts=2)
+        assert tc.device_status() == pkg.HFMM_OK
+        # BF16 split in three products: ~1e-5 relative to the far field
+        assert np.linalg.norm(far_tc - far_simt) < 3e-5 * np.linalg.norm(far_simt)
+        e_tc = rel(_apply(tc, c1["s"]), c1["ref"])
+        e_simt = rel(_apply(simt, c1["s"]), c1["ref"])
+        assert e_tc < e_simt + 2e-6
+        if p == 7:
+            assert e_tc < 1e-4
+    finally:
+        tc.close()
+        simt.close()
