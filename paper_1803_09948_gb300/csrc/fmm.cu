@@ -63,8 +63,8 @@ __device__ __forceinline__ float horner(const float (&c)[D + 1], float u) {
     return a;
 }
 
-// Accumulates the interactions of one target with the points [j0, j1) of one
-// source leaf.  (tx,ty,tz): target relative to the source leaf centre, scaled by k.
+// Accumulates the interactions of one target with the points j0, j0+stride, ... < j1
+// of one source leaf.  (tx,ty,tz): target relative to the source leaf centre, scaled by k.
 template <bool POLY, bool MASK>
 __device__ __forceinline__ void p2p_leaf(float tx, float ty, float tz, int32_t j0, int32_t j1, int32_t self_i,
                                          const float4* __restrict__ pts, const float2* __restrict__ sig,
@@ -72,7 +72,7 @@ __device__ __forceinline__ void p2p_leaf(float tx, float ty, float tz, int32_t j
     constexpr float kC[HFMM_POLY_C_DEG + 1] = HFMM_POLY_C_INIT;
     constexpr float kS[HFMM_POLY_S_DEG + 1] = HFMM_POLY_S_INIT;
 #pragma unroll 4
-    for (int32_t j = j0; j < j1; ++j) {
+    for (int32_t j = j0; j < j1; j += kP2PSub) {
         float4 sp = __ldg(pts + j);
         float2 sg = __ldg(sig + j);
         if (MASK && j == self_i) sg = make_float2(0.f, 0.f);
@@ -94,10 +94,12 @@ __device__ __forceinline__ void p2p_leaf(float tx, float ty, float tz, int32_t j
     }
 }
 
-// One warp per target tile (<= 32 points of one leaf); lanes own targets,
-// sources are read with warp-uniform (broadcast) loads.
+// One warp per tile of up to kP2PTile targets of one leaf; each target is
+// shared by kP2PSub lanes that take every kP2PSub-th source, and the partial
+// sums meet in two shuffles.  Source loads are broadcast within each group of
+// lanes that read the same point.
 template <bool POLY>
-__global__ void __launch_bounds__(128) k_p2p(int64_t ntiles, const int4* __restrict__ tiles,
+__global__ void __launch_bounds__(256) k_p2p(int64_t ntiles, const int4* __restrict__ tiles,
                                              const int32_t* __restrict__ leaf_start,
                                              const int4* __restrict__ leaf_ijk,
                                              const int32_t* __restrict__ nbr_ptr, const int32_t* __restrict__ nbr,
@@ -108,8 +110,9 @@ __global__ void __launch_bounds__(128) k_p2p(int64_t ntiles, const int4* __restr
     if (w >= ntiles) return;
     int4 tl = tiles[w];
     int leaf = tl.x;
-    bool active = lane < tl.z;
-    int32_t i = tl.y + (active ? lane : 0);
+    const int tloc = lane / kP2PSub, sub = lane % kP2PSub;
+    bool active = tloc < tl.z;
+    int32_t i = tl.y + (active ? tloc : 0);
     float4 t = __ldg(pts + i);
     int4 tij = __ldg(leaf_ijk + leaf);
     float ar = 0.f, ai = 0.f;
@@ -120,11 +123,16 @@ __global__ void __launch_bounds__(128) k_p2p(int64_t ntiles, const int4* __restr
         float tx = fmaf((float)(tij.x - sij.x), shift, t.x);
         float ty = fmaf((float)(tij.y - sij.y), shift, t.y);
         float tz = fmaf((float)(tij.z - sij.z), shift, t.z);
-        int32_t j0 = __ldg(leaf_start + s), j1 = __ldg(leaf_start + s + 1);
+        int32_t j0 = __ldg(leaf_start + s) + sub, j1 = __ldg(leaf_start + s + 1);
         if (s == leaf) p2p_leaf<POLY, true>(tx, ty, tz, j0, j1, i, pts, sig, ar, ai);
         else p2p_leaf<POLY, false>(tx, ty, tz, j0, j1, i, pts, sig, ar, ai);
     }
-    if (active) phi[i] = make_float2(ar, ai);
+#pragma unroll
+    for (int o = 1; o < kP2PSub; o <<= 1) {
+        ar += __shfl_xor_sync(0xffffffffu, ar, o);
+        ai += __shfl_xor_sync(0xffffffffu, ai, o);
+    }
+    if (active && sub == 0) phi[i] = make_float2(ar, ai);
 }
 
 // ============================================================== FP32 special functions
@@ -197,127 +205,186 @@ __device__ __forceinline__ Dir make_dir(float x, float y, float z) {
     return d;
 }
 
-// ============================================================== P2M
-// One block per leaf.  Points are staged in chunks: each staged point stores
-// jt_n Q_n^m (m >= 0, triangular index) and sh e^{-i m phi}, sh e^{+i m phi}.
-__global__ void k_p2m(const int32_t* __restrict__ leaf_start, const float4* __restrict__ pts,
-                      const float2* __restrict__ sig, int p, float s, int chunk, float2* __restrict__ M) {
-    extern __shared__ float sm[];
-    int leaf = blockIdx.x;
-    int P = (p + 1) * (p + 1);
-    int H = (p + 1) * (p + 2) / 2;
-    int stride = H + 4 * (p + 1);
-    int32_t b0 = leaf_start[leaf], b1 = leaf_start[leaf + 1];
-    for (int c0 = 0; c0 < P; c0 += blockDim.x) {
-        int c = c0 + threadIdx.x;
-        int n = 0, m = 0;
-        if (c < P) {
-            n = (int)sqrtf((float)c);
-            while (n * n > c) --n;
-            while ((n + 1) * (n + 1) <= c) ++n;
-            m = c - n * n - n;
+// ============================================================== Legendre tables
+// Normalised associated Legendre functions Q_n^m (orthonormal Y without the
+// Condon-Shortley phase):  Q_m^m = qmm[m] sin^m,  Q_{m+1}^m = sqrt(2m+3) cos Q_m^m,
+// Q_n^m = a_nm (cos Q_{n-1}^m - b_nm Q_{n-2}^m), indexed by n(n+1)/2 + m.
+constexpr int kLegH = (HFMM_PMAX + 1) * (HFMM_PMAX + 2) / 2;
+__constant__ float c_leg_a[kLegH];
+__constant__ float c_leg_b[kLegH];
+__constant__ float c_leg_qmm[HFMM_PMAX + 1];
+
+void upload_legendre_tables() {
+    static bool done[64] = {};
+    int dev = 0;
+    HFMM_CUDA(cudaGetDevice(&dev));
+    if (dev < 64 && done[dev]) return;
+    std::vector<float> a(kLegH, 0.f), b(kLegH, 0.f), q(HFMM_PMAX + 1, 0.f);
+    double qmm = 0.28209479177387814;  // 1/sqrt(4 pi)
+    for (int m = 0; m <= HFMM_PMAX; ++m) {
+        if (m > 0) qmm *= std::sqrt((2.0 * m + 1.0) / (2.0 * m));
+        q[m] = (float)qmm;
+        for (int n = m; n <= HFMM_PMAX; ++n) {
+            int h = n * (n + 1) / 2 + m;
+            if (n == m + 1) a[h] = (float)std::sqrt(2.0 * m + 3.0);
+            if (n >= m + 2) {
+                a[h] = (float)std::sqrt((4.0 * n * n - 1.0) / ((double)n * n - (double)m * m));
+                b[h] = (float)std::sqrt(((double)(n - 1) * (n - 1) - (double)m * m) / (4.0 * (n - 1) * (n - 1) - 1.0));
+            }
         }
-        int hidx = n * (n + 1) / 2 + (m < 0 ? -m : m);
-        float accr = 0.f, acci = 0.f;
-        for (int32_t j0 = b0; j0 < b1; j0 += chunk) {
-            int cnt = min(chunk, b1 - j0);
+    }
+    HFMM_CUDA(cudaMemcpyToSymbol(c_leg_a, a.data(), sizeof(float) * kLegH));
+    HFMM_CUDA(cudaMemcpyToSymbol(c_leg_b, b.data(), sizeof(float) * kLegH));
+    HFMM_CUDA(cudaMemcpyToSymbol(c_leg_qmm, q.data(), sizeof(float) * (HFMM_PMAX + 1)));
+    if (dev < 64) done[dev] = true;
+}
+
+// ============================================================== P2M
+// One block (128 threads) per leaf; points are taken in chunks of up to 32:
+//   phase 1: thread j computes the scaled radial functions jt_n(k r_j), n <= p;
+//   phase 2: thread (m, j) runs the Legendre recurrence in n for its order m and
+//            stores jt_n Q_n^m and sh e^{-/+ i m phi};
+//   phase 3: thread c accumulates coefficient c = n^2 + n + m over the chunk.
+__global__ void __launch_bounds__(128) k_p2m(const int32_t* __restrict__ leaf_start,
+                                             const float4* __restrict__ pts, const float2* __restrict__ sig,
+                                             int p, float s, float2* __restrict__ M) {
+    constexpr int kChunk = 32;
+    extern __shared__ float sm[];
+    const int leaf = blockIdx.x;
+    const int P = (p + 1) * (p + 1);
+    const int H = (p + 1) * (p + 2) / 2;
+    float* rad = sm;                          // [kChunk][p+1]
+    float* B = rad + kChunk * (p + 1);        // [kChunk][H]
+    float* E = B + kChunk * H;                // [kChunk][p+1][4]
+    float* geo = E + kChunk * (p + 1) * 4;    // [kChunk][4]: cos t, sin t, cos phi, sin phi
+    const int32_t b0 = leaf_start[leaf], b1 = leaf_start[leaf + 1];
+    // two coefficients per thread per pass; orders above 14 take more passes
+    for (int cg = 0; cg < P; cg += 256) {
+        int cc[2], hidx[2], eo[2];
+        for (int q = 0; q < 2; ++q) {
+            cc[q] = cg + threadIdx.x + 128 * q;
+            int n = 0, m = 0;
+            if (cc[q] < P) {
+                n = (int)sqrtf((float)cc[q]);
+                while (n * n > cc[q]) --n;
+                while ((n + 1) * (n + 1) <= cc[q]) ++n;
+                m = cc[q] - n * n - n;
+            }
+            hidx[q] = n * (n + 1) / 2 + (m < 0 ? -m : m);
+            eo[q] = 4 * (m < 0 ? -m : m) + (m < 0 ? 2 : 0);
+        }
+        float accr[2] = {0.f, 0.f}, acci[2] = {0.f, 0.f};
+        for (int32_t j0 = b0; j0 < b1; j0 += kChunk) {
+            const int cnt = min(kChunk, b1 - j0);
             if (threadIdx.x < cnt) {
-                float* row = sm + threadIdx.x * stride;
-                float4 y = pts[j0 + threadIdx.x];
-                float2 sg = sig[j0 + threadIdx.x];
-                Dir d = make_dir(y.x, y.y, y.z);
+                const int j = threadIdx.x;
+                const float4 y = pts[j0 + j];
+                const Dir d = make_dir(y.x, y.y, y.z);
                 float jr[HFMM_PMAX + 1];
                 f_jn_scaled(p, d.r, s, jr);
-                float qmm = 0.28209479177387814f;
-                float er = 1.f, ei = 0.f;
-                for (int mm = 0; mm <= p; ++mm) {
-                    if (mm > 0) {
-                        qmm *= sqrtf((2.f * mm + 1.f) / (2.f * mm)) * d.st;
-                        float t = er * d.ex - ei * d.ey;
-                        ei = er * d.ey + ei * d.ex;
-                        er = t;
-                    }
-                    // sh e^{-i m phi} and sh e^{+i m phi}
-                    row[H + 4 * mm + 0] = sg.x * er + sg.y * ei;
-                    row[H + 4 * mm + 1] = sg.y * er - sg.x * ei;
-                    row[H + 4 * mm + 2] = sg.x * er - sg.y * ei;
-                    row[H + 4 * mm + 3] = sg.y * er + sg.x * ei;
-                    float qa = qmm, qb = 0.f;
-                    for (int nn = mm; nn <= p; ++nn) {
-                        float qn;
-                        if (nn == mm) qn = qmm;
-                        else if (nn == mm + 1) qn = sqrtf(2.f * mm + 3.f) * d.ct * qmm;
-                        else {
-                            float a = sqrtf((4.f * nn * nn - 1.f) / (float)(nn * nn - mm * mm));
-                            float bb = sqrtf((float)((nn - 1) * (nn - 1) - mm * mm) / (4.f * (nn - 1) * (nn - 1) - 1.f));
-                            qn = a * (d.ct * qa - bb * qb);
-                        }
-                        if (nn > mm) { qb = qa; qa = qn; }
-                        row[nn * (nn + 1) / 2 + mm] = jr[nn] * qn;
-                    }
+                for (int q = 0; q <= p; ++q) rad[j * (p + 1) + q] = jr[q];
+                geo[4 * j + 0] = d.ct;
+                geo[4 * j + 1] = d.st;
+                geo[4 * j + 2] = d.ex;
+                geo[4 * j + 3] = d.ey;
+            }
+            __syncthreads();
+            for (int task = threadIdx.x; task < (p + 1) * kChunk; task += blockDim.x) {
+                const int mm = task / kChunk, j = task % kChunk;  // a warp shares one m
+                if (j >= cnt) continue;
+                const float ct = geo[4 * j], st = geo[4 * j + 1], ex = geo[4 * j + 2], ey = geo[4 * j + 3];
+                float qmm = c_leg_qmm[mm], er = 1.f, ei = 0.f;
+                for (int q = 0; q < mm; ++q) {
+                    qmm *= st;
+                    const float t = er * ex - ei * ey;
+                    ei = er * ey + ei * ex;
+                    er = t;
+                }
+                const float2 sg = sig[j0 + j];
+                float* e = E + (j * (p + 1) + mm) * 4;
+                e[0] = sg.x * er + sg.y * ei;  // sh e^{-i m phi}
+                e[1] = sg.y * er - sg.x * ei;
+                e[2] = sg.x * er - sg.y * ei;  // sh e^{+i m phi}
+                e[3] = sg.y * er + sg.x * ei;
+                const float* rj = rad + j * (p + 1);
+                float* bj = B + j * H;
+                float qa = qmm, qb = 0.f;
+                bj[mm * (mm + 1) / 2 + mm] = rj[mm] * qmm;
+                for (int nn = mm + 1; nn <= p; ++nn) {
+                    const int h = nn * (nn + 1) / 2 + mm;
+                    const float qn = (nn == mm + 1) ? c_leg_a[h] * ct * qmm : c_leg_a[h] * (ct * qa - c_leg_b[h] * qb);
+                    qb = qa;
+                    qa = qn;
+                    bj[h] = rj[nn] * qn;
                 }
             }
             __syncthreads();
-            if (c < P) {
-                int eo = H + 4 * (m < 0 ? -m : m) + (m < 0 ? 2 : 0);
-                for (int t = 0; t < cnt; ++t) {
-                    const float* row = sm + t * stride;
-                    float b = row[hidx];
-                    accr = fmaf(b, row[eo], accr);
-                    acci = fmaf(b, row[eo + 1], acci);
-                }
-            }
+#pragma unroll
+            for (int q = 0; q < 2; ++q)
+                if (cc[q] < P)
+                    for (int t = 0; t < cnt; ++t) {
+                        const float bb = B[t * H + hidx[q]];
+                        const float* e = E + t * (p + 1) * 4;
+                        accr[q] = fmaf(bb, e[eo[q]], accr[q]);
+                        acci[q] = fmaf(bb, e[eo[q] + 1], acci[q]);
+                    }
             __syncthreads();
         }
-        if (c < P) M[(int64_t)leaf * P + c] = make_float2(accr, acci);
+#pragma unroll
+        for (int q = 0; q < 2; ++q)
+            if (cc[q] < P) M[(int64_t)leaf * P + cc[q]] = make_float2(accr[q], acci[q]);
     }
 }
 
+size_t p2m_smem_bytes(int p) {
+    const int H = (p + 1) * (p + 2) / 2;
+    return sizeof(float) * (32 * (p + 1) + 32 * H + 32 * (p + 1) * 4 + 128);
+}
+
 // ============================================================== L2P
-__global__ void k_l2p(int64_t N, const int32_t* __restrict__ pt_leaf, const float4* __restrict__ pts, int p,
-                      float s, const float2* __restrict__ Lc, float2* __restrict__ phi) {
+__global__ void __launch_bounds__(128) k_l2p(int64_t N, const int32_t* __restrict__ pt_leaf,
+                                             const float4* __restrict__ pts, int p, float s,
+                                             const float2* __restrict__ Lc, float2* __restrict__ phi) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
-    int P = (p + 1) * (p + 1);
+    const int P = (p + 1) * (p + 1);
     const float2* L = Lc + (int64_t)pt_leaf[i] * P;
-    float4 y = pts[i];
-    Dir d = make_dir(y.x, y.y, y.z);
+    const float4 y = pts[i];
+    const Dir d = make_dir(y.x, y.y, y.z);
     float jr[HFMM_PMAX + 1];
     f_jn_scaled(p, d.r, s, jr);
     float accr = 0.f, acci = 0.f;
-    float qmm = 0.28209479177387814f;
-    float er = 1.f, ei = 0.f;
+    float stp = 1.f, er = 1.f, ei = 0.f;
     for (int m = 0; m <= p; ++m) {
         if (m > 0) {
-            qmm *= sqrtf((2.f * m + 1.f) / (2.f * m)) * d.st;
-            float t = er * d.ex - ei * d.ey;
+            stp *= d.st;
+            const float t = er * d.ex - ei * d.ey;
             ei = er * d.ey + ei * d.ex;
             er = t;
         }
+        const float qmm = c_leg_qmm[m] * stp;
         float qa = qmm, qb = 0.f;
         for (int n = m; n <= p; ++n) {
-            float qn;
-            if (n == m) qn = qmm;
-            else if (n == m + 1) qn = sqrtf(2.f * m + 3.f) * d.ct * qmm;
-            else {
-                float a = sqrtf((4.f * n * n - 1.f) / (float)(n * n - m * m));
-                float bb = sqrtf((float)((n - 1) * (n - 1) - m * m) / (4.f * (n - 1) * (n - 1) - 1.f));
-                qn = a * (d.ct * qa - bb * qb);
+            float qn = qmm;
+            if (n > m) {
+                const int h = n * (n + 1) / 2 + m;
+                qn = (n == m + 1) ? c_leg_a[h] * d.ct * qmm : c_leg_a[h] * (d.ct * qa - c_leg_b[h] * qb);
+                qb = qa;
+                qa = qn;
             }
-            if (n > m) { qb = qa; qa = qn; }
-            float b = jr[n] * qn;
-            float2 lp = L[n * n + n + m];
+            const float bq = jr[n] * qn;
+            const float2 lp = L[n * n + n + m];
             // L_{n,m} b e^{+i m phi}
-            accr += b * (lp.x * er - lp.y * ei);
-            acci += b * (lp.x * ei + lp.y * er);
+            accr += bq * (lp.x * er - lp.y * ei);
+            acci += bq * (lp.x * ei + lp.y * er);
             if (m > 0) {
-                float2 lm = L[n * n + n - m];
-                accr += b * (lm.x * er + lm.y * ei);
-                acci += b * (lm.y * er - lm.x * ei);
+                const float2 lm = L[n * n + n - m];
+                accr += bq * (lm.x * er + lm.y * ei);
+                acci += bq * (lm.y * er - lm.x * ei);
             }
         }
     }
-    float2 o = phi[i];
+    const float2 o = phi[i];
     phi[i] = make_float2(o.x + accr, o.y + acci);
 }
 
@@ -496,12 +563,12 @@ void run_matvec_sorted(hfmm_plan* P, int parts, cudaStream_t st) {
     int64_t N = P->N;
     mark_stage(P, 1, st);
     if (parts & 1) {
-        unsigned nb = (unsigned)((P->ntiles * 32 + 127) / 128);
+        unsigned nb = (unsigned)((P->ntiles * 32 + 255) / 256);
         if (P->poly_p2p)
-            k_p2p<true><<<nb, 128, 0, st>>>(P->ntiles, P->tiles.p, P->leaf_start.p, P->leaf_ijk.p, P->nbr_ptr.p,
+            k_p2p<true><<<nb, 256, 0, st>>>(P->ntiles, P->tiles.p, P->leaf_start.p, P->leaf_ijk.p, P->nbr_ptr.p,
                                             P->nbr.p, P->pts.p, P->sig.p, P->p2p_shift, P->phi.p);
         else
-            k_p2p<false><<<nb, 128, 0, st>>>(P->ntiles, P->tiles.p, P->leaf_start.p, P->leaf_ijk.p, P->nbr_ptr.p,
+            k_p2p<false><<<nb, 256, 0, st>>>(P->ntiles, P->tiles.p, P->leaf_start.p, P->leaf_ijk.p, P->nbr_ptr.p,
                                              P->nbr.p, P->pts.p, P->sig.p, P->p2p_shift, P->phi.p);
         ++P->launches;
     } else {
@@ -514,11 +581,11 @@ void run_matvec_sorted(hfmm_plan* P, int parts, cudaStream_t st) {
         // multipoles above the leaves and all locals accumulate: clear them
         HFMM_CUDA(cudaMemsetAsync(P->coef.p, 0, sizeof(float2) * P->coef_total, st));
         const LevelInfo& lv = P->lev[L];
-        int p = lv.p;
-        int H = (p + 1) * (p + 2) / 2, stride = H + 4 * (p + 1);
-        int chunk = std::max(1, std::min(32, (40 * 1024) / (stride * 4)));
-        k_p2m<<<(unsigned)P->nleaf, 128, (size_t)chunk * stride * sizeof(float), st>>>(
-            P->leaf_start.p, P->pts.p, P->sig.p, p, (float)lv.s, chunk, P->coef.p + lv.mofs);
+        const size_t smem = p2m_smem_bytes(lv.p);
+        if (smem > 48 * 1024)
+            HFMM_CUDA(cudaFuncSetAttribute(k_p2m, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_p2m<<<(unsigned)P->nleaf, 128, smem, st>>>(P->leaf_start.p, P->pts.p, P->sig.p, lv.p, (float)lv.s,
+                                                       P->coef.p + lv.mofs);
         ++P->launches;
     }
     mark_stage(P, 3, st);

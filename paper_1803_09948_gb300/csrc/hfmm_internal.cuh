@@ -13,6 +13,8 @@
 #define HFMM_PMAX 40          // largest expansion order a plan accepts
 #define HFMM_NEAR_CAP 128     // largest near/self triangle set per target
 #define HFMM_TRANS_NB 64      // columns per translation work item
+constexpr int kP2PTile = 8;   // targets per near-field warp
+constexpr int kP2PSub = 4;    // lanes sharing one target (kP2PTile * kP2PSub == 32)
 
 // ---------------------------------------------------------------- errors
 struct HfmmError {
@@ -163,6 +165,8 @@ void run_matvec_sorted(hfmm_plan* P, int parts, cudaStream_t st);
 void mark_stage(hfmm_plan* P, int q, cudaStream_t st);
 void run_direct_sorted(hfmm_plan* P, cudaStream_t st);
 void launch_planewave(hfmm_plan* P, double dx, double dy, double dz, float2* out, cudaStream_t st);
+// copies the normalised Legendre recurrence tables to the current device (once per device)
+void upload_legendre_tables();
 
 // ---------------------------------------------------------------- kernels: plan build (FP64)
 struct ProjectionJob {

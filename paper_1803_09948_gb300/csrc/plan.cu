@@ -263,8 +263,8 @@ static void build_plan(hfmm_plan* P, const double* V, int64_t nv, const int32_t*
                     if (s >= 0) nbr.push_back((int32_t)s);
                 }
         nbr_ptr[b + 1] = (int32_t)nbr.size();
-        for (int32_t i0 = leaves.start[b]; i0 < leaves.start[b + 1]; i0 += 32)
-            tiles.push_back(make_int4((int)b, i0, std::min(32, leaves.start[b + 1] - i0), 0));
+        for (int32_t i0 = leaves.start[b]; i0 < leaves.start[b + 1]; i0 += kP2PTile)
+            tiles.push_back(make_int4((int)b, i0, std::min(kP2PTile, leaves.start[b + 1] - i0), 0));
     }
     P->ntiles = (int64_t)tiles.size();
     double pairs = 0.0;
@@ -279,6 +279,7 @@ static void build_plan(hfmm_plan* P, const double* V, int64_t nv, const int32_t*
     P->poly_p2p = 12.0 * (k * sideL) * (k * sideL) * 1.001 <= (double)HFMM_POLY_UMAX;
 
     size_t* cnt = &P->dev_bytes;
+    upload_legendre_tables();
     P->pts.upload(pts, cnt, st);
     P->perm.upload(perm, cnt, st);
     P->iperm.upload(iperm, cnt, st);
