@@ -135,6 +135,104 @@ __global__ void __launch_bounds__(256) k_p2p(int64_t ntiles, const int4* __restr
     if (active && sub == 0) phi[i] = make_float2(ar, ai);
 }
 
+// One block (4 warps) per target leaf.  The sources of all neighbour leaves are
+// staged once in shared memory, shifted into the target leaf's frame, self leaf
+// first (its entries are the targets themselves).  Warp w handles target tiles
+// w, w+4, ...; within a tile each target is shared by kP2PSub lanes.  The self
+// segment carries the j != i mask and the u = 0 guard; the rest runs unmasked.
+template <bool POLY, bool MASK>
+__device__ __forceinline__ void p2p_span(float tx, float ty, float tz, int k0, int k1, int self_k,
+                                         const float4* __restrict__ sp, const float* __restrict__ sim,
+                                         float& ar, float& ai) {
+    constexpr float kC[HFMM_POLY_C_DEG + 1] = HFMM_POLY_C_INIT;
+    constexpr float kS[HFMM_POLY_S_DEG + 1] = HFMM_POLY_S_INIT;
+#pragma unroll 4
+    for (int k = k0; k < k1; k += kP2PSub) {
+        const float4 q = sp[k];  // x, y, z, Re sigma
+        float sr = q.w, si = sim[k];
+        if (MASK && k == self_k) sr = si = 0.f;
+        const float dx = tx - q.x, dy = ty - q.y, dz = tz - q.z;
+        const float u = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+        const float rinv = MASK ? rsqrtf(fmaxf(u, 1e-30f)) : rsqrtf(u);
+        float re, im;
+        if (POLY) {
+            re = horner<HFMM_POLY_C_DEG>(kC, u) * rinv;
+            im = horner<HFMM_POLY_S_DEG>(kS, u);
+        } else {
+            float r = u * rinv, sn, cs;
+            sincosf(r, &sn, &cs);
+            re = cs * rinv;
+            im = sn * rinv;
+        }
+        ar = fmaf(sr, re, fmaf(-si, im, ar));
+        ai = fmaf(sr, im, fmaf(si, re, ai));
+    }
+}
+
+template <bool POLY>
+__global__ void __launch_bounds__(128) k_p2p_staged(const int32_t* __restrict__ leaf_start,
+                                                    const int4* __restrict__ leaf_ijk,
+                                                    const int32_t* __restrict__ nbr_ptr,
+                                                    const int32_t* __restrict__ nbr,
+                                                    const float4* __restrict__ pts,
+                                                    const float2* __restrict__ sig, float shift, int cap,
+                                                    float2* __restrict__ phi) {
+    extern __shared__ float4 sp[];  // [cap]: shifted position, Re sigma
+    float* sim = reinterpret_cast<float*>(sp + cap);  // [cap]: Im sigma
+    __shared__ int s_off[29], s_leaf[28];
+    const int b = blockIdx.x, tid = threadIdx.x;
+    const int4 tij = __ldg(leaf_ijk + b);
+    const int nb0 = __ldg(nbr_ptr + b), nn = __ldg(nbr_ptr + b + 1) - nb0;
+    if (tid == 0) {
+        int k = 0, o = 0;
+        s_leaf[k++] = b;  // self first
+        for (int q = 0; q < nn; ++q) {
+            const int sl = __ldg(nbr + nb0 + q);
+            if (sl != b) s_leaf[k++] = sl;
+        }
+        for (int q = 0; q < k; ++q) {
+            s_off[q] = o;
+            o += __ldg(leaf_start + s_leaf[q] + 1) - __ldg(leaf_start + s_leaf[q]);
+        }
+        s_off[k] = o;
+        s_off[28] = k;
+    }
+    __syncthreads();
+    const int nl = s_off[28], total = s_off[nl];
+    for (int q = 0; q < nl; ++q) {
+        const int sl = s_leaf[q];
+        const int j0 = __ldg(leaf_start + sl), n = s_off[q + 1] - s_off[q];
+        const int4 sij = __ldg(leaf_ijk + sl);
+        const float ox = (float)(sij.x - tij.x) * shift, oy = (float)(sij.y - tij.y) * shift,
+                    oz = (float)(sij.z - tij.z) * shift;
+        for (int e = tid; e < n; e += blockDim.x) {
+            const float4 p = __ldg(pts + j0 + e);
+            const float2 g = __ldg(sig + j0 + e);
+            sp[s_off[q] + e] = make_float4(p.x + ox, p.y + oy, p.z + oz, g.x);
+            sim[s_off[q] + e] = g.y;
+        }
+    }
+    __syncthreads();
+    const int warp = tid >> 5, lane = tid & 31;
+    const int nself = s_off[1];
+    const int tloc = lane / kP2PSub, sub = lane % kP2PSub;
+    for (int tile = warp; tile * kP2PTile < nself; tile += 4) {
+        const int it = tile * kP2PTile + tloc;
+        const bool active = it < nself;
+        const int ik = active ? it : 0;
+        const float4 t = sp[ik];
+        float ar = 0.f, ai = 0.f;
+        p2p_span<POLY, true>(t.x, t.y, t.z, sub, nself, ik, sp, sim, ar, ai);
+        p2p_span<POLY, false>(t.x, t.y, t.z, nself + sub, total, -1, sp, sim, ar, ai);
+#pragma unroll
+        for (int o = 1; o < kP2PSub; o <<= 1) {
+            ar += __shfl_xor_sync(0xffffffffu, ar, o);
+            ai += __shfl_xor_sync(0xffffffffu, ai, o);
+        }
+        if (active && sub == 0) phi[__ldg(leaf_start + b) + it] = make_float2(ar, ai);
+    }
+}
+
 // ============================================================== FP32 special functions
 // out[n] = j_n(x) / s^n, n = 0..p
 __device__ static void f_jn_scaled(int p, float x, float s, float* out) {
@@ -464,28 +562,41 @@ __global__ void __launch_bounds__(128) k_translate(const TransItem* __restrict__
 }
 
 // ============================================================== correction (CSR SpMV)
-__global__ void k_corr(int64_t N, const int64_t* __restrict__ ptr, const int32_t* __restrict__ col,
-                       const float2* __restrict__ val, const float2* __restrict__ sig, float2* __restrict__ phi) {
-    int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    int lane = threadIdx.x & 31;
-    if (row >= N) return;
-    int64_t e0 = ptr[row], e1 = ptr[row + 1];
+// kCorrLanes lanes per row (rows hold ~3 * (near triangles) nonzeros, a few dozen)
+constexpr int kCorrLanes = 8;
+__global__ void __launch_bounds__(256) k_corr(int64_t N, const int64_t* __restrict__ ptr,
+                                              const int32_t* __restrict__ col, const float2* __restrict__ val,
+                                              const float2* __restrict__ sig, float2* __restrict__ phi) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t row = t / kCorrLanes;
+    const int sub = (int)(t % kCorrLanes);
+    const bool active = row < N;
     float ar = 0.f, ai = 0.f;
-    for (int64_t e = e0 + lane; e < e1; e += 32) {
-        float2 v = __ldg(val + e);
-        float2 s = __ldg(sig + __ldg(col + e));
-        ar = fmaf(v.x, s.x, fmaf(-v.y, s.y, ar));
-        ai = fmaf(v.x, s.y, fmaf(v.y, s.x, ai));
+    if (active) {
+        const int64_t e0 = __ldg(ptr + row), e1 = __ldg(ptr + row + 1);
+        for (int64_t e = e0 + sub; e < e1; e += kCorrLanes) {
+            const float2 v = __ldg(val + e);
+            const float2 s = __ldg(sig + __ldg(col + e));
+            ar = fmaf(v.x, s.x, fmaf(-v.y, s.y, ar));
+            ai = fmaf(v.x, s.y, fmaf(v.y, s.x, ai));
+        }
     }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
+    for (int o = kCorrLanes / 2; o > 0; o >>= 1) {
         ar += __shfl_xor_sync(0xffffffffu, ar, o);
         ai += __shfl_xor_sync(0xffffffffu, ai, o);
     }
-    if (lane == 0) {
-        float2 v = phi[row];
+    if (active && sub == 0) {
+        const float2 v = phi[row];
         phi[row] = make_float2(v.x + ar, v.y + ai);
     }
+}
+
+static void launch_corr(hfmm_plan* P, cudaStream_t st) {
+    const int64_t threads = P->N * kCorrLanes;
+    k_corr<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(P->N, P->corr_ptr.p, P->corr_col.p, P->corr_val.p,
+                                                              P->sig.p, P->phi.p);
+    ++P->launches;
 }
 
 // ============================================================== direct O(N^2) sum
@@ -563,6 +674,23 @@ void run_matvec_sorted(hfmm_plan* P, int parts, cudaStream_t st) {
     int64_t N = P->N;
     mark_stage(P, 1, st);
     if (parts & 1) {
+        const size_t staged = (size_t)P->p2p_cap * (sizeof(float4) + sizeof(float));
+        if (P->p2p_cap > 0 && staged <= 96 * 1024) {
+            if (staged > 48 * 1024) {
+                HFMM_CUDA(cudaFuncSetAttribute(k_p2p_staged<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)staged));
+                HFMM_CUDA(cudaFuncSetAttribute(k_p2p_staged<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)staged));
+            }
+            if (P->poly_p2p)
+                k_p2p_staged<true><<<(unsigned)P->nleaf, 128, staged, st>>>(
+                    P->leaf_start.p, P->leaf_ijk.p, P->nbr_ptr.p, P->nbr.p, P->pts.p, P->sig.p, P->p2p_shift,
+                    P->p2p_cap, P->phi.p);
+            else
+                k_p2p_staged<false><<<(unsigned)P->nleaf, 128, staged, st>>>(
+                    P->leaf_start.p, P->leaf_ijk.p, P->nbr_ptr.p, P->nbr.p, P->pts.p, P->sig.p, P->p2p_shift,
+                    P->p2p_cap, P->phi.p);
+        } else {
         unsigned nb = (unsigned)((P->ntiles * 32 + 255) / 256);
         if (P->poly_p2p)
             k_p2p<true><<<nb, 256, 0, st>>>(P->ntiles, P->tiles.p, P->leaf_start.p, P->leaf_ijk.p, P->nbr_ptr.p,
@@ -570,6 +698,7 @@ void run_matvec_sorted(hfmm_plan* P, int parts, cudaStream_t st) {
         else
             k_p2p<false><<<nb, 256, 0, st>>>(P->ntiles, P->tiles.p, P->leaf_start.p, P->leaf_ijk.p, P->nbr_ptr.p,
                                              P->nbr.p, P->pts.p, P->sig.p, P->p2p_shift, P->phi.p);
+        }
         ++P->launches;
     } else {
         HFMM_CUDA(cudaMemsetAsync(P->phi.p, 0, sizeof(float2) * N, st));
@@ -590,7 +719,16 @@ void run_matvec_sorted(hfmm_plan* P, int parts, cudaStream_t st) {
     }
     mark_stage(P, 3, st);
     if (far)
-        for (int l = L - 1; l >= 2; --l) launch_translate(P, P->m2m_items_begin[l], P->m2m_items_end[l], st);
+        for (int l = L - 1; l >= 2; --l) {
+            const auto& g = P->m2m_tc[l];
+            if (g.second > g.first) {
+                m2l_tc_launch(P->tc_groups.p + g.first, g.second - g.first, P->items.p, P->item_cols.p, P->aops.p,
+                              P->coef.p, P->dev_err.p, st);
+                ++P->launches;
+            } else {
+                launch_translate(P, P->m2m_items_begin[l], P->m2m_items_end[l], st);
+            }
+        }
     mark_stage(P, 4, st);
     if (far) {
         for (const auto& r : P->m2l_simt_ranges) launch_translate(P, r.first, r.second, st);
@@ -602,7 +740,16 @@ void run_matvec_sorted(hfmm_plan* P, int parts, cudaStream_t st) {
     }
     mark_stage(P, 5, st);
     if (far)
-        for (int l = 3; l <= L; ++l) launch_translate(P, P->l2l_items_begin[l], P->l2l_items_end[l], st);
+        for (int l = 3; l <= L; ++l) {
+            const auto& g = P->l2l_tc[l];
+            if (g.second > g.first) {
+                m2l_tc_launch(P->tc_groups.p + g.first, g.second - g.first, P->items.p, P->item_cols.p, P->aops.p,
+                              P->coef.p, P->dev_err.p, st);
+                ++P->launches;
+            } else {
+                launch_translate(P, P->l2l_items_begin[l], P->l2l_items_end[l], st);
+            }
+        }
     mark_stage(P, 6, st);
     if (far) {
         const LevelInfo& lv = P->lev[L];
@@ -612,9 +759,7 @@ void run_matvec_sorted(hfmm_plan* P, int parts, cudaStream_t st) {
     }
     mark_stage(P, 7, st);
     if ((parts & 4) && P->corr_nnz > 0) {
-        k_corr<<<(unsigned)((N * 32 + 255) / 256), 256, 0, st>>>(N, P->corr_ptr.p, P->corr_col.p, P->corr_val.p,
-                                                               P->sig.p, P->phi.p);
-        ++P->launches;
+        launch_corr(P, st);
     }
     mark_stage(P, 8, st);
     HFMM_CUDA(cudaGetLastError());
@@ -626,9 +771,7 @@ void run_direct_sorted(hfmm_plan* P, cudaStream_t st) {
                                                           P->p2p_shift, P->phi.p);
     ++P->launches;
     if (P->corr_nnz > 0) {
-        k_corr<<<(unsigned)((N * 32 + 255) / 256), 256, 0, st>>>(N, P->corr_ptr.p, P->corr_col.p, P->corr_val.p,
-                                                               P->sig.p, P->phi.p);
-        ++P->launches;
+        launch_corr(P, st);
     }
     HFMM_CUDA(cudaGetLastError());
 }

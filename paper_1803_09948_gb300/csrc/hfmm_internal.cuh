@@ -102,6 +102,7 @@ struct hfmm_plan {
     size_t dev_bytes = 0;
     bool poly_p2p = true;   // near field fits the polynomial kernel range
     float p2p_shift = 0.f;  // k * side of a leaf
+    int p2p_cap = 0;        // most source points in one leaf's neighbourhood (staged near field)
 
     // sorted point data
     DBuf<float4> pts;        // k * (x - leaf centre), sorted
@@ -129,7 +130,8 @@ struct hfmm_plan {
     std::vector<std::pair<int64_t, int64_t>> m2l_simt_ranges;  // M2L item ranges on the SIMT kernel
     DBuf<uint16_t> aops;       // tensor-core M2L operators (BF16 hi/lo, packed)
     DBuf<int4> tc_groups;      // (first item, item count, operator, P) per tensor-core block
-    int64_t n_tc_groups = 0;
+    int64_t n_tc_groups = 0;   // the first n_tc_groups groups are M2L
+    std::vector<std::pair<int64_t, int64_t>> m2m_tc, l2l_tc;  // tensor-core group ranges per level
     DBuf<int> dev_err;         // set by kernels whose bounded waits gave up
     // correction
     DBuf<int64_t> corr_ptr;

@@ -274,6 +274,14 @@ static void build_plan(hfmm_plan* P, const double* V, int64_t nv, const int32_t*
             pairs += nt_b * (double)(leaves.start[nbr[q] + 1] - leaves.start[nbr[q]]);
     }
     P->cost[0] = pairs - (double)N;
+    int64_t cap = 0;
+    for (int64_t b = 0; b < nleaf; ++b) {
+        int64_t tot = 0;
+        for (int32_t q = nbr_ptr[b]; q < nbr_ptr[b + 1]; ++q)
+            tot += leaves.start[nbr[q] + 1] - leaves.start[nbr[q]];
+        cap = std::max(cap, tot);
+    }
+    P->p2p_cap = (int)std::min<int64_t>(cap, 1 << 30);
     P->cost[4] = (double)N;
     P->p2p_shift = (float)(k * sideL);
     P->poly_p2p = 12.0 * (k * sideL) * (k * sideL) * 1.001 <= (double)HFMM_POLY_UMAX;
@@ -443,42 +451,6 @@ static void build_plan(hfmm_plan* P, const double* V, int64_t nv, const int32_t*
             lev_item_e[l] = (int64_t)items.size();
         }
         P->m2l_items_end = (int64_t)items.size();
-        // tensor-core M2L for levels with (p+1)^2 <= 64: pack operators, group items by operator
-        std::vector<int4> groups;
-        int64_t tc_ops = 0;
-        std::vector<int64_t> tc_base(L + 1, -1);
-        for (int l = 2; l <= L; ++l)
-            if (cfg.m2l_tensor && P->lev[l].P <= 64) {
-                tc_base[l] = tc_ops;
-                tc_ops += 316;
-            }
-        if (tc_ops > 0) {
-            P->aops.alloc((size_t)tc_ops * m2l_tc_op_elems(), cnt);
-            for (int l = 2; l <= L; ++l)
-                if (tc_base[l] >= 0)
-                    m2l_tc_pack(P->ops.p + P->lev[l].m2l_op, P->lev[l].P, 316,
-                                P->aops.p + (size_t)tc_base[l] * m2l_tc_op_elems(), st);
-        }
-        const int kGroupItems = m2l_tc_max_group();
-        for (int l = 2; l <= L; ++l) {
-            if (tc_base[l] < 0) {
-                if (!P->m2l_simt_ranges.empty() && P->m2l_simt_ranges.back().second == lev_item_b[l])
-                    P->m2l_simt_ranges.back().second = lev_item_e[l];
-                else
-                    P->m2l_simt_ranges.push_back({lev_item_b[l], lev_item_e[l]});
-                continue;
-            }
-            int64_t PP = (int64_t)P->lev[l].P * P->lev[l].P;
-            for (int64_t b = lev_item_b[l]; b < lev_item_e[l];) {
-                int64_t e = b;
-                while (e < lev_item_e[l] && e - b < kGroupItems && items[e].op == items[b].op) ++e;
-                int slot = (int)((items[b].op - P->lev[l].m2l_op) / PP);
-                groups.push_back(make_int4((int)b, (int)(e - b), (int)(tc_base[l] + slot), P->lev[l].P));
-                b = e;
-            }
-        }
-        P->n_tc_groups = (int64_t)groups.size();
-        P->tc_groups.upload(groups, cnt, st);
         P->m2l_count = m2l_count;
         for (int l = 3; l <= L; ++l) {  // L2L: parents at l-1 -> children at l
             PairBuckets pb(8);
@@ -494,6 +466,84 @@ static void build_plan(hfmm_plan* P, const double* V, int64_t nv, const int32_t*
             P->l2l_items_end[l] = (int64_t)items.size();
             P->cost[2] += (double)ch.key.size() * P->lev[l].P * P->lev[l - 1].P;
         }
+        // Tensor-core translations: M2L of levels with (p+1)^2 <= 64, and M2M / L2L between
+        // two such levels of equal order.  Operators are packed once; items of one operator
+        // are grouped (consecutive in the item list) for one block each.
+        std::vector<int4> groups;
+        std::vector<std::pair<int64_t, int64_t>> pack;  // (fp32 operator offset, count) per packed block
+        std::vector<int> pack_P;
+        int64_t tc_ops = 0;
+        auto tc_level = [&](int l) { return cfg.m2l_tensor && P->lev[l].P <= 64; };
+        std::vector<int64_t> m2l_base(L + 2, -1), m2m_base(L + 2, -1), l2l_base(L + 2, -1);
+        for (int l = 2; l <= L; ++l) {
+            if (tc_level(l)) {
+                m2l_base[l] = tc_ops;
+                pack.push_back({P->lev[l].m2l_op, 316});
+                pack_P.push_back(P->lev[l].P);
+                tc_ops += 316;
+            }
+            if (l <= L - 1 && tc_level(l) && tc_level(l + 1) && P->lev[l].P == P->lev[l + 1].P) {
+                m2m_base[l] = tc_ops;  // parents at l
+                pack.push_back({P->lev[l + 1].m2m_op, 8});
+                pack_P.push_back(P->lev[l].P);
+                tc_ops += 8;
+            }
+            if (l >= 3 && tc_level(l) && tc_level(l - 1) && P->lev[l].P == P->lev[l - 1].P) {
+                l2l_base[l] = tc_ops;  // children at l
+                pack.push_back({P->lev[l].pc_op, 8});
+                pack_P.push_back(P->lev[l].P);
+                tc_ops += 8;
+            }
+        }
+        if (tc_ops > 0) {
+            P->aops.alloc((size_t)tc_ops * m2l_tc_op_elems(), cnt);
+            int64_t at = 0;
+            for (size_t q = 0; q < pack.size(); ++q) {
+                m2l_tc_pack(P->ops.p + pack[q].first, pack_P[q], (int)pack[q].second,
+                            P->aops.p + (size_t)at * m2l_tc_op_elems(), st);
+                at += pack[q].second;
+            }
+        }
+        const int kGroupItems = m2l_tc_max_group();
+        const int kSmallGroup = 4;  // M2M/L2L have 8 operators per level: small groups keep every SM busy
+        auto make_groups = [&](int64_t ib, int64_t ie, int64_t op0, int64_t opsz, int64_t base, int Pl,
+                               int gmax) {
+            for (int64_t b = ib; b < ie;) {
+                int64_t e = b;
+                while (e < ie && e - b < gmax && items[e].op == items[b].op) ++e;
+                groups.push_back(make_int4((int)b, (int)(e - b), (int)(base + (items[b].op - op0) / opsz), Pl));
+                b = e;
+            }
+        };
+        for (int l = 2; l <= L; ++l) {
+            if (m2l_base[l] < 0) {
+                if (!P->m2l_simt_ranges.empty() && P->m2l_simt_ranges.back().second == lev_item_b[l])
+                    P->m2l_simt_ranges.back().second = lev_item_e[l];
+                else
+                    P->m2l_simt_ranges.push_back({lev_item_b[l], lev_item_e[l]});
+                continue;
+            }
+            make_groups(lev_item_b[l], lev_item_e[l], P->lev[l].m2l_op, (int64_t)P->lev[l].P * P->lev[l].P,
+                        m2l_base[l], P->lev[l].P, kGroupItems);
+        }
+        P->n_tc_groups = (int64_t)groups.size();  // M2L groups come first
+        P->m2m_tc.assign(L + 2, {0, 0});
+        P->l2l_tc.assign(L + 2, {0, 0});
+        for (int l = 2; l <= L; ++l) {
+            if (m2m_base[l] >= 0) {
+                int64_t g0 = (int64_t)groups.size();
+                make_groups(P->m2m_items_begin[l], P->m2m_items_end[l], P->lev[l + 1].m2m_op,
+                            (int64_t)P->lev[l].P * P->lev[l + 1].P, m2m_base[l], P->lev[l].P, kSmallGroup);
+                P->m2m_tc[l] = {g0, (int64_t)groups.size()};
+            }
+            if (l2l_base[l] >= 0) {
+                int64_t g0 = (int64_t)groups.size();
+                make_groups(P->l2l_items_begin[l], P->l2l_items_end[l], P->lev[l].pc_op,
+                            (int64_t)P->lev[l].P * P->lev[l - 1].P, l2l_base[l], P->lev[l].P, kSmallGroup);
+                P->l2l_tc[l] = {g0, (int64_t)groups.size()};
+            }
+        }
+        P->tc_groups.upload(groups, cnt, st);
         P->items.upload(items, cnt, st);
         P->item_cols.upload(cols, cnt, st);
     }
