@@ -11,10 +11,10 @@
 // A and B are split into BF16 high and low parts (x = hi + lo, 16 significant
 // bits), and D = A_hi B_hi + A_hi B_lo + A_lo B_hi is accumulated in FP32 in
 // tensor memory: tcgen05.mma kind::f16, M = 128, N = 64, K = 16 per
-// instruction, operands in shared memory in the K-major no-swizzle
-// (core-matrix) layout.  A is split once at plan time; B is gathered from the
-// multipole array and split on the fly.  A block keeps one T in shared memory
-// for a group of work items of the same offset.
+// instruction.  A is split once at plan time and, for the work items of one
+// offset grouped in a block, held in tensor memory (written once with
+// tcgen05.st); B is gathered from the multipole array, split on the fly and
+// staged in shared memory in the K-major no-swizzle (core-matrix) layout.
 #include <cuda_bf16.h>
 
 #include "hfmm_internal.cuh"
@@ -32,7 +32,8 @@ constexpr uint32_t kSBO = kKc * kCoreBytes;          // next 8-row group
 constexpr uint32_t kLBO = kCoreBytes;                // next 8-element K group
 constexpr uint32_t kABytes = kM * kK * 2;            // 32 KiB per BF16 part
 constexpr uint32_t kBBytes = kN * kK * 2;            // 16 KiB per BF16 part
-constexpr uint32_t kTmemCols = 64;
+constexpr uint32_t kTmemCols = 64;    // one accumulator (N = 64 FP32 columns)
+constexpr uint32_t kTmemA = 128;      // A hi (64 columns) and lo (64 columns): 128 x 128 BF16 each
 constexpr long long kWaitLimit = 1ll << 26;          // try_wait polls before giving up
 
 // element (r, k) of a K-major core-matrix tile with kKc core matrices per 8-row group
@@ -64,6 +65,26 @@ __device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b
         "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n"
         :
         : "r"(tmem_d), "l"(a), "l"(b), "r"(kIdesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_bf16_ta(uint32_t tmem_d, uint32_t tmem_a, uint64_t b, uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}\n"
+        :
+        : "r"(tmem_d), "r"(tmem_a), "l"(b), "r"(kIdesc), "r"(accumulate)
+        : "memory");
+}
+
+// 16 consecutive 32-bit columns of this thread's lane
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&v)[16]) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+        "%14, %15, %16};" ::"r"(taddr),
+        "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]), "r"(v[9]),
+        "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15])
         : "memory");
 }
 
@@ -119,7 +140,7 @@ __device__ __forceinline__ void split_bf16(float x, __nv_bfloat16& hi, __nv_bflo
     lo = __float2bfloat16_rn(x - __bfloat162float(hi));
 }
 
-// Operator conversion (plan time): FP32 complex T [P][P] -> A_hi, A_lo (core-matrix layout).
+// Operator conversion (plan time): FP32 complex T [P][P] -> A_hi, A_lo (row-major BF16).
 __global__ void k_m2l_tc_pack(const float2* __restrict__ T, int P, int nops, __nv_bfloat16* __restrict__ out) {
     int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= (int64_t)nops * kM * kK) return;
@@ -137,8 +158,8 @@ __global__ void k_m2l_tc_pack(const float2* __restrict__ T, int P, int nops, __n
     __nv_bfloat16 hi, lo;
     split_bf16(v, hi, lo);
     __nv_bfloat16* o = out + (int64_t)op * 2 * kM * kK;
-    o[core_index(r, k)] = hi;
-    o[kM * kK + core_index(r, k)] = lo;
+    o[r * kK + k] = hi;  // row-major: row r is TMEM lane r, two K elements per column
+    o[kM * kK + r * kK + k] = lo;
 }
 
 constexpr int kStages = 2;         // B stages and TMEM accumulators in flight
@@ -149,7 +170,6 @@ constexpr int kMmaWarp = (kEpilogue + kProducers) / 32;  // TMEM owner and MMA i
 constexpr int kThreads = kEpilogue + kProducers + 32;
 
 struct TcSmem {
-    __nv_bfloat16 a[2][kM * kK];            // operator T of the group: hi, lo
     __nv_bfloat16 b[kStages][2][kN * kK];   // gathered multipoles: hi, lo per stage
     uint64_t full[kStages];                 // producers -> MMA: stage written
     uint64_t empty[kStages];                // MMA done reading the stage
@@ -214,7 +234,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 
     if (warp == kMmaWarp) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&S.tmem)),
-                     "r"(kStages * kTmemCols)
+                     "r"(kTmemA + kStages * kTmemCols)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -236,13 +256,36 @@ __global__ void __launch_bounds__(kThreads, 1)
             const int w = q / kN, c = q % kN;
             S.cols[w][c] = c < S.items[w].ncol ? cols[S.items[w].cols + c] : make_int2(0, 0);
         }
-        // the group's operator (hi and lo), a straight copy of the packed layout
-        const uint4* src = reinterpret_cast<const uint4*>(aops + (int64_t)g.z * 2 * kM * kK);
-        uint4* dst = reinterpret_cast<uint4*>(&S.a[0][0]);
-        for (int q = tid; q < (int)(2 * kABytes / 16); q += kThreads) dst[q] = __ldg(src + q);
         // K beyond 2P stays zero in B (A is zero there too), so no stale NaN enters a product
         uint4* bz = reinterpret_cast<uint4*>(&S.b[0][0][0]);
         for (int q = tid; q < (int)(kStages * 2 * kBBytes / 16); q += kThreads) bz[q] = make_uint4(0, 0, 0, 0);
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp < 4) {
+        // the group's operator into tensor memory: thread r writes row r (its lane),
+        // hi into columns 0..63 and lo into 64..127, two BF16 per column
+        const uint4* src = reinterpret_cast<const uint4*>(aops + (int64_t)g.z * 2 * kM * kK);
+        const uint32_t lane_base = S.tmem + ((uint32_t)(warp * 32) << 16);
+#pragma unroll 1
+        for (int part = 0; part < 2; ++part) {
+            const uint4* row = src + (size_t)part * (kM * kK / 8) + (size_t)tid * (kK / 8);
+#pragma unroll 1
+            for (int cb = 0; cb < 4; ++cb) {
+                uint32_t v[16];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const uint4 x = __ldg(row + 4 * cb + q);
+                    v[4 * q] = x.x;
+                    v[4 * q + 1] = x.y;
+                    v[4 * q + 2] = x.z;
+                    v[4 * q + 3] = x.w;
+                }
+                tmem_st16(lane_base + (uint32_t)(part * 64 + cb * 16), v);
+            }
+        }
+        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
     }
     fence_async_smem();
     tc_fence_before();
@@ -333,21 +376,25 @@ __global__ void __launch_bounds__(kThreads, 1)
         // ---------------------------------------------------------------- MMA issuer
         int issued = -1;
         if (lane == 0) {
-            const uint32_t a_hi = smem_u32(&S.a[0][0]), a_lo = smem_u32(&S.a[1][0]);
             for (int w = 0; w < nitems; ++w) {
                 const int s = w & 1;
                 const uint32_t ph = (uint32_t)(w >> 1) & 1u;
                 if (!wait_or_abort(smem_u32(&S.full[s]), ph, abort, err)) break;
                 if (!wait_or_abort(smem_u32(&S.tempty[s]), ph ^ 1u, abort, err)) break;
                 tc_fence_after();
-                const uint32_t b_hi = smem_u32(&S.b[s][0][0]), b_lo = smem_u32(&S.b[s][1][0]);
-                const uint32_t d = tmem + (uint32_t)(s * kTmemCols);
-#pragma unroll 1
+                const uint32_t d = tmem + kTmemA + (uint32_t)(s * kTmemCols);
+                // B descriptors of K-step 0; a K-step of 16 advances the start address by
+                // 2 core matrices, i.e. (2 * kLBO) >> 4 in the descriptor's address field.
+                // A of K-step k sits in tensor-memory columns 8k (hi) and 64 + 8k (lo).
+                const uint64_t dbh = umma_desc(smem_u32(&S.b[s][0][0])), dbl = umma_desc(smem_u32(&S.b[s][1][0]));
+                constexpr uint64_t kStep = (2 * kLBO) >> 4;
+#pragma unroll
                 for (int k = 0; k < kK / 16; ++k) {
-                    const uint32_t ko = (uint32_t)k * 2 * kLBO;
-                    mma_bf16(d, umma_desc(a_hi + ko), umma_desc(b_hi + ko), k > 0);
-                    mma_bf16(d, umma_desc(a_hi + ko), umma_desc(b_lo + ko), 1);
-                    mma_bf16(d, umma_desc(a_lo + ko), umma_desc(b_hi + ko), 1);
+                    const uint64_t ko = (uint64_t)k * kStep;
+                    const uint32_t ah = tmem + (uint32_t)(8 * k), al = tmem + 64u + (uint32_t)(8 * k);
+                    mma_bf16_ta(d, ah, dbh + ko, k > 0);
+                    mma_bf16_ta(d, ah, dbl + ko, 1);
+                    mma_bf16_ta(d, al, dbh + ko, 1);
                 }
                 tc_commit(smem_u32(&S.empty[s]));
                 tc_commit(smem_u32(&S.tfull[s]));
@@ -375,7 +422,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             tc_fence_after();
             const TransItem& it = S.items[w];
             const int ncol = it.ncol;
-            const uint32_t base = tmem + (uint32_t)(s * kTmemCols) + ((uint32_t)(warp * 32) << 16);
+            const uint32_t base = tmem + kTmemA + (uint32_t)(s * kTmemCols) + ((uint32_t)(warp * 32) << 16);
             float v[kN];
             tmem_ld64(base, v);
             if ((P & 1) == 0) {
@@ -389,7 +436,19 @@ __global__ void __launch_bounds__(kThreads, 1)
                 tc_fence_before();
                 mbar_arrive(smem_u32(&S.tempty[s]));  // accumulator drained
                 asm volatile("bar.sync 2, 128;" ::: "memory");
-                if (r < ncol) {
+                if (r < ncol && 2 * P == kM) {
+                    // a run of consecutive destination boxes is one contiguous block in both
+                    // the stage and the expansion array: the run's first column adds it all
+                    const int dc = S.cols[w][r].y;
+                    if (r == 0 || S.cols[w][r - 1].y != dc - 1) {
+                        int run = 1;
+                        while (r + run < ncol && S.cols[w][r + run].y == dc + run) ++run;
+                        float2* dst = coef + it.dst + (int64_t)dc * P;
+                        asm volatile("cp.reduce.async.bulk.global.shared::cta.bulk_group.add.f32 [%0], [%1], %2;" ::"l"(dst),
+                                     "r"(smem_u32(&S.stage[s][r][0])), "r"(8 * P * run)
+                                     : "memory");
+                    }
+                } else if (r < ncol) {
                     float2* dst = coef + it.dst + (int64_t)S.cols[w][r].y * P;
                     asm volatile("cp.reduce.async.bulk.global.shared::cta.bulk_group.add.f32 [%0], [%1], %2;" ::"l"(dst),
                                  "r"(smem_u32(&S.stage[s][r][0])), "r"(8 * P)
@@ -420,7 +479,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     __syncthreads();
     tc_fence_after();
     if (warp == kMmaWarp)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kStages * kTmemCols)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"(kTmemA + kStages * kTmemCols)
                      : "memory");
 }
 
