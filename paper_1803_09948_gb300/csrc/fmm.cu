@@ -488,7 +488,9 @@ __global__ void __launch_bounds__(128) k_l2p(int64_t N, const int32_t* __restric
 
 // ============================================================== batched translations
 // Out[:, dst] += T * In[:, src] for the column pairs of one work item.
-// 128 threads, 32-row x 64-column output tiles, K in slices of 32.
+// 128 threads; a block computes one 32-row x 64-column output tile (blockIdx.y
+// selects the rows) with K in slices of 32, so the high orders of the coarse
+// levels, where a level has only a few items, still fill the GPU.
 __global__ void __launch_bounds__(128) k_translate(const TransItem* __restrict__ items, int64_t item0,
                                                    const int2* __restrict__ cols, const float2* __restrict__ ops,
                                                    float2* __restrict__ coef) {
@@ -498,11 +500,13 @@ __global__ void __launch_bounds__(128) k_translate(const TransItem* __restrict__
     TransItem it = items[item0 + blockIdx.x];
     int tid = threadIdx.x;
     int ncol = it.ncol, Pin = it.pin, Pout = it.pout;
+    const int r0 = 32 * (int)blockIdx.y;
+    if (r0 >= Pout) return;  // uniform over the block: items of a lower order in the same launch
     if (tid < HFMM_TRANS_NB) sc[tid] = tid < ncol ? cols[it.cols + tid] : make_int2(0, 0);
     __syncthreads();
     const float2* T = ops + it.op;
     int tx = tid & 15, ty = tid >> 4;  // 16 column groups x 8 row groups
-    for (int r0 = 0; r0 < Pout; r0 += 32) {
+    {
         float accr[4][4], acci[4][4];
 #pragma unroll
         for (int a = 0; a < 4; ++a)
@@ -664,9 +668,11 @@ void mark_stage(hfmm_plan* P, int q, cudaStream_t st) {
     if (P->stage_ev) HFMM_CUDA(cudaEventRecord(P->stage_ev[q], st));
 }
 
-static void launch_translate(hfmm_plan* P, int64_t b, int64_t e, cudaStream_t st) {
+// tiles: 32-row output tiles of the largest output order among the items [b, e)
+static void launch_translate(hfmm_plan* P, int64_t b, int64_t e, int tiles, cudaStream_t st) {
     if (e <= b) return;
-    k_translate<<<(unsigned)(e - b), 128, 0, st>>>(P->items.p, b, P->item_cols.p, P->ops.p, P->coef.p);
+    k_translate<<<dim3((unsigned)(e - b), (unsigned)tiles), 128, 0, st>>>(P->items.p, b, P->item_cols.p, P->ops.p,
+                                                                         P->coef.p);
     ++P->launches;
 }
 
@@ -726,12 +732,13 @@ void run_matvec_sorted(hfmm_plan* P, int parts, cudaStream_t st) {
                               P->coef.p, P->dev_err.p, st);
                 ++P->launches;
             } else {
-                launch_translate(P, P->m2m_items_begin[l], P->m2m_items_end[l], st);
+                launch_translate(P, P->m2m_items_begin[l], P->m2m_items_end[l], (P->lev[l].P + 31) / 32, st);
             }
         }
     mark_stage(P, 4, st);
     if (far) {
-        for (const auto& r : P->m2l_simt_ranges) launch_translate(P, r.first, r.second, st);
+        for (size_t q = 0; q < P->m2l_simt_ranges.size(); ++q)
+            launch_translate(P, P->m2l_simt_ranges[q].first, P->m2l_simt_ranges[q].second, P->m2l_simt_tiles[q], st);
         if (P->n_tc_groups > 0) {
             m2l_tc_launch(P->tc_groups.p, P->n_tc_groups, P->items.p, P->item_cols.p, P->aops.p, P->coef.p,
                           P->dev_err.p, st);
@@ -747,7 +754,7 @@ void run_matvec_sorted(hfmm_plan* P, int parts, cudaStream_t st) {
                               P->coef.p, P->dev_err.p, st);
                 ++P->launches;
             } else {
-                launch_translate(P, P->l2l_items_begin[l], P->l2l_items_end[l], st);
+                launch_translate(P, P->l2l_items_begin[l], P->l2l_items_end[l], (P->lev[l].P + 31) / 32, st);
             }
         }
     mark_stage(P, 6, st);

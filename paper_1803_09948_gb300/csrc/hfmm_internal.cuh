@@ -128,6 +128,7 @@ struct hfmm_plan {
     std::vector<int64_t> l2l_items_begin, l2l_items_end;  // per level l (children at l)
     int64_t m2l_items_begin = 0, m2l_items_end = 0;
     std::vector<std::pair<int64_t, int64_t>> m2l_simt_ranges;  // M2L item ranges on the SIMT kernel
+    std::vector<int> m2l_simt_tiles;  // 32-row output tiles of the largest order in each range
     DBuf<uint16_t> aops;       // tensor-core M2L operators (BF16 hi/lo, packed)
     DBuf<int4> tc_groups;      // (first item, item count, operator, P) per tensor-core block
     int64_t n_tc_groups = 0;   // the first n_tc_groups groups are M2L

@@ -517,10 +517,14 @@ static void build_plan(hfmm_plan* P, const double* V, int64_t nv, const int32_t*
         };
         for (int l = 2; l <= L; ++l) {
             if (m2l_base[l] < 0) {
-                if (!P->m2l_simt_ranges.empty() && P->m2l_simt_ranges.back().second == lev_item_b[l])
+                const int tiles = (P->lev[l].P + 31) / 32;
+                if (!P->m2l_simt_ranges.empty() && P->m2l_simt_ranges.back().second == lev_item_b[l]) {
                     P->m2l_simt_ranges.back().second = lev_item_e[l];
-                else
+                    P->m2l_simt_tiles.back() = std::max(P->m2l_simt_tiles.back(), tiles);
+                } else {
                     P->m2l_simt_ranges.push_back({lev_item_b[l], lev_item_e[l]});
+                    P->m2l_simt_tiles.push_back(tiles);
+                }
                 continue;
             }
             make_groups(lev_item_b[l], lev_item_e[l], P->lev[l].m2l_op, (int64_t)P->lev[l].P * P->lev[l].P,
