@@ -488,78 +488,83 @@ __global__ void __launch_bounds__(128) k_l2p(int64_t N, const int32_t* __restric
 
 // ============================================================== batched translations
 // Out[:, dst] += T * In[:, src] for the column pairs of one work item.
-// 128 threads; a block computes one 32-row x 64-column output tile (blockIdx.y
-// selects the rows) with K in slices of 32, so the high orders of the coarse
-// levels, where a level has only a few items, still fill the GPU.
+// 128 threads; a block computes one output tile of 4 * (128 / CG) rows x 4 * CG
+// columns (blockIdx.y selects the rows), each thread 4 rows x 4 columns, with K
+// in slices staged in shared memory.  CG = 16 (32 x 64 tiles) serves items with
+// many columns; CG = 4 (128 x 16) and CG = 2 (256 x 8) serve the coarse levels,
+// where an offset has only a few targets and the high order makes T the large
+// operand.  Row tiles in separate blocks let a level with few items fill the GPU.
+template <int CG>
 __global__ void __launch_bounds__(128) k_translate(const TransItem* __restrict__ items, int64_t item0,
                                                    const int2* __restrict__ cols, const float2* __restrict__ ops,
                                                    float2* __restrict__ coef) {
-    __shared__ float2 sT[32][33];
-    __shared__ float2 sX[32][65];
-    __shared__ int2 sc[HFMM_TRANS_NB];
+    constexpr int RG = 128 / CG;             // row groups
+    constexpr int TR = 4 * RG, TC = 4 * CG;  // tile rows, tile columns
+    constexpr int KS = TR > 128 ? 16 : 32;   // K slice (T tile <= 32 KiB)
+    __shared__ float2 sT[TR][KS + 1];
+    __shared__ float2 sX[KS][TC + 1];
+    __shared__ int2 sc[TC];
     TransItem it = items[item0 + blockIdx.x];
     int tid = threadIdx.x;
     int ncol = it.ncol, Pin = it.pin, Pout = it.pout;
-    const int r0 = 32 * (int)blockIdx.y;
+    const int r0 = TR * (int)blockIdx.y;
     if (r0 >= Pout) return;  // uniform over the block: items of a lower order in the same launch
-    if (tid < HFMM_TRANS_NB) sc[tid] = tid < ncol ? cols[it.cols + tid] : make_int2(0, 0);
+    if (tid < TC) sc[tid] = tid < ncol ? cols[it.cols + tid] : make_int2(0, 0);
     __syncthreads();
     const float2* T = ops + it.op;
-    int tx = tid & 15, ty = tid >> 4;  // 16 column groups x 8 row groups
-    {
-        float accr[4][4], acci[4][4];
+    const int tx = tid % CG, ty = tid / CG;
+    float accr[4][4], acci[4][4];
 #pragma unroll
-        for (int a = 0; a < 4; ++a)
+    for (int a = 0; a < 4; ++a)
 #pragma unroll
-            for (int b = 0; b < 4; ++b) accr[a][b] = acci[a][b] = 0.f;
-        for (int k0 = 0; k0 < Pin; k0 += 32) {
-            // T tile: rows r0..r0+31, cols k0..k0+31
-            for (int e = tid; e < 32 * 32; e += 128) {
-                int rr = e >> 5, kk = e & 31;
-                int r = r0 + rr, kq = k0 + kk;
-                sT[rr][kk] = (r < Pout && kq < Pin) ? __ldg(T + (int64_t)r * Pin + kq) : make_float2(0.f, 0.f);
-            }
-            // X tile: rows k0..k0+31 of the gathered source columns
-            for (int e = tid; e < 32 * HFMM_TRANS_NB; e += 128) {
-                int cc = e >> 5, kk = e & 31;
-                int kq = k0 + kk;
-                sX[kk][cc] = (cc < ncol && kq < Pin) ? __ldg(coef + it.src + (int64_t)sc[cc].x * Pin + kq)
-                                                     : make_float2(0.f, 0.f);
-            }
-            __syncthreads();
-#pragma unroll 8
-            for (int kk = 0; kk < 32; ++kk) {
-                float2 a[4], b[4];
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    a[q] = sT[ty + 8 * q][kk];
-                    b[q] = sX[kk][tx + 16 * q];
-                }
-#pragma unroll
-                for (int qa = 0; qa < 4; ++qa)
-#pragma unroll
-                    for (int qb = 0; qb < 4; ++qb) {
-                        accr[qa][qb] = fmaf(a[qa].x, b[qb].x, fmaf(-a[qa].y, b[qb].y, accr[qa][qb]));
-                        acci[qa][qb] = fmaf(a[qa].x, b[qb].y, fmaf(a[qa].y, b[qb].x, acci[qa][qb]));
-                    }
-            }
-            __syncthreads();
+        for (int b = 0; b < 4; ++b) accr[a][b] = acci[a][b] = 0.f;
+    for (int k0 = 0; k0 < Pin; k0 += KS) {
+        // T tile: rows r0 .. r0 + TR - 1, columns k0 .. k0 + KS - 1
+        for (int e = tid; e < TR * KS; e += 128) {
+            int rr = e / KS, kk = e % KS;
+            int r = r0 + rr, kq = k0 + kk;
+            sT[rr][kk] = (r < Pout && kq < Pin) ? __ldg(T + (int64_t)r * Pin + kq) : make_float2(0.f, 0.f);
         }
+        // X tile: rows k0 .. k0 + KS - 1 of the gathered source columns
+        for (int e = tid; e < KS * TC; e += 128) {
+            int cc = e / KS, kk = e % KS;
+            int kq = k0 + kk;
+            sX[kk][cc] =
+                (cc < ncol && kq < Pin) ? __ldg(coef + it.src + (int64_t)sc[cc].x * Pin + kq) : make_float2(0.f, 0.f);
+        }
+        __syncthreads();
+#pragma unroll 8
+        for (int kk = 0; kk < KS; ++kk) {
+            float2 a[4], b[4];
 #pragma unroll
-        for (int qa = 0; qa < 4; ++qa) {
-            int r = r0 + ty + 8 * qa;
-            if (r >= Pout) continue;
+            for (int q = 0; q < 4; ++q) {
+                a[q] = sT[ty + RG * q][kk];
+                b[q] = sX[kk][tx + CG * q];
+            }
 #pragma unroll
-            for (int qb = 0; qb < 4; ++qb) {
-                int cc = tx + 16 * qb;
-                if (cc >= ncol) continue;
-                float2* o = coef + it.dst + (int64_t)sc[cc].y * Pout + r;
-                if (it.atomic) {
-                    red_add(o, make_float2(accr[qa][qb], acci[qa][qb]));
-                } else {
-                    float2 v = *o;
-                    *o = make_float2(v.x + accr[qa][qb], v.y + acci[qa][qb]);
+            for (int qa = 0; qa < 4; ++qa)
+#pragma unroll
+                for (int qb = 0; qb < 4; ++qb) {
+                    accr[qa][qb] = fmaf(a[qa].x, b[qb].x, fmaf(-a[qa].y, b[qb].y, accr[qa][qb]));
+                    acci[qa][qb] = fmaf(a[qa].x, b[qb].y, fmaf(a[qa].y, b[qb].x, acci[qa][qb]));
                 }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int qa = 0; qa < 4; ++qa) {
+        int r = r0 + ty + RG * qa;
+        if (r >= Pout) continue;
+#pragma unroll
+        for (int qb = 0; qb < 4; ++qb) {
+            int cc = tx + CG * qb;
+            if (cc >= ncol) continue;
+            float2* o = coef + it.dst + (int64_t)sc[cc].y * Pout + r;
+            if (it.atomic) {
+                red_add(o, make_float2(accr[qa][qb], acci[qa][qb]));
+            } else {
+                float2 v = *o;
+                *o = make_float2(v.x + accr[qa][qb], v.y + acci[qa][qb]);
             }
         }
     }
@@ -668,11 +673,17 @@ void mark_stage(hfmm_plan* P, int q, cudaStream_t st) {
     if (P->stage_ev) HFMM_CUDA(cudaEventRecord(P->stage_ev[q], st));
 }
 
-// tiles: 32-row output tiles of the largest output order among the items [b, e)
-static void launch_translate(hfmm_plan* P, int64_t b, int64_t e, int tiles, cudaStream_t st) {
+// Items [b, e) of at most `width` columns (64, 16 or 8) and output order <= pout_max.
+static void launch_translate(hfmm_plan* P, int64_t b, int64_t e, int pout_max, int width, cudaStream_t st) {
     if (e <= b) return;
-    k_translate<<<dim3((unsigned)(e - b), (unsigned)tiles), 128, 0, st>>>(P->items.p, b, P->item_cols.p, P->ops.p,
-                                                                         P->coef.p);
+    const int rows = width >= 64 ? 32 : width >= 16 ? 128 : 256;
+    const dim3 grid((unsigned)(e - b), (unsigned)((pout_max + rows - 1) / rows));
+    if (width >= 64)
+        k_translate<16><<<grid, 128, 0, st>>>(P->items.p, b, P->item_cols.p, P->ops.p, P->coef.p);
+    else if (width >= 16)
+        k_translate<4><<<grid, 128, 0, st>>>(P->items.p, b, P->item_cols.p, P->ops.p, P->coef.p);
+    else
+        k_translate<2><<<grid, 128, 0, st>>>(P->items.p, b, P->item_cols.p, P->ops.p, P->coef.p);
     ++P->launches;
 }
 
@@ -732,13 +743,12 @@ void run_matvec_sorted(hfmm_plan* P, int parts, cudaStream_t st) {
                               P->coef.p, P->dev_err.p, st);
                 ++P->launches;
             } else {
-                launch_translate(P, P->m2m_items_begin[l], P->m2m_items_end[l], (P->lev[l].P + 31) / 32, st);
+                launch_translate(P, P->m2m_items_begin[l], P->m2m_items_end[l], P->lev[l].P, HFMM_TRANS_NB, st);
             }
         }
     mark_stage(P, 4, st);
     if (far) {
-        for (size_t q = 0; q < P->m2l_simt_ranges.size(); ++q)
-            launch_translate(P, P->m2l_simt_ranges[q].first, P->m2l_simt_ranges[q].second, P->m2l_simt_tiles[q], st);
+        for (const SimtRange& r : P->m2l_simt) launch_translate(P, r.begin, r.end, r.pout_max, r.width, st);
         if (P->n_tc_groups > 0) {
             m2l_tc_launch(P->tc_groups.p, P->n_tc_groups, P->items.p, P->item_cols.p, P->aops.p, P->coef.p,
                           P->dev_err.p, st);
@@ -754,7 +764,7 @@ void run_matvec_sorted(hfmm_plan* P, int parts, cudaStream_t st) {
                               P->coef.p, P->dev_err.p, st);
                 ++P->launches;
             } else {
-                launch_translate(P, P->l2l_items_begin[l], P->l2l_items_end[l], (P->lev[l].P + 31) / 32, st);
+                launch_translate(P, P->l2l_items_begin[l], P->l2l_items_end[l], P->lev[l].P, HFMM_TRANS_NB, st);
             }
         }
     mark_stage(P, 6, st);

@@ -76,6 +76,12 @@ struct TransItem {
     int16_t pad[2];
 };
 
+// A run of SIMT translation items of one column width (64, 16 or 8).
+struct SimtRange {
+    int64_t begin, end;
+    int pout_max, width;
+};
+
 struct LevelInfo {
     int p = 0, P = 0;       // order and (p+1)^2
     double s = 1.0;         // scale min(1, k a)
@@ -127,8 +133,7 @@ struct hfmm_plan {
     std::vector<int64_t> m2m_items_begin, m2m_items_end;  // per level l (parents at l)
     std::vector<int64_t> l2l_items_begin, l2l_items_end;  // per level l (children at l)
     int64_t m2l_items_begin = 0, m2l_items_end = 0;
-    std::vector<std::pair<int64_t, int64_t>> m2l_simt_ranges;  // M2L item ranges on the SIMT kernel
-    std::vector<int> m2l_simt_tiles;  // 32-row output tiles of the largest order in each range
+    std::vector<SimtRange> m2l_simt;  // M2L item ranges on the SIMT kernel
     DBuf<uint16_t> aops;       // tensor-core M2L operators (BF16 hi/lo, packed)
     DBuf<int4> tc_groups;      // (first item, item count, operator, P) per tensor-core block
     int64_t n_tc_groups = 0;   // the first n_tc_groups groups are M2L

@@ -91,16 +91,17 @@ struct PairBuckets {
 };
 
 void emit_items(const PairBuckets& pb, const std::vector<int64_t>& op_of_bucket, int64_t src, int64_t dst, int pin,
-                int pout, int atomic, std::vector<TransItem>& items, std::vector<int2>& cols) {
+                int pout, int atomic, std::vector<TransItem>& items, std::vector<int2>& cols,
+                int width = HFMM_TRANS_NB) {
     for (size_t g = 0; g < pb.b.size(); ++g) {
         const auto& v = pb.b[g];
-        for (size_t c0 = 0; c0 < v.size(); c0 += HFMM_TRANS_NB) {
+        for (size_t c0 = 0; c0 < v.size(); c0 += width) {
             TransItem it{};
             it.op = op_of_bucket[g];
             it.src = src;
             it.dst = dst;
             it.cols = (int32_t)cols.size();
-            it.ncol = (int16_t)std::min<size_t>(HFMM_TRANS_NB, v.size() - c0);
+            it.ncol = (int16_t)std::min<size_t>(width, v.size() - c0);
             it.pin = (int16_t)pin;
             it.pout = (int16_t)pout;
             it.atomic = (int16_t)atomic;
@@ -418,6 +419,7 @@ static void build_plan(hfmm_plan* P, const double* V, int64_t nv, const int32_t*
         P->m2l_items_begin = (int64_t)items.size();
         int64_t m2l_count = 0;
         std::vector<int64_t> lev_item_b(L + 1, 0), lev_item_e(L + 1, 0);
+        std::vector<int> lev_width(L + 1, HFMM_TRANS_NB);
         for (int l = 2; l <= L; ++l) {
             lev_item_b[l] = (int64_t)items.size();
             PairBuckets pb(316);
@@ -447,7 +449,19 @@ static void build_plan(hfmm_plan* P, const double* V, int64_t nv, const int32_t*
             }
             std::vector<int64_t> ops(316);
             for (int o = 0; o < 316; ++o) ops[o] = P->lev[l].m2l_op + (int64_t)o * P->lev[l].P * P->lev[l].P;
-            emit_items(pb, ops, P->lev[l].mofs, P->lev[l].lofs, P->lev[l].P, P->lev[l].P, 1, items, cols);
+            // SIMT levels with few targets per offset (the coarse ones) take narrow items
+            int width = HFMM_TRANS_NB;
+            if (!(cfg.m2l_tensor && P->lev[l].P <= 64)) {
+                int64_t busy = 0, pairs = 0;
+                for (const auto& v : pb.b) {
+                    busy += !v.empty();
+                    pairs += (int64_t)v.size();
+                }
+                const int64_t mean = busy ? pairs / busy : 0;
+                width = mean <= 12 ? 8 : mean <= 28 ? 16 : HFMM_TRANS_NB;
+            }
+            lev_width[l] = width;
+            emit_items(pb, ops, P->lev[l].mofs, P->lev[l].lofs, P->lev[l].P, P->lev[l].P, 1, items, cols, width);
             lev_item_e[l] = (int64_t)items.size();
         }
         P->m2l_items_end = (int64_t)items.size();
@@ -517,13 +531,12 @@ static void build_plan(hfmm_plan* P, const double* V, int64_t nv, const int32_t*
         };
         for (int l = 2; l <= L; ++l) {
             if (m2l_base[l] < 0) {
-                const int tiles = (P->lev[l].P + 31) / 32;
-                if (!P->m2l_simt_ranges.empty() && P->m2l_simt_ranges.back().second == lev_item_b[l]) {
-                    P->m2l_simt_ranges.back().second = lev_item_e[l];
-                    P->m2l_simt_tiles.back() = std::max(P->m2l_simt_tiles.back(), tiles);
+                auto& R = P->m2l_simt;
+                if (!R.empty() && R.back().end == lev_item_b[l] && R.back().width == lev_width[l]) {
+                    R.back().end = lev_item_e[l];
+                    R.back().pout_max = std::max(R.back().pout_max, P->lev[l].P);
                 } else {
-                    P->m2l_simt_ranges.push_back({lev_item_b[l], lev_item_e[l]});
-                    P->m2l_simt_tiles.push_back(tiles);
+                    R.push_back({lev_item_b[l], lev_item_e[l], P->lev[l].P, lev_width[l]});
                 }
                 continue;
             }
