@@ -140,6 +140,13 @@ __global__ void __launch_bounds__(256) k_p2p(int64_t ntiles, const int4* __restr
 // first (its entries are the targets themselves).  Warp w handles target tiles
 // w, w+4, ...; within a tile each target is shared by kP2PSub lanes.  The self
 // segment carries the j != i mask and the u = 0 guard; the rest runs unmasked.
+// hardware reciprocal square root; its inputs are normal numbers (distinct points, or the guard)
+__device__ __forceinline__ float rsqrt_ftz(float x) {
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 template <bool POLY, bool MASK>
 __device__ __forceinline__ void p2p_span(float tx, float ty, float tz, int k0, int k1, int self_k,
                                          const float4* __restrict__ sp, const float* __restrict__ sim,
@@ -153,7 +160,7 @@ __device__ __forceinline__ void p2p_span(float tx, float ty, float tz, int k0, i
         if (MASK && k == self_k) sr = si = 0.f;
         const float dx = tx - q.x, dy = ty - q.y, dz = tz - q.z;
         const float u = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-        const float rinv = MASK ? rsqrtf(fmaxf(u, 1e-30f)) : rsqrtf(u);
+        const float rinv = rsqrt_ftz(MASK ? fmaxf(u, 1e-30f) : u);
         float re, im;
         if (POLY) {
             re = horner<HFMM_POLY_C_DEG>(kC, u) * rinv;
