@@ -15,6 +15,14 @@
 // offset grouped in a block, held in tensor memory (written once with
 // tcgen05.st); B is gathered from the multipole array, split on the fly and
 // staged in shared memory in the K-major no-swizzle (core-matrix) layout.
+//
+// Roles per block: producer warps gather and split B; one thread issues the
+// MMAs; four epilogue warps move each accumulator from tensor memory into one
+// of several shared-memory output stages; two issuer warps add the staged
+// expansions into global memory with bulk-copy reductions (a run of
+// consecutive destination boxes is one contiguous reduction).  The issuers are
+// decoupled from the epilogue so that the bulk-copy engine, whose per-operation
+// cost bounds the output, stays busy while the next accumulator drains.
 #include <cuda_bf16.h>
 
 #include "hfmm_internal.cuh"
@@ -30,7 +38,6 @@ constexpr int kKc = kK / 8;    // core matrices along K
 constexpr uint32_t kCoreBytes = 128;                 // 8 rows x 16 bytes
 constexpr uint32_t kSBO = kKc * kCoreBytes;          // next 8-row group
 constexpr uint32_t kLBO = kCoreBytes;                // next 8-element K group
-constexpr uint32_t kABytes = kM * kK * 2;            // 32 KiB per BF16 part
 constexpr uint32_t kBBytes = kN * kK * 2;            // 16 KiB per BF16 part
 constexpr uint32_t kTmemCols = 64;    // one accumulator (N = 64 FP32 columns)
 constexpr uint32_t kTmemA = 128;      // A hi (64 columns) and lo (64 columns): 128 x 128 BF16 each
@@ -57,16 +64,6 @@ __device__ __forceinline__ uint64_t umma_desc(uint32_t addr) {
 // kind::f16 instruction descriptor: D f32, A/B bf16, both K-major, N = 64, M = 128
 constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kN >> 3) << 17) |
                             ((uint32_t)(kM >> 4) << 24);
-
-__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t accumulate) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n"
-        :
-        : "r"(tmem_d), "l"(a), "l"(b), "r"(kIdesc), "r"(accumulate)
-        : "memory");
-}
 
 __device__ __forceinline__ void mma_bf16_ta(uint32_t tmem_d, uint32_t tmem_a, uint64_t b, uint32_t accumulate) {
     asm volatile(
@@ -103,19 +100,6 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t addr, uint32_t parity) {
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
-    uint32_t r[16];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-        "%15}, [%16];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int q = 0; q < 16; ++q) v[q] = __uint_as_float(r[q]);
-}
 
 // 64 consecutive columns of this thread's lane: four loads in flight, one wait
 __device__ __forceinline__ void tmem_ld64(uint32_t taddr, float (&v)[64]) {
@@ -163,11 +147,15 @@ __global__ void k_m2l_tc_pack(const float2* __restrict__ T, int P, int nops, __n
 }
 
 constexpr int kStages = 2;         // B stages and TMEM accumulators in flight
+constexpr int kOutStages = 4;      // shared-memory output stages (epilogue -> issuers)
+constexpr int kIssuers = 2;        // output-issuing warps; issuer q takes items q, q + 2, ...
 constexpr int kMaxGroup = 32;      // work items per block (one operator)
 constexpr int kProducers = 256;    // threads gathering B (warps 4..11)
 constexpr int kEpilogue = 128;     // threads draining TMEM (warps 0..3, one per TMEM lane quarter)
 constexpr int kMmaWarp = (kEpilogue + kProducers) / 32;  // TMEM owner and MMA issuer
-constexpr int kThreads = kEpilogue + kProducers + 32;
+constexpr int kIssuerWarp = kMmaWarp + 1;                // first output-issuing warp
+constexpr int kThreads = kEpilogue + kProducers + 32 + 32 * kIssuers;
+static_assert(kOutStages == 2 * kIssuers, "each issuer cycles through two output stages");
 
 struct TcSmem {
     __nv_bfloat16 b[kStages][2][kN * kK];   // gathered multipoles: hi, lo per stage
@@ -175,7 +163,9 @@ struct TcSmem {
     uint64_t empty[kStages];                // MMA done reading the stage
     uint64_t tfull[kStages];                // accumulator ready
     uint64_t tempty[kStages];               // epilogue done reading the accumulator
-    float stage[kStages][kN][kM];           // accumulator columns = target expansions (Re/Im interleaved)
+    uint64_t staged[kOutStages];            // epilogue -> issuer: output stage written
+    uint64_t sfree[kOutStages];             // issuer -> epilogue: stage read by the bulk engine
+    float stage[kOutStages][kN][kM];        // accumulator columns = target expansions (Re/Im interleaved)
     TransItem items[kMaxGroup];             // the group's work items
     int2 cols[kMaxGroup][kN];               // their (source, destination) columns
     uint32_t tmem;
@@ -244,6 +234,10 @@ __global__ void __launch_bounds__(kThreads, 1)
             mbar_init(smem_u32(&S.empty[q]), 1);
             mbar_init(smem_u32(&S.tfull[q]), 1);
             mbar_init(smem_u32(&S.tempty[q]), kEpilogue);
+        }
+        for (int q = 0; q < kOutStages; ++q) {
+            mbar_init(smem_u32(&S.staged[q]), kEpilogue);
+            mbar_init(smem_u32(&S.sfree[q]), 1);
         }
         S.abort = 0;
     }
@@ -409,6 +403,51 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
         }
         __syncwarp();
+    } else if (warp >= kIssuerWarp) {
+        // ---------------------------------------------------------------- output issuers
+        // Lane l handles columns l and l + 32 of its items; the first column of a run of
+        // consecutive destination boxes adds the whole run (one contiguous block in both
+        // the stage and the expansion array when 2P = kM).  Bulk groups are per thread:
+        // every lane commits one group per item and confirms the reads of its previous
+        // item before that item's stage is handed back.
+        const int q = warp - kIssuerWarp;
+        int prev = -1;
+        if ((P & 1) == 0) {
+            for (int w = q; w < nitems; w += kIssuers) {
+                const int o = w % kOutStages;
+                const uint32_t po = (uint32_t)(w / kOutStages) & 1u;
+                bool ok = true;
+                if (lane == 0) ok = wait_or_abort(smem_u32(&S.staged[o]), po, abort, err);
+                if (!__shfl_sync(0xffffffffu, (int)ok, 0)) break;
+                const TransItem& it = S.items[w];
+                const int ncol = it.ncol;
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int c = lane + 32 * h;
+                    if (c >= ncol) continue;
+                    const int dc = S.cols[w][c].y;
+                    uint32_t bytes = 8u * (uint32_t)P;
+                    if (2 * P == kM) {
+                        if (c > 0 && S.cols[w][c - 1].y == dc - 1) continue;  // inside a run
+                        int run = 1;
+                        while (c + run < ncol && S.cols[w][c + run].y == dc + run) ++run;
+                        bytes *= (uint32_t)run;
+                    }
+                    asm volatile("cp.reduce.async.bulk.global.shared::cta.bulk_group.add.f32 [%0], [%1], %2;" ::"l"(
+                                     coef + it.dst + (int64_t)dc * P),
+                                 "r"(smem_u32(&S.stage[o][c][0])), "r"(bytes)
+                                 : "memory");
+                }
+                asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+                if (prev >= 0) {
+                    asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");  // prev's stage read
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(smem_u32(&S.sfree[prev % kOutStages]));
+                }
+                prev = w;
+            }
+        }
+        asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");  // every reduction landed
     } else {
         // ---------------------------------------------------------------- epilogue (warps 0..3)
         const int r = tid;  // TMEM lane = row of D
@@ -427,34 +466,18 @@ __global__ void __launch_bounds__(kThreads, 1)
             tmem_ld64(base, v);
             if ((P & 1) == 0) {
                 // Column c of D, rows 0..2P-1, is the 8P-byte image of the target expansion
-                // L[dst_c] (Re, Im interleaved): stage it and let the bulk-copy engine add it.
-                if (r < kN) asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");  // stage[s] free
-                asm volatile("bar.sync 2, 128;" ::: "memory");
-#pragma unroll
-                for (int c = 0; c < kN; ++c) S.stage[s][c][r] = v[c];
-                fence_async_smem();
+                // L[dst_c] (Re, Im interleaved): free the accumulator, stage the columns for
+                // the issuer warps
                 tc_fence_before();
-                mbar_arrive(smem_u32(&S.tempty[s]));  // accumulator drained
-                asm volatile("bar.sync 2, 128;" ::: "memory");
-                if (r < ncol && 2 * P == kM) {
-                    // a run of consecutive destination boxes is one contiguous block in both
-                    // the stage and the expansion array: the run's first column adds it all
-                    const int dc = S.cols[w][r].y;
-                    if (r == 0 || S.cols[w][r - 1].y != dc - 1) {
-                        int run = 1;
-                        while (r + run < ncol && S.cols[w][r + run].y == dc + run) ++run;
-                        float2* dst = coef + it.dst + (int64_t)dc * P;
-                        asm volatile("cp.reduce.async.bulk.global.shared::cta.bulk_group.add.f32 [%0], [%1], %2;" ::"l"(dst),
-                                     "r"(smem_u32(&S.stage[s][r][0])), "r"(8 * P * run)
-                                     : "memory");
-                    }
-                } else if (r < ncol) {
-                    float2* dst = coef + it.dst + (int64_t)S.cols[w][r].y * P;
-                    asm volatile("cp.reduce.async.bulk.global.shared::cta.bulk_group.add.f32 [%0], [%1], %2;" ::"l"(dst),
-                                 "r"(smem_u32(&S.stage[s][r][0])), "r"(8 * P)
-                                 : "memory");
-                }
-                if (r < kN) asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+                mbar_arrive(smem_u32(&S.tempty[s]));  // accumulator drained: it is in v[]
+                const int o = w % kOutStages;
+                const uint32_t po = (uint32_t)(w / kOutStages) & 1u;
+                const bool fr = wait_or_abort(smem_u32(&S.sfree[o]), po ^ 1u, abort, err);
+                if (!epilogue_all(fr)) break;
+#pragma unroll
+                for (int c = 0; c < kN; ++c) S.stage[o][c][r] = v[c];
+                fence_async_smem();
+                mbar_arrive(smem_u32(&S.staged[o]));
                 continue;
             }
             // odd P: per-lane reductions.  Column pairs (c, c+1): the even lane (Re row) sends
@@ -473,7 +496,6 @@ __global__ void __launch_bounds__(kThreads, 1)
             tc_fence_before();
             mbar_arrive(smem_u32(&S.tempty[s]));
         }
-        if (r < kN) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");  // bulk reductions landed
     }
     tc_fence_before();
     __syncthreads();
