@@ -34,6 +34,28 @@ WORKLOADS = {
 }
 
 
+def _m2l_traffic(translations):
+    """DRAM bytes of one tensor-core M2L launch, from the committed ncu summary of that kernel
+    (bytes per translation on a smaller case, scaled by this launch's translations); None when
+    the kernel source has changed since the capture."""
+    import hashlib
+
+    src = os.path.join(ROOT, "paper_1803_09948_gb300", "csrc", "m2l_tc.cu")
+    prof = os.path.join(ROOT, "profiles", "k_m2l_tc_sphere_163840.md")
+    try:
+        with open(prof) as f:
+            kv = dict(line.strip().split(" = ", 1) for line in f if " = " in line and line.startswith("    "))
+        with open(src, "rb") as f:
+            sha = hashlib.sha256(f.read()).hexdigest()[:16]
+        if sha != kv["kernel_source_sha256_16"]:
+            return None, "kernel changed since the ncu capture"
+        per = float(kv["dram_bytes_per_translation"])
+        return per * translations, (f"ncu dram__bytes_read+write on sphere_163840 ({per:.1f} B per translation), "
+                                    f"scaled to {int(translations)} translations")
+    except (OSError, KeyError, ValueError):
+        return None, "no ncu capture"
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -293,23 +315,29 @@ def main():
     props = torch.cuda.get_device_properties(local)
     fp32_peak = props.multi_processor_count * 128 * 2 * smax * 1e6 / 1e12  # TFLOP/s
     dom = max(stages, key=stages.get)
+    tc_cmacs = costs["m2l_tc_cmacs"]
     work = {
         "p2p": ("alu", costs["p2p_pairs"] * 24 / 1e12, "TFLOP/s", fp32_peak, "24 flop per source-target pair"),
-        "m2l": ("alu", costs["m2l_cmacs"] * 8 / 1e12, "TFLOP/s", fp32_peak, "8 flop per complex multiply-add")
-        if args.simt else
-        ("tensor", costs["m2l_cmacs"] * 8 * 3 / 1e12, "TFLOP/s", bf16_peak,
-         "8 flop per complex multiply-add x 3 BF16 products (hi*hi, hi*lo, lo*hi)"),
+        "m2l_simt": ("alu", (costs["m2l_cmacs"] - tc_cmacs) * 8 / 1e12, "TFLOP/s", fp32_peak,
+                     "8 flop per complex multiply-add, P_l^2 per translation (SIMT levels)"),
+        "m2l": ("tensor", tc_cmacs * 8 * 3 / 1e12, "TFLOP/s", bf16_peak,
+                "real-form contraction, 8 flop per complex multiply-add (P^2 per translation) x 3 BF16 "
+                "products (hi*hi, hi*lo, lo*hi); "
+                f"{int(costs['m2l_tc_translations'])} translations per launch"),
         "m2m": ("alu", costs["m2m_l2l_cmacs"] * 4 / 1e12, "TFLOP/s", fp32_peak, "M2M half of the M2M+L2L work"),
         "l2l": ("alu", costs["m2m_l2l_cmacs"] * 4 / 1e12, "TFLOP/s", fp32_peak, "L2L half of the M2M+L2L work"),
         "corr": ("hbm", (costs["corr_nnz"] * 12 + costs["n_points"] * 16) / 1e9, "GB/s", hbm,
                  "12 B per nonzero + 16 B per row"),
     }
     rl = None
+    traffic, traffic_note = None, None
+    if dom == "m2l":
+        traffic, traffic_note = _m2l_traffic(costs["m2l_tc_translations"])
     if dom in work:
         bound, amount, unit, peak, note = work[dom]
         achieved = amount / (stages[dom] / 1e3)
         rl = {"kernel": dom, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
-              "frac": achieved / peak, "traffic": None,
+              "frac": achieved / peak, "traffic": traffic, "traffic_source": traffic_note,
               "peak_source": (f"FP32: {props.multi_processor_count} SMs x 128 lanes x 2 flop x {smax:.0f} MHz"
                               if bound == "alu" else
                               (f"dense BF16 cuBLAS burst, {peak_src}" if bound == "tensor"

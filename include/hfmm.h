@@ -159,18 +159,23 @@ int hfmm_solve(hfmm_plan* plan, const void* rhs, void* x_out, int nrhs, int* ite
 
 /*
  * hfmm_matvec for one right-hand side with CUDA events recorded on `stream`
- * between the stages; returns after completion.  stage_ms (HOST, 9 floats)
- * receives the device time of: 0 density prep, 1 near field (P2P), 2 P2M,
- * 3 M2M, 4 M2L, 5 L2L, 6 L2P, 7 correction, 8 output permutation.
+ * between the stages; returns after completion.  stage_ms (HOST,
+ * HFMM_NUM_STAGES floats) receives the device time of: 0 density prep, 1 near
+ * field (P2P), 2 P2M, 3 M2M, 4 M2L on the FP32 SIMT kernel (levels above the
+ * tensor-core order limit, or every level when m2l_tensor = 0), 5 M2L on the
+ * tensor cores, 6 L2L, 7 L2P, 8 correction, 9 output permutation.
  */
+#define HFMM_NUM_STAGES 10
 int hfmm_matvec_timed(hfmm_plan* plan, const void* density, void* potential, float* stage_ms,
                       void* stream);
 
 /*
- * Algorithmic work of one matvec (HOST, 6 doubles): 0 near-field source-target
+ * Algorithmic work of one matvec (HOST, 8 doubles): 0 near-field source-target
  * pairs (j != i), 1 M2L complex multiply-adds (sum over translations of
  * P_l^2), 2 M2M + L2L complex multiply-adds, 3 correction nonzeros,
- * 4 points N, 5 expansion coefficients (all levels, multipoles + locals).
+ * 4 points N, 5 expansion coefficients (all levels, multipoles + locals),
+ * 6 the part of 1 done on the tensor cores, 7 the number of M2L translations
+ * done on the tensor cores.
  */
 int hfmm_plan_costs(const hfmm_plan* plan, double* costs);
 

@@ -32,7 +32,7 @@ EXPORTED = [
     "hfmm_plan_costs", "hfmm_point_sum_noalloc", "hfmm_device_status",
 ]
 HFMM_NOALLOC_MAX_POINTS = 262144
-STAGES = ["prep", "p2p", "p2m", "m2m", "m2l", "l2l", "l2p", "corr", "output"]
+STAGES = ["prep", "p2p", "p2m", "m2m", "m2l_simt", "m2l", "l2l", "l2p", "corr", "output"]
 
 
 class hfmm_config(ctypes.Structure):
@@ -215,15 +215,16 @@ def hfmm_matvec_timed(plan, density, potential, stream=None):
     n = hfmm_num_points(plan)
     _vec(density, n, 1, "density")
     _vec(potential, n, 1, "potential")
-    ms = (ctypes.c_float * 9)()
+    ms = (ctypes.c_float * len(STAGES))()
     _check(lib().hfmm_matvec_timed(plan, _ptr(density), _ptr(potential), ms, _stream(stream)), "hfmm_matvec_timed")
     return dict(zip(STAGES, [float(v) for v in ms]))
 
 
 def hfmm_plan_costs(plan):
-    c = (ctypes.c_double * 6)()
+    keys = ["p2p_pairs", "m2l_cmacs", "m2m_l2l_cmacs", "corr_nnz", "n_points", "coefficients", "m2l_tc_cmacs",
+            "m2l_tc_translations"]
+    c = (ctypes.c_double * len(keys))()
     _check(lib().hfmm_plan_costs(plan, c), "hfmm_plan_costs")
-    keys = ["p2p_pairs", "m2l_cmacs", "m2m_l2l_cmacs", "corr_nnz", "n_points", "coefficients"]
     return dict(zip(keys, [float(v) for v in c]))
 
 

@@ -507,7 +507,7 @@ __global__ void __launch_bounds__(128) k_translate(const TransItem* __restrict__
                                                    float2* __restrict__ coef) {
     constexpr int RG = 128 / CG;             // row groups
     constexpr int TR = 4 * RG, TC = 4 * CG;  // tile rows, tile columns
-    constexpr int KS = TR > 128 ? 16 : 32;   // K slice (T tile <= 32 KiB)
+    constexpr int KS = TR >= 128 ? 2048 / TR : 32;  // K slice: <= 16 T elements per thread
     __shared__ float2 sT[TR][KS + 1];
     __shared__ float2 sX[KS][TC + 1];
     __shared__ int2 sc[TC];
@@ -525,21 +525,39 @@ __global__ void __launch_bounds__(128) k_translate(const TransItem* __restrict__
     for (int a = 0; a < 4; ++a)
 #pragma unroll
         for (int b = 0; b < 4; ++b) accr[a][b] = acci[a][b] = 0.f;
-    for (int k0 = 0; k0 < Pin; k0 += KS) {
-        // T tile: rows r0 .. r0 + TR - 1, columns k0 .. k0 + KS - 1
-        for (int e = tid; e < TR * KS; e += 128) {
-            int rr = e / KS, kk = e % KS;
-            int r = r0 + rr, kq = k0 + kk;
-            sT[rr][kk] = (r < Pout && kq < Pin) ? __ldg(T + (int64_t)r * Pin + kq) : make_float2(0.f, 0.f);
+    // A slice's tiles pass through registers: every load of the next slice is issued
+    // before the current slice is multiplied, so the loads overlap the arithmetic.
+    constexpr int NT = TR * KS / 128, NX = (KS * TC + 127) / 128;
+    float2 rT[NT], rX[NX];
+    auto fetch = [&](int k0) {
+#pragma unroll
+        for (int q = 0; q < NT; ++q) {
+            const int e = tid + 128 * q, rr = e / KS, kk = e % KS;
+            const int r = r0 + rr, kq = k0 + kk;
+            rT[q] = (r < Pout && kq < Pin) ? __ldg(T + (int64_t)r * Pin + kq) : make_float2(0.f, 0.f);
         }
-        // X tile: rows k0 .. k0 + KS - 1 of the gathered source columns
-        for (int e = tid; e < KS * TC; e += 128) {
-            int cc = e / KS, kk = e % KS;
-            int kq = k0 + kk;
-            sX[kk][cc] =
-                (cc < ncol && kq < Pin) ? __ldg(coef + it.src + (int64_t)sc[cc].x * Pin + kq) : make_float2(0.f, 0.f);
+#pragma unroll
+        for (int q = 0; q < NX; ++q) {
+            const int e = tid + 128 * q, cc = e / KS, kk = e % KS;
+            const int kq = k0 + kk;
+            rX[q] = (e < KS * TC && cc < ncol && kq < Pin) ? __ldg(coef + it.src + (int64_t)sc[cc].x * Pin + kq)
+                                                           : make_float2(0.f, 0.f);
+        }
+    };
+    fetch(0);
+    for (int k0 = 0; k0 < Pin; k0 += KS) {
+#pragma unroll
+        for (int q = 0; q < NT; ++q) {
+            const int e = tid + 128 * q;
+            sT[e / KS][e % KS] = rT[q];
+        }
+#pragma unroll
+        for (int q = 0; q < NX; ++q) {
+            const int e = tid + 128 * q;
+            if (e < KS * TC) sX[e % KS][e / KS] = rX[q];
         }
         __syncthreads();
+        if (k0 + KS < Pin) fetch(k0 + KS);
 #pragma unroll 8
         for (int kk = 0; kk < KS; ++kk) {
             float2 a[4], b[4];
@@ -754,15 +772,17 @@ void run_matvec_sorted(hfmm_plan* P, int parts, cudaStream_t st) {
             }
         }
     mark_stage(P, 4, st);
-    if (far) {
+    if (far)
         for (const SimtRange& r : P->m2l_simt) launch_translate(P, r.begin, r.end, r.pout_max, r.width, st);
+    mark_stage(P, 5, st);
+    if (far) {
         if (P->n_tc_groups > 0) {
             m2l_tc_launch(P->tc_groups.p, P->n_tc_groups, P->items.p, P->item_cols.p, P->aops.p, P->coef.p,
                           P->dev_err.p, st);
             ++P->launches;
         }
     }
-    mark_stage(P, 5, st);
+    mark_stage(P, 6, st);
     if (far)
         for (int l = 3; l <= L; ++l) {
             const auto& g = P->l2l_tc[l];
@@ -774,18 +794,18 @@ void run_matvec_sorted(hfmm_plan* P, int parts, cudaStream_t st) {
                 launch_translate(P, P->l2l_items_begin[l], P->l2l_items_end[l], P->lev[l].P, HFMM_TRANS_NB, st);
             }
         }
-    mark_stage(P, 6, st);
+    mark_stage(P, 7, st);
     if (far) {
         const LevelInfo& lv = P->lev[L];
         k_l2p<<<(unsigned)((N + 127) / 128), 128, 0, st>>>(N, P->pt_leaf.p, P->pts.p, lv.p, (float)lv.s,
                                                            P->coef.p + lv.lofs, P->phi.p);
         ++P->launches;
     }
-    mark_stage(P, 7, st);
+    mark_stage(P, 8, st);
     if ((parts & 4) && P->corr_nnz > 0) {
         launch_corr(P, st);
     }
-    mark_stage(P, 8, st);
+    mark_stage(P, 9, st);
     HFMM_CUDA(cudaGetLastError());
 }
 

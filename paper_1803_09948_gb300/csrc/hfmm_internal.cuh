@@ -151,7 +151,7 @@ struct hfmm_plan {
     DBuf<double> gred;         // reduction scratch
     int kry_m = 0;
     int64_t launches = 0;       // kernels launched by this plan
-    double cost[6] = {0, 0, 0, 0, 0, 0};  // see hfmm_plan_costs
+    double cost[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // see hfmm_plan_costs
     cudaEvent_t* stage_ev = nullptr;  // set by hfmm_matvec_timed: events after each stage
 };
 

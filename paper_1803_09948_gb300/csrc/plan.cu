@@ -420,6 +420,7 @@ static void build_plan(hfmm_plan* P, const double* V, int64_t nv, const int32_t*
         int64_t m2l_count = 0;
         std::vector<int64_t> lev_item_b(L + 1, 0), lev_item_e(L + 1, 0);
         std::vector<int> lev_width(L + 1, HFMM_TRANS_NB);
+        std::vector<int64_t> lev_pairs(L + 1, 0);
         for (int l = 2; l <= L; ++l) {
             lev_item_b[l] = (int64_t)items.size();
             PairBuckets pb(316);
@@ -443,6 +444,7 @@ static void build_plan(hfmm_plan* P, const double* V, int64_t nv, const int32_t*
                                 int sl = slot[(dx + 3) * 49 + (dy + 3) * 7 + (dz + 3)];
                                 pb.b[sl].push_back(make_int2((int)s, (int)t));
                                 ++m2l_count;
+                                ++lev_pairs[l];
                                 P->cost[1] += (double)P->lev[l].P * P->lev[l].P;
                             }
                         }
@@ -530,6 +532,10 @@ static void build_plan(hfmm_plan* P, const double* V, int64_t nv, const int32_t*
             }
         };
         for (int l = 2; l <= L; ++l) {
+            if (m2l_base[l] >= 0) {
+                P->cost[6] += (double)lev_pairs[l] * P->lev[l].P * P->lev[l].P;
+                P->cost[7] += (double)lev_pairs[l];
+            }
             if (m2l_base[l] < 0) {
                 auto& R = P->m2l_simt;
                 if (!R.empty() && R.back().end == lev_item_b[l] && R.back().width == lev_width[l]) {
@@ -729,7 +735,7 @@ int hfmm_matvec(hfmm_plan* P, const void* density, void* potential, int nrhs, vo
 
 int hfmm_matvec_timed(hfmm_plan* P, const void* density, void* potential, float* stage_ms, void* stream) {
     if (!P || !density || !potential || !stage_ms) return HFMM_E_INVALID;
-    cudaEvent_t ev[10] = {};
+    cudaEvent_t ev[HFMM_NUM_STAGES + 1] = {};
     HFMM_GUARD_BEGIN
     cudaStream_t st = (cudaStream_t)stream;
     struct Cleanup {
@@ -737,19 +743,19 @@ int hfmm_matvec_timed(hfmm_plan* P, const void* density, void* potential, float*
         cudaEvent_t* ev;
         ~Cleanup() {
             P->stage_ev = nullptr;
-            for (int q = 0; q < 10; ++q)
+            for (int q = 0; q <= HFMM_NUM_STAGES; ++q)
                 if (ev[q]) cudaEventDestroy(ev[q]);
         }
     } cleanup{P, ev};
-    for (int q = 0; q < 10; ++q) HFMM_CUDA(cudaEventCreate(&ev[q]));
+    for (int q = 0; q <= HFMM_NUM_STAGES; ++q) HFMM_CUDA(cudaEventCreate(&ev[q]));
     P->stage_ev = ev;
     mark_stage(P, 0, st);
     launch_density_prep(P, density, false, P->sig.p, st);
     run_matvec_sorted(P, 7, st);
     launch_output(P, P->phi.p, potential, false, st);
-    mark_stage(P, 9, st);
-    HFMM_CUDA(cudaEventSynchronize(ev[9]));
-    for (int q = 0; q < 9; ++q) HFMM_CUDA(cudaEventElapsedTime(&stage_ms[q], ev[q], ev[q + 1]));
+    mark_stage(P, HFMM_NUM_STAGES, st);
+    HFMM_CUDA(cudaEventSynchronize(ev[HFMM_NUM_STAGES]));
+    for (int q = 0; q < HFMM_NUM_STAGES; ++q) HFMM_CUDA(cudaEventElapsedTime(&stage_ms[q], ev[q], ev[q + 1]));
     return HFMM_OK;
     HFMM_GUARD_END
 }
@@ -774,7 +780,7 @@ int hfmm_device_status(hfmm_plan* P, void* stream) {
 
 int hfmm_plan_costs(const hfmm_plan* P, double* costs) {
     if (!P || !costs) return HFMM_E_INVALID;
-    for (int q = 0; q < 6; ++q) costs[q] = P->cost[q];
+    for (int q = 0; q < 8; ++q) costs[q] = P->cost[q];
     return HFMM_OK;
 }
 
