@@ -145,8 +145,11 @@ int hfmm_rhs_planewave(hfmm_plan* plan, const double* dirs, int nrhs, void* rhs_
 
 /*
  * Solves Z x = rhs by restarted GMRES(m) (the paper's solver, Sec. 5.1 and
- * 6.4) with FP64 Krylov basis, Gram-Schmidt (two classical passes), Givens
- * rotations and residual tests, and the FP32 FMM matvec.  x0 = 0.  Stops when
+ * 6.4) with the FP32 FMM matvec.  The Krylov basis and the element-wise
+ * Arnoldi arithmetic (Gram-Schmidt, two classical passes; norms; updates) are
+ * FP64-class double-float (hi + lo FP32 pairs, 48-bit significand, error-free
+ * transformations); partial sums, the Hessenberg matrix, Givens rotations,
+ * the least-squares solve and the residual tests are FP64.  x0 = 0.  Stops when
  * the relative residual reaches cfg->tol (checked on the true residual at
  * exit).  rhs, x_out: device complex64, N x nrhs (right-hand sides solved one
  * after another).  iters_out / relres_out (HOST, nrhs entries each, may be

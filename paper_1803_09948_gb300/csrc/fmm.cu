@@ -32,25 +32,25 @@ __global__ void k_output(int64_t N, const int32_t* __restrict__ perm, const floa
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     float2 v = phi[i];
-    T o;
+    T o{};  // a double-float output (float4) gets zero low parts
     o.x = v.x;
     o.y = v.y;
     out[perm[i]] = o;
 }
 
-void launch_density_prep(hfmm_plan* P, const void* density, bool fp64, float2* sig, cudaStream_t st) {
+void launch_density_prep(hfmm_plan* P, const void* density, VecKind kind, float2* sig, cudaStream_t st) {
     ++P->launches;
     unsigned nb = (unsigned)((P->N + 255) / 256);
-    if (fp64)
-        k_density_prep<double2><<<nb, 256, 0, st>>>(P->N, P->perm.p, P->wscale.p, (const double2*)density, sig);
+    if (kind == VecKind::DoubleFloat)  // (re_hi, im_hi, re_lo, im_lo): the FP32 value is the high part
+        k_density_prep<float4><<<nb, 256, 0, st>>>(P->N, P->perm.p, P->wscale.p, (const float4*)density, sig);
     else
         k_density_prep<float2><<<nb, 256, 0, st>>>(P->N, P->perm.p, P->wscale.p, (const float2*)density, sig);
 }
 
-void launch_output(hfmm_plan* P, const float2* phi, void* out, bool fp64, cudaStream_t st) {
+void launch_output(hfmm_plan* P, const float2* phi, void* out, VecKind kind, cudaStream_t st) {
     ++P->launches;
     unsigned nb = (unsigned)((P->N + 255) / 256);
-    if (fp64) k_output<double2><<<nb, 256, 0, st>>>(P->N, P->perm.p, phi, (double2*)out);
+    if (kind == VecKind::DoubleFloat) k_output<float4><<<nb, 256, 0, st>>>(P->N, P->perm.p, phi, (float4*)out);
     else k_output<float2><<<nb, 256, 0, st>>>(P->N, P->perm.p, phi, (float2*)out);
 }
 

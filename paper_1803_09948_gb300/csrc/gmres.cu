@@ -1,10 +1,21 @@
 // Restarted GMRES(m) on the device (the paper's solver: GMRES with the FMM as
 // the matvec, exit at a relative residual of 1e-4; Sec. 1, 5.1, 6.4).
 //
-// Krylov basis, Gram-Schmidt (two classical passes), norms and the solution
-// update run in FP64 on the GPU; the matvec is the FP32 FMM.  The (m+1) x m
-// Hessenberg matrix and its Givens rotations live on the host: one small
-// device-to-host copy per iteration.
+// Precision.  The Krylov basis, the work vector, the iterate and the
+// right-hand side are double-float complex vectors: each real value is an
+// unevaluated sum hi + lo of two FP32 numbers (48-bit significand), stored as
+// float4 (re_hi, im_hi, re_lo, im_lo), the same 16 bytes per element as FP64
+// complex.  The element-wise Arnoldi work (Gram-Schmidt inner products and
+// updates, norms, scaling, the solution update) runs on the FP32 pipe with
+// error-free transformations: the exact product error of an FMA (TwoProd),
+// Knuth's TwoSum, and the compensated dot product of Ogita, Rump and Oishi
+// (Dot2), which returns a sum as accurate as if it were accumulated in twice
+// the working precision.  This keeps the orthogonalisation FP64-class
+// (relative errors near 2^-48) while the FP32 pipe, about 70 times faster than
+// this GPU's FP64 pipe, leaves the kernels bound by HBM.  Per-block partial
+// sums are combined in FP64; the (m+1) x m Hessenberg matrix, its Givens
+// rotations and the triangular solve live on the host in FP64, with one small
+// device-to-host copy per Gram-Schmidt pass.  The matvec is the FP32 FMM.
 #include <cmath>
 #include <complex>
 #include <vector>
@@ -17,25 +28,90 @@ using cd = std::complex<double>;
 
 static constexpr int RB = 256;  // threads per reduction block
 static constexpr int RG = 296;  // reduction blocks per vector (2 per SM)
+static constexpr int kDotVecs = 8;  // basis vectors per inner-product block (w is read once per 8)
 
-__global__ void k_f2d(int64_t N, const float2* __restrict__ a, double2* __restrict__ b) {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < N) b[i] = make_double2(a[i].x, a[i].y);
+// ------------------------------------------------------------ error-free transformations
+// Every operation is an explicit round-to-nearest intrinsic, so nothing is fused or reassociated.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = __fadd_rn(a, b);
+    const float bb = __fadd_rn(s, -a);
+    e = __fadd_rn(__fadd_rn(a, -__fadd_rn(s, -bb)), __fadd_rn(b, -bb));
 }
-__global__ void k_d2f(int64_t N, const double2* __restrict__ a, float2* __restrict__ b) {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < N) b[i] = make_float2((float)a[i].x, (float)a[i].y);
-}
-__global__ void k_scale(int64_t N, const double2* __restrict__ a, double s, double2* __restrict__ b) {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < N) b[i] = make_double2(s * a[i].x, s * a[i].y);
-}
-__global__ void k_sub(int64_t N, const double2* __restrict__ a, const double2* __restrict__ b,
-                      double2* __restrict__ c) {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < N) c[i] = make_double2(a[i].x - b[i].x, a[i].y - b[i].y);
+__device__ __forceinline__ void fast_two_sum(float a, float b, float& s, float& e) {  // |a| >= |b| or a = 0
+    s = __fadd_rn(a, b);
+    e = __fadd_rn(b, -__fadd_rn(s, -a));
 }
 
+// Dot2 accumulator: the value is s + c (s carries the running sum, c its error terms).
+struct Acc {
+    float s = 0.f, c = 0.f;
+    // += (ah + al)(bh + bl); the al*bl term (relative size 2^-48) is dropped
+    __device__ __forceinline__ void add_prod(float ah, float al, float bh, float bl) {
+        const float p = __fmul_rn(ah, bh);
+        float q = __fmaf_rn(ah, bh, -p);  // exact: ah bh = p + q
+        q = __fmaf_rn(ah, bl, __fmaf_rn(al, bh, q));
+        float t, r;
+        two_sum(s, p, t, r);
+        s = t;
+        c = __fadd_rn(c, __fadd_rn(q, r));
+    }
+    __device__ __forceinline__ double value() const { return (double)s + (double)c; }
+};
+
+// (ah + al) + (bh + bl), renormalised so that |lo| <= ulp(hi) / 2
+__device__ __forceinline__ void df_add(float ah, float al, float bh, float bl, float& h, float& l) {
+    float s, e;
+    two_sum(ah, bh, s, e);
+    e = __fadd_rn(e, __fadd_rn(al, bl));
+    fast_two_sum(s, e, h, l);
+}
+
+// a double as hi + lo (host side)
+static inline void split_df(double x, float& hi, float& lo) {
+    hi = (float)x;
+    lo = (float)(x - (double)hi);
+}
+
+// ------------------------------------------------------------ element-wise kernels
+__global__ void k_c64_to_df(int64_t N, const float2* __restrict__ a, float4* __restrict__ b) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < N) b[i] = make_float4(a[i].x, a[i].y, 0.f, 0.f);
+}
+__global__ void k_df_to_c64(int64_t N, const float4* __restrict__ a, float2* __restrict__ b) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < N) b[i] = make_float2(a[i].x, a[i].y);  // hi = round(hi + lo) for a normalised pair
+}
+// b = s a with s = sh + sl
+__global__ void k_scale_df(int64_t N, const float4* __restrict__ a, float sh, float sl, float4* __restrict__ b) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const float4 v = a[i];
+    float4 o;
+    {
+        const float p = __fmul_rn(v.x, sh);
+        const float q = __fmaf_rn(v.x, sl, __fmaf_rn(v.z, sh, __fmaf_rn(v.x, sh, -p)));
+        fast_two_sum(p, q, o.x, o.z);
+    }
+    {
+        const float p = __fmul_rn(v.y, sh);
+        const float q = __fmaf_rn(v.y, sl, __fmaf_rn(v.w, sh, __fmaf_rn(v.y, sh, -p)));
+        fast_two_sum(p, q, o.y, o.w);
+    }
+    b[i] = o;
+}
+// c = a - b
+__global__ void k_sub_df(int64_t N, const float4* __restrict__ a, const float4* __restrict__ b,
+                         float4* __restrict__ c) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const float4 u = a[i], v = b[i];
+    float4 o;
+    df_add(u.x, u.z, -v.x, -v.z, o.x, o.z);
+    df_add(u.y, u.w, -v.y, -v.w, o.y, o.w);
+    c[i] = o;
+}
+
+// block-wide FP64 sum of a complex value (thread 0 gets it)
 __device__ __forceinline__ double2 block_sum2(double2 v, double2* sh) {
     for (int o = 16; o > 0; o >>= 1) {
         v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
@@ -54,35 +130,50 @@ __device__ __forceinline__ double2 block_sum2(double2 v, double2* sh) {
     return r;
 }
 
-// partial[i * RG + blk] = sum over the block's rows of conj(V_i) w   (grid RG x nvec)
-__global__ void __launch_bounds__(RB) k_dots(int64_t N, const double2* __restrict__ V, const double2* __restrict__ w,
-                                             double2* __restrict__ partial) {
+// partial[i * RG + blk] = sum over the block's rows of conj(V_i) w, for the kDotVecs vectors
+// i = blockIdx.y * kDotVecs + c (< nvec); grid RG x ceil(nvec / kDotVecs)
+__global__ void __launch_bounds__(RB) k_dots_df(int64_t N, const float4* __restrict__ V, int nvec,
+                                                const float4* __restrict__ w, double2* __restrict__ partial) {
     __shared__ double2 sh[RB / 32];
-    int i = blockIdx.y;
-    const double2* v = V + (int64_t)i * N;
-    double2 acc = make_double2(0, 0);
+    const int i0 = blockIdx.y * kDotVecs;
+    const int nv = min(kDotVecs, nvec - i0);
+    Acc re[kDotVecs], im[kDotVecs];
     for (int64_t r = (int64_t)blockIdx.x * RB + threadIdx.x; r < N; r += (int64_t)RG * RB) {
-        double2 a = v[r], b = w[r];
-        acc.x += a.x * b.x + a.y * b.y;
-        acc.y += a.x * b.y - a.y * b.x;
+        const float4 b = w[r];
+#pragma unroll
+        for (int c = 0; c < kDotVecs; ++c) {
+            if (c >= nv) break;
+            const float4 a = V[(int64_t)(i0 + c) * N + r];
+            // conj(a) b = (ar br + ai bi) + i (ar bi - ai br)
+            re[c].add_prod(a.x, a.z, b.x, b.z);
+            re[c].add_prod(a.y, a.w, b.y, b.w);
+            im[c].add_prod(a.x, a.z, b.y, b.w);
+            im[c].add_prod(-a.y, -a.w, b.x, b.z);
+        }
     }
-    double2 s = block_sum2(acc, sh);
-    if (threadIdx.x == 0) partial[(int64_t)i * RG + blockIdx.x] = s;
+#pragma unroll
+    for (int c = 0; c < kDotVecs; ++c) {
+        if (c >= nv) break;  // uniform over the block
+        const double2 s = block_sum2(make_double2(re[c].value(), im[c].value()), sh);
+        if (threadIdx.x == 0) partial[(int64_t)(i0 + c) * RG + blockIdx.x] = s;
+    }
 }
 
 // partial[blk] = sum |w|^2 over the block's rows
-__global__ void __launch_bounds__(RB) k_norm2(int64_t N, const double2* __restrict__ w, double2* __restrict__ partial) {
+__global__ void __launch_bounds__(RB) k_norm2_df(int64_t N, const float4* __restrict__ w,
+                                                 double2* __restrict__ partial) {
     __shared__ double2 sh[RB / 32];
-    double2 acc = make_double2(0, 0);
+    Acc a;
     for (int64_t r = (int64_t)blockIdx.x * RB + threadIdx.x; r < N; r += (int64_t)RG * RB) {
-        double2 b = w[r];
-        acc.x += b.x * b.x + b.y * b.y;
+        const float4 b = w[r];
+        a.add_prod(b.x, b.z, b.x, b.z);
+        a.add_prod(b.y, b.w, b.y, b.w);
     }
-    double2 s = block_sum2(acc, sh);
+    const double2 s = block_sum2(make_double2(a.value(), 0.0), sh);
     if (threadIdx.x == 0) partial[blockIdx.x] = s;
 }
 
-// out[i] = sum_b partial[i * RG + b]   (one block per vector)
+// out[i] = sum_b partial[i * RG + b]   (one block per vector, FP64)
 __global__ void __launch_bounds__(RB) k_reduce(const double2* __restrict__ partial, double2* __restrict__ out) {
     __shared__ double2 sh[RB / 32];
     double2 acc = make_double2(0, 0);
@@ -95,32 +186,30 @@ __global__ void __launch_bounds__(RB) k_reduce(const double2* __restrict__ parti
     if (threadIdx.x == 0) out[blockIdx.x] = s;
 }
 
-// w -= sum_i h_i V_i
-__global__ void k_update(int64_t N, const double2* __restrict__ V, int nvec, const double2* __restrict__ h,
-                         double2* __restrict__ w) {
-    int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+// x += sign * sum_i h_i V_i, with h given as double-float pairs hdf[i] = (re_hi, im_hi, re_lo, im_lo)
+__global__ void k_axpy_df(int64_t N, const float4* __restrict__ V, int nvec, const float4* __restrict__ hdf,
+                          float sign, float4* __restrict__ x) {
+    extern __shared__ float4 hs[];
+    for (int q = threadIdx.x; q < nvec; q += blockDim.x) hs[q] = hdf[q];
+    __syncthreads();
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= N) return;
-    double2 acc = w[r];
+    Acc ar, ai;
     for (int i = 0; i < nvec; ++i) {
-        double2 a = V[(int64_t)i * N + r], c = h[i];
-        acc.x -= c.x * a.x - c.y * a.y;
-        acc.y -= c.x * a.y + c.y * a.x;
+        const float4 a = V[(int64_t)i * N + r], h = hs[i];
+        // h a = (hr ar - hi ai) + i (hr ai + hi ar)
+        ar.add_prod(h.x, h.z, a.x, a.z);
+        ar.add_prod(-h.y, -h.w, a.y, a.w);
+        ai.add_prod(h.x, h.z, a.y, a.w);
+        ai.add_prod(h.y, h.w, a.x, a.z);
     }
-    w[r] = acc;
-}
-
-// x += sum_i y_i V_i
-__global__ void k_combine(int64_t N, const double2* __restrict__ V, int nvec, const double2* __restrict__ y,
-                          double2* __restrict__ x) {
-    int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= N) return;
-    double2 acc = x[r];
-    for (int i = 0; i < nvec; ++i) {
-        double2 a = V[(int64_t)i * N + r], c = y[i];
-        acc.x += c.x * a.x - c.y * a.y;
-        acc.y += c.x * a.y + c.y * a.x;
-    }
-    x[r] = acc;
+    float4 o = x[r];
+    float sh, sl;
+    two_sum(ar.s, ar.c, sh, sl);
+    df_add(o.x, o.z, sign * sh, sign * sl, o.x, o.z);
+    two_sum(ai.s, ai.c, sh, sl);
+    df_add(o.y, o.w, sign * sh, sign * sl, o.y, o.w);
+    x[r] = o;
 }
 
 namespace {
@@ -131,15 +220,16 @@ struct Ctx {
     unsigned nb;
     double2* partial;  // RG * (m + 1)
     double2* small;    // m + 2 values
+    float4* coeff;     // m + 2 double-float complex coefficients
 
     void count(int n = 1) { P->launches += n; }
-    void matvec(const double2* in, double2* out) {
-        launch_density_prep(P, in, true, P->sig.p, st);
+    void matvec(const float4* in, float4* out) {
+        launch_density_prep(P, in, VecKind::DoubleFloat, P->sig.p, st);
         run_matvec_sorted(P, 7, st);
-        launch_output(P, P->phi.p, out, true, st);
+        launch_output(P, P->phi.p, out, VecKind::DoubleFloat, st);
     }
-    double norm(const double2* w) {
-        k_norm2<<<RG, RB, 0, st>>>(N, w, partial);
+    double norm(const float4* w) {
+        k_norm2_df<<<RG, RB, 0, st>>>(N, w, partial);
         k_reduce<<<1, RB, 0, st>>>(partial, small);
         count(2);
         double2 h;
@@ -147,16 +237,39 @@ struct Ctx {
         HFMM_CUDA(cudaStreamSynchronize(st));
         return std::sqrt(h.x);
     }
-    // h = V[0..nvec)^H w (device, in small), then w -= V h; adds h into hsum
-    void cgs_pass(const double2* V, int nvec, double2* w, std::vector<cd>& hsum) {
-        k_dots<<<dim3(RG, nvec), RB, 0, st>>>(N, V, w, partial);
+    void scale(const float4* a, double s, float4* b) {
+        float sh, sl;
+        split_df(s, sh, sl);
+        k_scale_df<<<nb, 256, 0, st>>>(N, a, sh, sl, b);
+        count();
+    }
+    // x += sign * V[0..nvec) c  (c on the host, FP64)
+    void axpy(const float4* V, int nvec, const std::vector<cd>& c, float sign, float4* x) {
+        std::vector<float4> cf(nvec);
+        for (int i = 0; i < nvec; ++i) {
+            float rh, rl, ih, il;
+            split_df(c[i].real(), rh, rl);
+            split_df(c[i].imag(), ih, il);
+            cf[i] = make_float4(rh, ih, rl, il);
+        }
+        HFMM_CUDA(cudaMemcpyAsync(coeff, cf.data(), sizeof(float4) * nvec, cudaMemcpyHostToDevice, st));
+        k_axpy_df<<<nb, 256, sizeof(float4) * nvec, st>>>(N, V, nvec, coeff, sign, x);
+        count();
+    }
+    // h = V[0..nvec)^H w, then w -= V h; adds h into hsum
+    void cgs_pass(const float4* V, int nvec, float4* w, std::vector<cd>& hsum) {
+        k_dots_df<<<dim3(RG, (nvec + kDotVecs - 1) / kDotVecs), RB, 0, st>>>(N, V, nvec, w, partial);
         k_reduce<<<nvec, RB, 0, st>>>(partial, small);
-        k_update<<<nb, 256, 0, st>>>(N, V, nvec, small, w);
-        count(3);
+        count(2);
         std::vector<double2> h(nvec);
         HFMM_CUDA(cudaMemcpyAsync(h.data(), small, sizeof(double2) * nvec, cudaMemcpyDeviceToHost, st));
         HFMM_CUDA(cudaStreamSynchronize(st));
-        for (int i = 0; i < nvec; ++i) hsum[i] += cd(h[i].x, h[i].y);
+        std::vector<cd> hc(nvec);
+        for (int i = 0; i < nvec; ++i) {
+            hc[i] = cd(h[i].x, h[i].y);
+            hsum[i] += hc[i];
+        }
+        axpy(V, nvec, hc, -1.f, w);
     }
 };
 }  // namespace
@@ -171,17 +284,19 @@ int run_gmres(hfmm_plan* P, const void* rhs, void* x_out, int* iters, double* re
         P->gw.alloc(N, nullptr);
         P->gx.alloc(N, nullptr);
         P->gb.alloc(N, nullptr);
-        P->gred.alloc((size_t)2 * RG * (m + 2) + 2 * (m + 2), nullptr);
+        P->gred.alloc((size_t)2 * RG * (m + 2) + 2 * (m + 2) + 4 * (m + 2), nullptr);
         P->kry_m = m;
     }
-    Ctx c{P, st, N, (unsigned)((N + 255) / 256), (double2*)P->gred.p, (double2*)P->gred.p + (size_t)RG * (m + 2)};
-    double2* V = P->kry.p;
-    k_f2d<<<c.nb, 256, 0, st>>>(N, (const float2*)rhs, P->gb.p);
+    double2* red = (double2*)P->gred.p;
+    Ctx c{P, st, N, (unsigned)((N + 255) / 256), red, red + (size_t)RG * (m + 2),
+          reinterpret_cast<float4*>(red + (size_t)RG * (m + 2) + (m + 2))};
+    float4* V = P->kry.p;
+    k_c64_to_df<<<c.nb, 256, 0, st>>>(N, (const float2*)rhs, P->gb.p);
     c.count();
-    HFMM_CUDA(cudaMemsetAsync(P->gx.p, 0, sizeof(double2) * N, st));
+    HFMM_CUDA(cudaMemsetAsync(P->gx.p, 0, sizeof(float4) * N, st));
     double bnorm = c.norm(P->gb.p);
     if (bnorm == 0.0) {
-        k_d2f<<<c.nb, 256, 0, st>>>(N, P->gx.p, (float2*)x_out);
+        k_df_to_c64<<<c.nb, 256, 0, st>>>(N, P->gx.p, (float2*)x_out);
         c.count();
         HFMM_CUDA(cudaStreamSynchronize(st));
         *iters = 0;
@@ -189,28 +304,24 @@ int run_gmres(hfmm_plan* P, const void* rhs, void* x_out, int* iters, double* re
         return HFMM_OK;
     }
     // r0 = b (x0 = 0)
-    HFMM_CUDA(cudaMemcpyAsync(P->gw.p, P->gb.p, sizeof(double2) * N, cudaMemcpyDeviceToDevice, st));
+    HFMM_CUDA(cudaMemcpyAsync(P->gw.p, P->gb.p, sizeof(float4) * N, cudaMemcpyDeviceToDevice, st));
     double beta = bnorm;
     int it = 0;
     bool converged = false;
     while (it < maxit && !converged) {
-        k_scale<<<c.nb, 256, 0, st>>>(N, P->gw.p, 1.0 / beta, V);
-        c.count();
+        c.scale(P->gw.p, 1.0 / beta, V);
         std::vector<cd> H((size_t)(m + 1) * m, cd(0)), cs(m), sn(m), g(m + 1, cd(0));
         g[0] = beta;
         int jdone = 0;
         for (int j = 0; j < m && it < maxit; ++j) {
-            double2* w = P->gw.p;
+            float4* w = P->gw.p;
             c.matvec(V + (int64_t)j * N, w);
             std::vector<cd> h(j + 2, cd(0));
             c.cgs_pass(V, j + 1, w, h);
             c.cgs_pass(V, j + 1, w, h);
             double hn = c.norm(w);
             h[j + 1] = hn;
-            if (hn > 0.0) {
-                k_scale<<<c.nb, 256, 0, st>>>(N, w, 1.0 / hn, V + (int64_t)(j + 1) * N);
-                c.count();
-            }
+            if (hn > 0.0) c.scale(w, 1.0 / hn, V + (int64_t)(j + 1) * N);
             // previous rotations, each acting on rows (i, i+1) as [[conj c, conj s], [-s, c]]
             for (int i = 0; i < j; ++i) {
                 cd t = std::conj(cs[i]) * h[i] + std::conj(sn[i]) * h[i + 1];
@@ -234,26 +345,22 @@ int run_gmres(hfmm_plan* P, const void* rhs, void* x_out, int* iters, double* re
             jdone = j + 1;
             if (std::abs(g[j + 1]) / bnorm <= tol || hn == 0.0) break;
         }
-        // y = H^{-1} g (upper triangular), x += V y
+        // y = H^{-1} g (upper triangular, FP64), x += V y
         std::vector<cd> y(jdone);
         for (int i = jdone - 1; i >= 0; --i) {
             cd s = g[i];
             for (int q = i + 1; q < jdone; ++q) s -= H[(size_t)i * m + q] * y[q];
             y[i] = s / H[(size_t)i * m + i];
         }
-        std::vector<double2> yd(jdone);
-        for (int i = 0; i < jdone; ++i) yd[i] = make_double2(y[i].real(), y[i].imag());
-        HFMM_CUDA(cudaMemcpyAsync(c.small, yd.data(), sizeof(double2) * jdone, cudaMemcpyHostToDevice, st));
-        k_combine<<<c.nb, 256, 0, st>>>(N, V, jdone, c.small, P->gx.p);
-        c.count();
+        c.axpy(V, jdone, y, 1.f, P->gx.p);
         // true residual r = b - A x
         c.matvec(P->gx.p, P->gw.p);
-        k_sub<<<c.nb, 256, 0, st>>>(N, P->gb.p, P->gw.p, P->gw.p);
+        k_sub_df<<<c.nb, 256, 0, st>>>(N, P->gb.p, P->gw.p, P->gw.p);
         c.count();
         beta = c.norm(P->gw.p);
         converged = beta / bnorm <= tol;
     }
-    k_d2f<<<c.nb, 256, 0, st>>>(N, P->gx.p, (float2*)x_out);
+    k_df_to_c64<<<c.nb, 256, 0, st>>>(N, P->gx.p, (float2*)x_out);
     c.count();
     HFMM_CUDA(cudaGetLastError());
     HFMM_CUDA(cudaStreamSynchronize(st));

@@ -146,8 +146,8 @@ struct hfmm_plan {
     // scratch (one matvec at a time per plan)
     DBuf<float2> sig, phi;
     // GMRES workspace (allocated on first solve, kept resident)
-    DBuf<double2> kry;         // (restart + 1) x N
-    DBuf<double2> gw, gx, gb;  // work vector, iterate, right-hand side
+    DBuf<float4> kry;          // (restart + 1) x N, double-float complex
+    DBuf<float4> gw, gx, gb;   // work vector, iterate, right-hand side (double-float complex)
     DBuf<double> gred;         // reduction scratch
     int kry_m = 0;
     int64_t launches = 0;       // kernels launched by this plan
@@ -164,9 +164,12 @@ __device__ __forceinline__ void red_add(float2* p, float2 v) {
 }
 
 // sig_sorted = k w / (4 pi) * density[perm]  (one right-hand side)
-void launch_density_prep(hfmm_plan* P, const void* density, bool fp64, float2* sig, cudaStream_t st);
+// Complex vectors the matvec reads and writes: complex64, or double-float complex
+// (float4 = re_hi, im_hi, re_lo, im_lo; value = hi + lo) for the Krylov solver.
+enum class VecKind { Complex64, DoubleFloat };
+void launch_density_prep(hfmm_plan* P, const void* density, VecKind kind, float2* sig, cudaStream_t st);
 // out[perm[i]] = phi[i]
-void launch_output(hfmm_plan* P, const float2* phi, void* out, bool fp64, cudaStream_t st);
+void launch_output(hfmm_plan* P, const float2* phi, void* out, VecKind kind, cudaStream_t st);
 // parts bit 0 near, 1 far, 2 correction; writes P->phi
 void run_matvec_sorted(hfmm_plan* P, int parts, cudaStream_t st);
 // records stage event q (if timing is active)

@@ -720,9 +720,9 @@ int hfmm_matvec_parts(hfmm_plan* P, const void* density, void* potential, int nr
     for (int r = 0; r < nrhs; ++r) {
         const float2* d = (const float2*)density + (int64_t)r * P->N;
         float2* o = (float2*)potential + (int64_t)r * P->N;
-        launch_density_prep(P, d, false, P->sig.p, st);
+        launch_density_prep(P, d, VecKind::Complex64, P->sig.p, st);
         run_matvec_sorted(P, parts, st);
-        launch_output(P, P->phi.p, o, false, st);
+        launch_output(P, P->phi.p, o, VecKind::Complex64, st);
     }
     HFMM_CUDA(cudaGetLastError());
     return HFMM_OK;
@@ -750,9 +750,9 @@ int hfmm_matvec_timed(hfmm_plan* P, const void* density, void* potential, float*
     for (int q = 0; q <= HFMM_NUM_STAGES; ++q) HFMM_CUDA(cudaEventCreate(&ev[q]));
     P->stage_ev = ev;
     mark_stage(P, 0, st);
-    launch_density_prep(P, density, false, P->sig.p, st);
+    launch_density_prep(P, density, VecKind::Complex64, P->sig.p, st);
     run_matvec_sorted(P, 7, st);
-    launch_output(P, P->phi.p, potential, false, st);
+    launch_output(P, P->phi.p, potential, VecKind::Complex64, st);
     mark_stage(P, HFMM_NUM_STAGES, st);
     HFMM_CUDA(cudaEventSynchronize(ev[HFMM_NUM_STAGES]));
     for (int q = 0; q < HFMM_NUM_STAGES; ++q) HFMM_CUDA(cudaEventElapsedTime(&stage_ms[q], ev[q], ev[q + 1]));
@@ -789,9 +789,9 @@ int hfmm_direct(hfmm_plan* P, const void* density, void* potential, int nrhs, vo
     HFMM_GUARD_BEGIN
     cudaStream_t st = (cudaStream_t)stream;
     for (int r = 0; r < nrhs; ++r) {
-        launch_density_prep(P, (const float2*)density + (int64_t)r * P->N, false, P->sig.p, st);
+        launch_density_prep(P, (const float2*)density + (int64_t)r * P->N, VecKind::Complex64, P->sig.p, st);
         run_direct_sorted(P, st);
-        launch_output(P, P->phi.p, (float2*)potential + (int64_t)r * P->N, false, st);
+        launch_output(P, P->phi.p, (float2*)potential + (int64_t)r * P->N, VecKind::Complex64, st);
     }
     HFMM_CUDA(cudaGetLastError());
     return HFMM_OK;
