@@ -501,10 +501,11 @@ __global__ void __launch_bounds__(128) k_l2p(int64_t N, const int32_t* __restric
 // many columns; CG = 4 (128 x 16) and CG = 2 (256 x 8) serve the coarse levels,
 // where an offset has only a few targets and the high order makes T the large
 // operand.  Row tiles in separate blocks let a level with few items fill the GPU.
+// rhs > 1: batched items (one box pair standing for the columns box * rhs + c).
 template <int CG>
 __global__ void __launch_bounds__(128) k_translate(const TransItem* __restrict__ items, int64_t item0,
                                                    const int2* __restrict__ cols, const float2* __restrict__ ops,
-                                                   float2* __restrict__ coef) {
+                                                   float2* __restrict__ coef, int rhs) {
     constexpr int RG = 128 / CG;             // row groups
     constexpr int TR = 4 * RG, TC = 4 * CG;  // tile rows, tile columns
     constexpr int KS = TR >= 128 ? 2048 / TR : 32;  // K slice: <= 16 T elements per thread
@@ -516,7 +517,18 @@ __global__ void __launch_bounds__(128) k_translate(const TransItem* __restrict__
     int ncol = it.ncol, Pin = it.pin, Pout = it.pout;
     const int r0 = TR * (int)blockIdx.y;
     if (r0 >= Pout) return;  // uniform over the block: items of a lower order in the same launch
-    if (tid < TC) sc[tid] = tid < ncol ? cols[it.cols + tid] : make_int2(0, 0);
+    if (tid < TC) {
+        int2 v = make_int2(0, 0);
+        if (tid < ncol) {
+            if (rhs > 1) {
+                const int2 pr = cols[it.cols];
+                v = make_int2(pr.x * rhs + tid, pr.y * rhs + tid);
+            } else {
+                v = cols[it.cols + tid];
+            }
+        }
+        sc[tid] = v;
+    }
     __syncthreads();
     const float2* T = ops + it.op;
     const int tx = tid % CG, ty = tid / CG;
@@ -699,16 +711,17 @@ void mark_stage(hfmm_plan* P, int q, cudaStream_t st) {
 }
 
 // Items [b, e) of at most `width` columns (64, 16 or 8) and output order <= pout_max.
-static void launch_translate(hfmm_plan* P, int64_t b, int64_t e, int pout_max, int width, cudaStream_t st) {
+static void launch_translate(hfmm_plan* P, const TransItem* items, float2* coef, int rhs, int64_t b, int64_t e,
+                             int pout_max, int width, cudaStream_t st) {
     if (e <= b) return;
-    const int rows = width >= 64 ? 32 : width >= 16 ? 128 : 256;
+    const int rows = width > 16 ? 32 : width > 8 ? 128 : 256;
     const dim3 grid((unsigned)(e - b), (unsigned)((pout_max + rows - 1) / rows));
-    if (width >= 64)
-        k_translate<16><<<grid, 128, 0, st>>>(P->items.p, b, P->item_cols.p, P->ops.p, P->coef.p);
-    else if (width >= 16)
-        k_translate<4><<<grid, 128, 0, st>>>(P->items.p, b, P->item_cols.p, P->ops.p, P->coef.p);
+    if (width > 16)
+        k_translate<16><<<grid, 128, 0, st>>>(items, b, P->item_cols.p, P->ops.p, coef, rhs);
+    else if (width > 8)
+        k_translate<4><<<grid, 128, 0, st>>>(items, b, P->item_cols.p, P->ops.p, coef, rhs);
     else
-        k_translate<2><<<grid, 128, 0, st>>>(P->items.p, b, P->item_cols.p, P->ops.p, P->coef.p);
+        k_translate<2><<<grid, 128, 0, st>>>(items, b, P->item_cols.p, P->ops.p, coef, rhs);
     ++P->launches;
 }
 
@@ -765,20 +778,22 @@ void run_matvec_sorted(hfmm_plan* P, int parts, cudaStream_t st) {
             const auto& g = P->m2m_tc[l];
             if (g.second > g.first) {
                 m2l_tc_launch(P->tc_groups.p + g.first, g.second - g.first, P->items.p, P->item_cols.p, P->aops.p,
-                              P->coef.p, P->dev_err.p, st);
+                              P->coef.p, P->dev_err.p, 1, st);
                 ++P->launches;
             } else {
-                launch_translate(P, P->m2m_items_begin[l], P->m2m_items_end[l], P->lev[l].P, HFMM_TRANS_NB, st);
+                launch_translate(P, P->items.p, P->coef.p, 1, P->m2m_items_begin[l], P->m2m_items_end[l], P->lev[l].P,
+                                 HFMM_TRANS_NB, st);
             }
         }
     mark_stage(P, 4, st);
     if (far)
-        for (const SimtRange& r : P->m2l_simt) launch_translate(P, r.begin, r.end, r.pout_max, r.width, st);
+        for (const SimtRange& r : P->m2l_simt)
+            launch_translate(P, P->items.p, P->coef.p, 1, r.begin, r.end, r.pout_max, r.width, st);
     mark_stage(P, 5, st);
     if (far) {
         if (P->n_tc_groups > 0) {
             m2l_tc_launch(P->tc_groups.p, P->n_tc_groups, P->items.p, P->item_cols.p, P->aops.p, P->coef.p,
-                          P->dev_err.p, st);
+                          P->dev_err.p, 1, st);
             ++P->launches;
         }
     }
@@ -788,10 +803,11 @@ void run_matvec_sorted(hfmm_plan* P, int parts, cudaStream_t st) {
             const auto& g = P->l2l_tc[l];
             if (g.second > g.first) {
                 m2l_tc_launch(P->tc_groups.p + g.first, g.second - g.first, P->items.p, P->item_cols.p, P->aops.p,
-                              P->coef.p, P->dev_err.p, st);
+                              P->coef.p, P->dev_err.p, 1, st);
                 ++P->launches;
             } else {
-                launch_translate(P, P->l2l_items_begin[l], P->l2l_items_end[l], P->lev[l].P, HFMM_TRANS_NB, st);
+                launch_translate(P, P->items.p, P->coef.p, 1, P->l2l_items_begin[l], P->l2l_items_end[l], P->lev[l].P,
+                                 HFMM_TRANS_NB, st);
             }
         }
     mark_stage(P, 7, st);
@@ -817,6 +833,475 @@ void run_direct_sorted(hfmm_plan* P, cudaStream_t st) {
     if (P->corr_nnz > 0) {
         launch_corr(P, st);
     }
+    HFMM_CUDA(cudaGetLastError());
+}
+
+// ============================================================== batched right-hand sides
+// R = 2..64 right-hand sides in one matvec.  Densities and potentials are held
+// [point][rhs] and expansions [box][rhs][P]: the R values a kernel needs for one
+// point or one box are one contiguous block.  The near field evaluates each
+// Green's-function tile once and multiplies it into all R densities; P2M and
+// L2P become small complex GEMMs over R; the translations reuse the single
+// right-hand-side kernels with one work item per box pair and R columns.
+constexpr int kBMax = 64;    // right-hand sides per batched matvec
+constexpr int kBChunk = 32;  // sources (P2P) or points (P2M, L2P) per shared-memory chunk
+constexpr int kBMaxP = 128;  // leaf expansion size the batched P2M / L2P kernels take
+
+// Regular basis b_c(y) = jt_n(r) Q_n^|m|(cos t) e^{i m phi}, c = n^2 + n + m, of a point y
+// relative to its leaf centre (scaled by k):  L2P is sum_c L_c b_c,  P2M is sum_j s_j conj(b_c(y_j)).
+__device__ void regular_basis(float4 y, int p, float s, float2* out) {
+    const Dir d = make_dir(y.x, y.y, y.z);
+    float jr[HFMM_PMAX + 1];
+    f_jn_scaled(p, d.r, s, jr);
+    float stp = 1.f, er = 1.f, ei = 0.f;
+    for (int m = 0; m <= p; ++m) {
+        if (m > 0) {
+            stp *= d.st;
+            const float t = er * d.ex - ei * d.ey;
+            ei = er * d.ey + ei * d.ex;
+            er = t;
+        }
+        const float qmm = c_leg_qmm[m] * stp;
+        float qa = qmm, qb = 0.f;
+        for (int n = m; n <= p; ++n) {
+            float qn = qmm;
+            if (n > m) {
+                const int h = n * (n + 1) / 2 + m;
+                qn = (n == m + 1) ? c_leg_a[h] * d.ct * qmm : c_leg_a[h] * (d.ct * qa - c_leg_b[h] * qb);
+                qb = qa;
+                qa = qn;
+            }
+            const float bq = jr[n] * qn;
+            out[n * n + n + m] = make_float2(bq * er, bq * ei);
+            if (m > 0) out[n * n + n - m] = make_float2(bq * er, -bq * ei);
+        }
+    }
+}
+
+// sig_b[i][r] = k w_i / (4 pi) density[r][perm_i]; 32 points per block, transposed in shared memory
+__global__ void __launch_bounds__(256) k_prep_b(int64_t N, int R, const int32_t* __restrict__ perm,
+                                                const float* __restrict__ wscale, const float2* __restrict__ dens,
+                                                float2* __restrict__ sig) {
+    __shared__ float2 t[32][kBMax + 1];
+    const int64_t i0 = (int64_t)blockIdx.x * 32;
+    const int ii = threadIdx.x & 31;
+    const int64_t i = i0 + ii;
+    const int32_t pi = i < N ? perm[i] : 0;
+    for (int r = threadIdx.x >> 5; r < R; r += 8) t[ii][r] = i < N ? dens[(int64_t)r * N + pi] : make_float2(0.f, 0.f);
+    __syncthreads();
+    for (int e = threadIdx.x; e < 32 * R; e += 256) {
+        const int a = e / R, r = e % R;
+        const int64_t row = i0 + a;
+        if (row < N) {
+            const float w = wscale[row];
+            const float2 v = t[a][r];
+            sig[row * R + r] = make_float2(w * v.x, w * v.y);
+        }
+    }
+}
+
+// out[r][perm_i] = phi_b[i][r]
+__global__ void __launch_bounds__(256) k_output_b(int64_t N, int R, const int32_t* __restrict__ perm,
+                                                  const float2* __restrict__ phi, float2* __restrict__ out) {
+    __shared__ float2 t[32][kBMax + 1];
+    const int64_t i0 = (int64_t)blockIdx.x * 32;
+    for (int e = threadIdx.x; e < 32 * R; e += 256) {
+        const int a = e / R, r = e % R;
+        const int64_t row = i0 + a;
+        t[a][r] = row < N ? phi[row * R + r] : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    const int ii = threadIdx.x & 31;
+    const int64_t i = i0 + ii;
+    if (i >= N) return;
+    const int32_t pi = perm[i];
+    for (int r = threadIdx.x >> 5; r < R; r += 8) out[(int64_t)r * N + pi] = t[ii][r];
+}
+
+// Near field for R right-hand sides: one block (8 warps) per target leaf.  Neighbour
+// sources are staged (positions in the leaf's frame, global index); per chunk of 32
+// sources the block evaluates G[s][t] once, loads the chunk's densities [s][r], and
+// each thread accumulates 2 targets (t, t + 32) x 8 right-hand sides (r, r + 8, ...).
+template <bool POLY>
+__global__ void __launch_bounds__(256) k_p2p_b(const int32_t* __restrict__ leaf_start, const int4* __restrict__ leaf_ijk,
+                                               const int32_t* __restrict__ nbr_ptr, const int32_t* __restrict__ nbr,
+                                               const float4* __restrict__ pts, const float2* __restrict__ sig,
+                                               float shift, int cap, int R, float2* __restrict__ phi) {
+    constexpr float kC[HFMM_POLY_C_DEG + 1] = HFMM_POLY_C_INIT;
+    constexpr float kS[HFMM_POLY_S_DEG + 1] = HFMM_POLY_S_INIT;
+    extern __shared__ float4 smem_b[];
+    const int cap4 = (cap + 3) & ~3;
+    float4* sp = smem_b;                                      // [cap4] positions in the target leaf frame
+    int* sj = reinterpret_cast<int*>(sp + cap4);              // [cap4] sorted index of each staged source
+    float2* G = reinterpret_cast<float2*>(sj + cap4);         // [kBChunk][64]
+    float2* Sg = G + kBChunk * 64;                            // [kBChunk][kBMax]
+    __shared__ int s_off[29], s_leaf[28];
+    const int b = blockIdx.x, tid = threadIdx.x;
+    const int4 tij = __ldg(leaf_ijk + b);
+    const int nb0 = __ldg(nbr_ptr + b), nn = __ldg(nbr_ptr + b + 1) - nb0;
+    if (tid == 0) {
+        int k = 0, o = 0;
+        s_leaf[k++] = b;  // self first
+        for (int q = 0; q < nn; ++q) {
+            const int sl = __ldg(nbr + nb0 + q);
+            if (sl != b) s_leaf[k++] = sl;
+        }
+        for (int q = 0; q < k; ++q) {
+            s_off[q] = o;
+            o += __ldg(leaf_start + s_leaf[q] + 1) - __ldg(leaf_start + s_leaf[q]);
+        }
+        s_off[k] = o;
+        s_off[28] = k;
+    }
+    __syncthreads();
+    const int nl = s_off[28], total = s_off[nl];
+    for (int q = 0; q < nl; ++q) {
+        const int sl = s_leaf[q];
+        const int j0 = __ldg(leaf_start + sl), n = s_off[q + 1] - s_off[q];
+        const int4 sij = __ldg(leaf_ijk + sl);
+        const float ox = (float)(sij.x - tij.x) * shift, oy = (float)(sij.y - tij.y) * shift,
+                    oz = (float)(sij.z - tij.z) * shift;
+        for (int e = tid; e < n; e += blockDim.x) {
+            const float4 p = __ldg(pts + j0 + e);
+            sp[s_off[q] + e] = make_float4(p.x + ox, p.y + oy, p.z + oz, 0.f);
+            sj[s_off[q] + e] = j0 + e;
+        }
+    }
+    const int nself = s_off[1], out0 = __ldg(leaf_start + b);
+    const int tt = tid & 31, rg = tid >> 5;
+    for (int t0 = 0; t0 < nself; t0 += 64) {
+        const int nt = min(64, nself - t0);
+        const bool two = nt > 32;  // uniform over the block
+        float2 acc0[8], acc1[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) acc0[q] = acc1[q] = make_float2(0.f, 0.f);
+        for (int s0 = 0; s0 < total; s0 += kBChunk) {
+            const int cnt = min(kBChunk, total - s0);
+            __syncthreads();  // staging done / previous chunk consumed
+            for (int e = tid; e < kBChunk * 64; e += 256) {
+                const int s = e >> 6, t = e & 63;
+                float2 g = make_float2(0.f, 0.f);
+                const int si = s0 + s, ti = t0 + t;
+                if (s < cnt && t < nt && si != ti) {  // si == ti: the target itself (self leaf first)
+                    const float4 a = sp[si], c = sp[ti];
+                    const float dx = c.x - a.x, dy = c.y - a.y, dz = c.z - a.z;
+                    const float u = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                    const float rinv = rsqrt_ftz(u);
+                    if (POLY) {
+                        g = make_float2(horner<HFMM_POLY_C_DEG>(kC, u) * rinv, horner<HFMM_POLY_S_DEG>(kS, u));
+                    } else {
+                        float sn, cs;
+                        sincosf(u * rinv, &sn, &cs);
+                        g = make_float2(cs * rinv, sn * rinv);
+                    }
+                }
+                G[e] = g;
+            }
+            for (int e = tid; e < kBChunk * kBMax; e += 256) {
+                const int s = e / kBMax, r = e % kBMax;
+                Sg[e] = (s < cnt && r < R) ? __ldg(sig + (int64_t)sj[s0 + s] * R + r) : make_float2(0.f, 0.f);
+            }
+            __syncthreads();
+            for (int s = 0; s < cnt; ++s) {
+                const float2 g0 = G[s * 64 + tt];
+                const float2 g1 = two ? G[s * 64 + tt + 32] : make_float2(0.f, 0.f);
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    const float2 v = Sg[s * kBMax + rg + 8 * q];
+                    acc0[q].x = fmaf(g0.x, v.x, fmaf(-g0.y, v.y, acc0[q].x));
+                    acc0[q].y = fmaf(g0.x, v.y, fmaf(g0.y, v.x, acc0[q].y));
+                    if (two) {
+                        acc1[q].x = fmaf(g1.x, v.x, fmaf(-g1.y, v.y, acc1[q].x));
+                        acc1[q].y = fmaf(g1.x, v.y, fmaf(g1.y, v.x, acc1[q].y));
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int r = rg + 8 * q;
+            if (r >= R) continue;
+            if (tt < nt) phi[(int64_t)(out0 + t0 + tt) * R + r] = acc0[q];
+            if (two && tt + 32 < nt) phi[(int64_t)(out0 + t0 + tt + 32) * R + r] = acc1[q];
+        }
+    }
+}
+
+static size_t p2p_b_smem(int cap) {
+    const size_t cap4 = (size_t)((cap + 3) & ~3);
+    return cap4 * (sizeof(float4) + sizeof(int)) + sizeof(float2) * kBChunk * (64 + kBMax);
+}
+
+// M[leaf][r][c] = sum_j conj(b_c(y_j)) sig_b[j][r]; one block per leaf, 16 x 16 threads,
+// 4 coefficients x 4 right-hand sides each, coefficient tiles of 64
+__global__ void __launch_bounds__(256) k_p2m_b(const int32_t* __restrict__ leaf_start, const float4* __restrict__ pts,
+                                               const float2* __restrict__ sig, int p, float s, int R,
+                                               float2* __restrict__ M) {
+    extern __shared__ float2 smem_p2m[];
+    const int P = (p + 1) * (p + 1);
+    float2* Bs = smem_p2m;          // [kBChunk][P]
+    float2* Ss = Bs + kBChunk * P;  // [kBChunk][kBMax]
+    const int leaf = blockIdx.x, tid = threadIdx.x;
+    const int b0 = leaf_start[leaf], b1 = leaf_start[leaf + 1];
+    const int cg = tid & 15, rg = tid >> 4;
+    for (int c0 = 0; c0 < P; c0 += 64) {
+        float2 acc[4][4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[a][q] = make_float2(0.f, 0.f);
+        for (int j0 = b0; j0 < b1; j0 += kBChunk) {
+            const int cnt = min(kBChunk, b1 - j0);
+            __syncthreads();
+            if (tid < cnt) regular_basis(pts[j0 + tid], p, s, Bs + tid * P);
+            for (int e = tid; e < kBChunk * kBMax; e += 256) {
+                const int j = e / kBMax, r = e % kBMax;
+                Ss[e] = (j < cnt && r < R) ? sig[(int64_t)(j0 + j) * R + r] : make_float2(0.f, 0.f);
+            }
+            __syncthreads();
+            for (int j = 0; j < cnt; ++j) {
+                float2 bb[4], v[4];
+#pragma unroll
+                for (int a = 0; a < 4; ++a) {
+                    const int c = c0 + cg + 16 * a;
+                    bb[a] = c < P ? Bs[j * P + c] : make_float2(0.f, 0.f);
+                }
+#pragma unroll
+                for (int q = 0; q < 4; ++q) v[q] = Ss[j * kBMax + rg + 16 * q];
+#pragma unroll
+                for (int a = 0; a < 4; ++a)
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {  // conj(b) v
+                        acc[a][q].x = fmaf(bb[a].x, v[q].x, fmaf(bb[a].y, v[q].y, acc[a][q].x));
+                        acc[a][q].y = fmaf(bb[a].x, v[q].y, fmaf(-bb[a].y, v[q].x, acc[a][q].y));
+                    }
+            }
+        }
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int c = c0 + cg + 16 * a, r = rg + 16 * q;
+                if (c < P && r < R) M[((int64_t)leaf * R + r) * P + c] = acc[a][q];
+            }
+    }
+}
+
+static size_t p2m_b_smem(int P) { return sizeof(float2) * kBChunk * (P + kBMax); }
+
+// phi_b[j][r] += sum_c b_c(y_j) L[leaf][r][c]; one block per leaf; thread (point jj, rhs rg + 8q)
+__global__ void __launch_bounds__(256) k_l2p_b(const int32_t* __restrict__ leaf_start, const float4* __restrict__ pts,
+                                               int p, float s, int R, const float2* __restrict__ L,
+                                               float2* __restrict__ phi) {
+    extern __shared__ float2 smem_l2p[];
+    const int P = (p + 1) * (p + 1), Pp = P + 1;
+    float2* Ls = smem_l2p;          // [kBMax][P]
+    float2* Bs = Ls + kBMax * P;    // [kBChunk][P + 1]
+    const int leaf = blockIdx.x, tid = threadIdx.x;
+    const int b0 = leaf_start[leaf], b1 = leaf_start[leaf + 1];
+    for (int e = tid; e < kBMax * P; e += 256)
+        Ls[e] = e < R * P ? L[(int64_t)leaf * R * P + e] : make_float2(0.f, 0.f);
+    const int jj = tid & 31, rg = tid >> 5;
+    for (int j0 = b0; j0 < b1; j0 += kBChunk) {
+        const int cnt = min(kBChunk, b1 - j0);
+        __syncthreads();
+        if (tid < cnt) regular_basis(pts[j0 + tid], p, s, Bs + tid * Pp);
+        __syncthreads();
+        if (jj >= cnt) continue;
+        float2 acc[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) acc[q] = make_float2(0.f, 0.f);
+        for (int c = 0; c < P; ++c) {
+            const float2 bb = Bs[jj * Pp + c];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const float2 l = Ls[(rg + 8 * q) * P + c];
+                acc[q].x = fmaf(bb.x, l.x, fmaf(-bb.y, l.y, acc[q].x));
+                acc[q].y = fmaf(bb.x, l.y, fmaf(bb.y, l.x, acc[q].y));
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int r = rg + 8 * q;
+            if (r >= R) continue;
+            float2* o = phi + (int64_t)(j0 + jj) * R + r;
+            const float2 v = *o;
+            *o = make_float2(v.x + acc[q].x, v.y + acc[q].y);
+        }
+    }
+}
+
+static size_t l2p_b_smem(int P) { return sizeof(float2) * ((size_t)kBMax * P + (size_t)kBChunk * (P + 1)); }
+
+// phi_b[i][r] += sum_nz C_i,col sig_b[col][r]: one warp per row, lanes on right-hand sides
+__global__ void __launch_bounds__(256) k_corr_b(int64_t N, int R, const int64_t* __restrict__ ptr,
+                                                const int32_t* __restrict__ col, const float2* __restrict__ val,
+                                                const float2* __restrict__ sig, float2* __restrict__ phi) {
+    const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (i >= N) return;
+    float2 acc[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+    for (int64_t q = ptr[i]; q < ptr[i + 1]; ++q) {
+        const float2 c = __ldg(val + q);
+        const float2* sg = sig + (int64_t)__ldg(col + q) * R;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int r = lane + 32 * h;
+            if (r < R) {
+                const float2 v = __ldg(sg + r);
+                acc[h].x = fmaf(c.x, v.x, fmaf(-c.y, v.y, acc[h].x));
+                acc[h].y = fmaf(c.x, v.y, fmaf(c.y, v.x, acc[h].y));
+            }
+        }
+    }
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int r = lane + 32 * h;
+        if (r < R) {
+            float2* o = phi + i * R + r;
+            const float2 v = *o;
+            *o = make_float2(v.x + acc[h].x, v.y + acc[h].y);
+        }
+    }
+}
+
+bool batch_supported(const hfmm_plan* P, int R) {
+    if (R < 2 || R > kBMax) return false;
+    if (P->L >= 2 && P->lev[P->L].P > kBMaxP) return false;
+    return P->p2p_cap > 0 && p2p_b_smem(P->p2p_cap) <= 200 * 1024;
+}
+
+void batch_setup(hfmm_plan* P, int R, cudaStream_t st) {
+    BatchState& B = P->batch;
+    if (B.R == R && B.sig.p) return;
+    if (B.graph) {
+        HFMM_CUDA(cudaGraphExecDestroy(B.graph));
+        B.graph = nullptr;
+    }
+    B.R = R;
+    const int64_t N = P->N;
+    size_t cnt = 0;
+    B.sig.alloc((size_t)N * R, &cnt);
+    B.phi.alloc((size_t)N * R, &cnt);
+    B.coef.alloc((size_t)std::max<int64_t>(P->coef_total, 1) * R, &cnt);
+    // one item per translation, R columns; offsets of the level arrays scale by R
+    const auto& hi = P->host_items;
+    std::vector<TransItem> items;
+    std::vector<int64_t> start(hi.size() + 1, 0);
+    for (size_t q = 0; q < hi.size(); ++q) {
+        start[q] = (int64_t)items.size();
+        for (int c = 0; c < hi[q].ncol; ++c) {
+            TransItem t = hi[q];
+            t.src = hi[q].src * R;
+            t.dst = hi[q].dst * R;
+            t.cols = hi[q].cols + c;
+            t.ncol = (int16_t)R;
+            items.push_back(t);
+        }
+    }
+    start[hi.size()] = (int64_t)items.size();
+    const int L = P->L;
+    B.m2m_items.assign(L + 2, {0, 0});
+    B.l2l_items.assign(L + 2, {0, 0});
+    for (int l = 0; l <= L && l < (int)P->m2m_items_begin.size(); ++l)
+        B.m2m_items[l] = {start[P->m2m_items_begin[l]], start[P->m2m_items_end[l]]};
+    for (int l = 0; l <= L && l < (int)P->l2l_items_begin.size(); ++l)
+        B.l2l_items[l] = {start[P->l2l_items_begin[l]], start[P->l2l_items_end[l]]};
+    B.m2l_simt.clear();
+    for (const SimtRange& r : P->m2l_simt) B.m2l_simt.push_back({start[r.begin], start[r.end], r.pout_max, R});
+    // tensor-core groups: each single-column group becomes runs of up to m2l_tc_max_group() items
+    const int gmax = m2l_tc_max_group();
+    std::vector<int4> groups;
+    auto regroup = [&](int64_t g0, int64_t g1) {
+        const int64_t before = (int64_t)groups.size();
+        for (int64_t g = g0; g < g1; ++g) {
+            const int4 sg = P->host_groups[g];
+            for (int64_t b = start[sg.x]; b < start[sg.x + sg.y]; b += gmax)
+                groups.push_back(make_int4((int)b, (int)std::min<int64_t>(gmax, start[sg.x + sg.y] - b), sg.z, sg.w));
+        }
+        return std::make_pair(before, (int64_t)groups.size());
+    };
+    B.n_tc_m2l = regroup(0, P->n_tc_groups).second;
+    B.m2m_tc.assign(L + 2, {0, 0});
+    B.l2l_tc.assign(L + 2, {0, 0});
+    for (int l = 0; l <= L && l < (int)P->m2m_tc.size(); ++l) B.m2m_tc[l] = regroup(P->m2m_tc[l].first, P->m2m_tc[l].second);
+    for (int l = 0; l <= L && l < (int)P->l2l_tc.size(); ++l) B.l2l_tc[l] = regroup(P->l2l_tc[l].first, P->l2l_tc[l].second);
+    B.items.upload(items, &cnt, st);
+    B.tc_groups.upload(groups, &cnt, st);
+    P->dev_bytes += cnt;
+    // shared-memory limits above 48 KiB, set before any capture
+    m2l_tc_init();
+    const size_t sp2p = p2p_b_smem(P->p2p_cap);
+    HFMM_CUDA(cudaFuncSetAttribute(k_p2p_b<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sp2p));
+    HFMM_CUDA(cudaFuncSetAttribute(k_p2p_b<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sp2p));
+    if (L >= 2) {
+        const int Pl = P->lev[L].P;
+        HFMM_CUDA(cudaFuncSetAttribute(k_p2m_b, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p2m_b_smem(Pl)));
+        HFMM_CUDA(cudaFuncSetAttribute(k_l2p_b, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)l2p_b_smem(Pl)));
+    }
+}
+
+void run_matvec_batched(hfmm_plan* P, const float2* density, float2* potential, cudaStream_t st) {
+    BatchState& B = P->batch;
+    const int64_t N = P->N;
+    const int R = B.R;
+    const unsigned nb32 = (unsigned)((N + 31) / 32);
+    k_prep_b<<<nb32, 256, 0, st>>>(N, R, P->perm.p, P->wscale.p, density, B.sig.p);
+    const size_t sp2p = p2p_b_smem(P->p2p_cap);
+    if (P->poly_p2p)
+        k_p2p_b<true><<<(unsigned)P->nleaf, 256, sp2p, st>>>(P->leaf_start.p, P->leaf_ijk.p, P->nbr_ptr.p, P->nbr.p,
+                                                             P->pts.p, B.sig.p, P->p2p_shift, P->p2p_cap, R, B.phi.p);
+    else
+        k_p2p_b<false><<<(unsigned)P->nleaf, 256, sp2p, st>>>(P->leaf_start.p, P->leaf_ijk.p, P->nbr_ptr.p, P->nbr.p,
+                                                              P->pts.p, B.sig.p, P->p2p_shift, P->p2p_cap, R, B.phi.p);
+    P->launches += 2;
+    const int L = P->L;
+    if (L >= 2) {
+        HFMM_CUDA(cudaMemsetAsync(B.coef.p, 0, sizeof(float2) * P->coef_total * R, st));
+        const LevelInfo& lv = P->lev[L];
+        k_p2m_b<<<(unsigned)P->nleaf, 256, p2m_b_smem(lv.P), st>>>(P->leaf_start.p, P->pts.p, B.sig.p, lv.p,
+                                                                  (float)lv.s, R, B.coef.p + lv.mofs * R);
+        ++P->launches;
+        for (int l = L - 1; l >= 2; --l) {
+            const auto& g = B.m2m_tc[l];
+            if (g.second > g.first) {
+                m2l_tc_launch(B.tc_groups.p + g.first, g.second - g.first, B.items.p, P->item_cols.p, P->aops.p,
+                              B.coef.p, P->dev_err.p, R, st);
+                ++P->launches;
+            } else {
+                launch_translate(P, B.items.p, B.coef.p, R, B.m2m_items[l].first, B.m2m_items[l].second, P->lev[l].P,
+                                 R, st);
+            }
+        }
+        for (const SimtRange& r : B.m2l_simt)
+            launch_translate(P, B.items.p, B.coef.p, R, r.begin, r.end, r.pout_max, r.width, st);
+        if (B.n_tc_m2l > 0) {
+            m2l_tc_launch(B.tc_groups.p, B.n_tc_m2l, B.items.p, P->item_cols.p, P->aops.p, B.coef.p, P->dev_err.p, R,
+                          st);
+            ++P->launches;
+        }
+        for (int l = 3; l <= L; ++l) {
+            const auto& g = B.l2l_tc[l];
+            if (g.second > g.first) {
+                m2l_tc_launch(B.tc_groups.p + g.first, g.second - g.first, B.items.p, P->item_cols.p, P->aops.p,
+                              B.coef.p, P->dev_err.p, R, st);
+                ++P->launches;
+            } else {
+                launch_translate(P, B.items.p, B.coef.p, R, B.l2l_items[l].first, B.l2l_items[l].second, P->lev[l].P,
+                                 R, st);
+            }
+        }
+        k_l2p_b<<<(unsigned)P->nleaf, 256, l2p_b_smem(lv.P), st>>>(P->leaf_start.p, P->pts.p, lv.p, (float)lv.s, R,
+                                                                  B.coef.p + lv.lofs * R, B.phi.p);
+        ++P->launches;
+    }
+    if (P->corr_nnz > 0) {
+        k_corr_b<<<(unsigned)((N * 32 + 255) / 256), 256, 0, st>>>(N, R, P->corr_ptr.p, P->corr_col.p, P->corr_val.p,
+                                                                  B.sig.p, B.phi.p);
+        ++P->launches;
+    }
+    k_output_b<<<nb32, 256, 0, st>>>(N, R, P->perm.p, B.phi.p, potential);
+    ++P->launches;
     HFMM_CUDA(cudaGetLastError());
 }
 

@@ -95,6 +95,30 @@ struct LevelInfo {
     int64_t m2m_op = 0;     // offset of 8 M2M operators [8][P_parent][P] (levels >= 3)
 };
 
+// State of the batched (multiple right-hand side) matvec for R = 2..64 right-hand sides.
+// Expansions are laid out [box][rhs][P], so the R expansions of one box are one
+// contiguous block and a translation between two boxes is a work item of R columns
+// (column index box * R + r); densities and potentials are [point][rhs].
+struct BatchState {
+    int R = 0;
+    DBuf<float2> sig, phi, coef;     // [N][R], [N][R], [coef_total][R]
+    DBuf<TransItem> items;           // one item per translation (R columns)
+    DBuf<int4> tc_groups;            // tensor-core groups over `items`
+    int64_t n_tc_m2l = 0;            // the first n_tc_m2l groups are M2L
+    std::vector<std::pair<int64_t, int64_t>> m2m_tc, l2l_tc;       // group ranges per level
+    std::vector<std::pair<int64_t, int64_t>> m2m_items, l2l_items;  // item ranges per level (SIMT)
+    std::vector<SimtRange> m2l_simt;
+    cudaStream_t cap_stream = nullptr;  // private stream the graph is captured on
+    cudaGraphExec_t graph = nullptr;    // the captured batched matvec
+    const void* g_in = nullptr;
+    void* g_out = nullptr;
+    int64_t g_launches = 0;             // kernels in one replay
+    ~BatchState() {
+        if (graph) cudaGraphExecDestroy(graph);
+        if (cap_stream) cudaStreamDestroy(cap_stream);
+    }
+};
+
 struct hfmm_plan {
     hfmm_config cfg;
     double k = 0.0;
@@ -130,6 +154,8 @@ struct hfmm_plan {
     DBuf<float2> ops;          // all translation operators
     DBuf<TransItem> items;
     DBuf<int2> item_cols;
+    std::vector<TransItem> host_items;  // host copies, for the batched work lists
+    std::vector<int4> host_groups;
     std::vector<int64_t> m2m_items_begin, m2m_items_end;  // per level l (parents at l)
     std::vector<int64_t> l2l_items_begin, l2l_items_end;  // per level l (children at l)
     int64_t m2l_items_begin = 0, m2l_items_end = 0;
@@ -153,6 +179,7 @@ struct hfmm_plan {
     int64_t launches = 0;       // kernels launched by this plan
     double cost[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // see hfmm_plan_costs
     cudaEvent_t* stage_ev = nullptr;  // set by hfmm_matvec_timed: events after each stage
+    BatchState batch;
 };
 
 // ---------------------------------------------------------------- kernels: FMM matvec
@@ -163,10 +190,10 @@ __device__ __forceinline__ void red_add(float2* p, float2 v) {
     asm volatile("red.global.add.v2.f32 [%0], {%1, %2};" ::"l"(p), "f"(v.x), "f"(v.y) : "memory");
 }
 
-// sig_sorted = k w / (4 pi) * density[perm]  (one right-hand side)
 // Complex vectors the matvec reads and writes: complex64, or double-float complex
 // (float4 = re_hi, im_hi, re_lo, im_lo; value = hi + lo) for the Krylov solver.
 enum class VecKind { Complex64, DoubleFloat };
+// sig_sorted = k w / (4 pi) * density[perm]  (one right-hand side)
 void launch_density_prep(hfmm_plan* P, const void* density, VecKind kind, float2* sig, cudaStream_t st);
 // out[perm[i]] = phi[i]
 void launch_output(hfmm_plan* P, const float2* phi, void* out, VecKind kind, cudaStream_t st);
@@ -175,6 +202,12 @@ void run_matvec_sorted(hfmm_plan* P, int parts, cudaStream_t st);
 // records stage event q (if timing is active)
 void mark_stage(hfmm_plan* P, int q, cudaStream_t st);
 void run_direct_sorted(hfmm_plan* P, cudaStream_t st);
+// Batched matvec for R right-hand sides (BatchState): whether this plan supports it,
+// building the work lists and buffers, and one matvec (density, potential: device
+// complex64, N x R column-major, user order).
+bool batch_supported(const hfmm_plan* P, int R);
+void batch_setup(hfmm_plan* P, int R, cudaStream_t st);
+void run_matvec_batched(hfmm_plan* P, const float2* density, float2* potential, cudaStream_t st);
 void launch_planewave(hfmm_plan* P, double dx, double dy, double dz, float2* out, cudaStream_t st);
 // copies the normalised Legendre recurrence tables to the current device (once per device)
 void upload_legendre_tables();
@@ -217,8 +250,11 @@ int64_t build_correction(hfmm_plan* P, const CorrInputs& in, cudaStream_t st);
 size_t m2l_tc_op_elems();  // BF16 elements per packed operator (hi + lo)
 int m2l_tc_max_group();    // work items per tensor-core block
 void m2l_tc_pack(const float2* T, int P, int nops, uint16_t* out, cudaStream_t st);
+void m2l_tc_init();        // sets the kernel's shared-memory limit on the current device (idempotent)
+// rhs > 1: batched items, each holding one (source box, target box) pair in `cols` and
+// standing for the rhs columns (box * rhs + r); their src / dst offsets are already scaled
 void m2l_tc_launch(const int4* groups, int64_t ngroups, const TransItem* items, const int2* cols,
-                   const uint16_t* aops, float2* coef, int* err, cudaStream_t st);
+                   const uint16_t* aops, float2* coef, int* err, int rhs, cudaStream_t st);
 
 // ---------------------------------------------------------------- GMRES
 int run_gmres(hfmm_plan* P, const void* rhs, void* x, int* iters, double* relres, cudaStream_t st);

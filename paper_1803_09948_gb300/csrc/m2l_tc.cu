@@ -214,7 +214,7 @@ __device__ __forceinline__ bool epilogue_all(bool v) {
 
 __global__ void __launch_bounds__(kThreads, 1)
     k_m2l_tc(const int4* __restrict__ groups, const TransItem* __restrict__ items, const int2* __restrict__ cols,
-             const __nv_bfloat16* __restrict__ aops, float2* __restrict__ coef, int* __restrict__ err) {
+             const __nv_bfloat16* __restrict__ aops, float2* __restrict__ coef, int* __restrict__ err, int rhs) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     TcSmem& S = *reinterpret_cast<TcSmem*>(smem_raw);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -248,7 +248,16 @@ __global__ void __launch_bounds__(kThreads, 1)
         __syncthreads();
         for (int q = tid; q < nitems * kN; q += kThreads) {
             const int w = q / kN, c = q % kN;
-            S.cols[w][c] = c < S.items[w].ncol ? cols[S.items[w].cols + c] : make_int2(0, 0);
+            int2 v = make_int2(0, 0);
+            if (c < S.items[w].ncol) {
+                if (rhs > 1) {  // one box pair, columns box * rhs + c
+                    const int2 pr = cols[S.items[w].cols];
+                    v = make_int2(pr.x * rhs + c, pr.y * rhs + c);
+                } else {
+                    v = cols[S.items[w].cols + c];
+                }
+            }
+            S.cols[w][c] = v;
         }
         // K beyond 2P stays zero in B (A is zero there too), so no stale NaN enters a product
         uint4* bz = reinterpret_cast<uint4*>(&S.b[0][0][0]);
@@ -517,13 +526,24 @@ void m2l_tc_pack(const float2* T, int P, int nops, uint16_t* out, cudaStream_t s
     HFMM_CUDA(cudaGetLastError());
 }
 
+void m2l_tc_init() {
+    // once per device, so that a later launch inside a stream capture sets nothing
+    static bool attr_set[64] = {};
+    int dev = 0;
+    HFMM_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64 || !attr_set[dev]) {
+        HFMM_CUDA(cudaFuncSetAttribute(k_m2l_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(TcSmem)));
+        if (dev >= 0 && dev < 64) attr_set[dev] = true;
+    }
+}
+
 void m2l_tc_launch(const int4* groups, int64_t ngroups, const TransItem* items, const int2* cols,
-                   const uint16_t* aops, float2* coef, int* err, cudaStream_t st) {
+                   const uint16_t* aops, float2* coef, int* err, int rhs, cudaStream_t st) {
     if (ngroups <= 0) return;
-    size_t smem = sizeof(TcSmem);
-    HFMM_CUDA(cudaFuncSetAttribute(k_m2l_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const size_t smem = sizeof(TcSmem);
+    m2l_tc_init();
     k_m2l_tc<<<(unsigned)ngroups, kThreads, smem, st>>>(groups, items, cols,
-                                                   reinterpret_cast<const __nv_bfloat16*>(aops), coef, err);
+                                                   reinterpret_cast<const __nv_bfloat16*>(aops), coef, err, rhs);
     HFMM_CUDA(cudaGetLastError());
 }
 

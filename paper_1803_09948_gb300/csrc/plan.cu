@@ -569,6 +569,8 @@ static void build_plan(hfmm_plan* P, const double* V, int64_t nv, const int32_t*
         P->tc_groups.upload(groups, cnt, st);
         P->items.upload(items, cnt, st);
         P->item_cols.upload(cols, cnt, st);
+        P->host_items = std::move(items);
+        P->host_groups = std::move(groups);
     }
 
     // ---------------------------------------------------------- self / near correction (Sec. 2.2)
@@ -713,16 +715,59 @@ int hfmm_plan_info(const hfmm_plan* P, int* depth, int* orders, int64_t* n_leave
     return HFMM_OK;
 }
 
+// R right-hand sides (2..64) in one batched matvec, replayed from a CUDA graph captured on
+// the plan's own stream (the caller's stream may be the legacy default stream, which cannot
+// be captured) and re-captured when the buffers change.
+static void batched_matvec(hfmm_plan* P, const float2* d, float2* o, int R, cudaStream_t st) {
+    BatchState& B = P->batch;
+    batch_setup(P, R, st);
+    if (!B.cap_stream) HFMM_CUDA(cudaStreamCreateWithFlags(&B.cap_stream, cudaStreamNonBlocking));
+    if (!B.graph || B.g_in != (const void*)d || B.g_out != (void*)o) {
+        if (B.graph) {
+            HFMM_CUDA(cudaGraphExecDestroy(B.graph));
+            B.graph = nullptr;
+        }
+        const int64_t l0 = P->launches;
+        cudaGraph_t g = nullptr;
+        HFMM_CUDA(cudaStreamBeginCapture(B.cap_stream, cudaStreamCaptureModeThreadLocal));
+        try {
+            run_matvec_batched(P, d, o, B.cap_stream);
+        } catch (...) {
+            cudaStreamEndCapture(B.cap_stream, &g);
+            if (g) cudaGraphDestroy(g);
+            P->launches = l0;
+            throw;
+        }
+        HFMM_CUDA(cudaStreamEndCapture(B.cap_stream, &g));
+        const cudaError_t e = cudaGraphInstantiate(&B.graph, g, 0);
+        cudaGraphDestroy(g);
+        HFMM_CUDA(e);
+        B.g_launches = P->launches - l0;
+        P->launches = l0;
+        B.g_in = d;
+        B.g_out = o;
+    }
+    HFMM_CUDA(cudaGraphLaunch(B.graph, st));
+    P->launches += B.g_launches;
+}
+
 int hfmm_matvec_parts(hfmm_plan* P, const void* density, void* potential, int nrhs, int parts, void* stream) {
     if (!P || !density || !potential || nrhs < 1 || parts < 0 || parts > 7) return HFMM_E_INVALID;
     HFMM_GUARD_BEGIN
     cudaStream_t st = (cudaStream_t)stream;
-    for (int r = 0; r < nrhs; ++r) {
-        const float2* d = (const float2*)density + (int64_t)r * P->N;
-        float2* o = (float2*)potential + (int64_t)r * P->N;
+    for (int r0 = 0; r0 < nrhs;) {
+        const int R = std::min(nrhs - r0, 64);
+        const float2* d = (const float2*)density + (int64_t)r0 * P->N;
+        float2* o = (float2*)potential + (int64_t)r0 * P->N;
+        if (parts == 7 && R > 1 && batch_supported(P, R)) {
+            batched_matvec(P, d, o, R, st);
+            r0 += R;
+            continue;
+        }
         launch_density_prep(P, d, VecKind::Complex64, P->sig.p, st);
         run_matvec_sorted(P, parts, st);
         launch_output(P, P->phi.p, o, VecKind::Complex64, st);
+        ++r0;
     }
     HFMM_CUDA(cudaGetLastError());
     return HFMM_OK;
