@@ -308,46 +308,32 @@ __global__ void __launch_bounds__(kThreads, 1)
             const int ncol = it.ncol;
             __nv_bfloat16* bh = &S.b[s][0][0];
             __nv_bfloat16* bl = &S.b[s][1][0];
-            if ((P & 7) == 0 && nchunk * kN == 2 * kProducers) {
-                // P = 64: two (column, chunk) tasks per thread, lanes on consecutive columns;
-                // all loads in flight before any use, split with packed BF16 pairs
-                const int c = pt & (kN - 1);
+            if (P == kN && kProducers == 8 * 32) {
+                // P = 64: producer warp q takes columns 8q..8q+7, four lanes per column, each
+                // lane the float4s j, j+4, ..., j+28 of its column (complex elements 2(j+4t),
+                // 2(j+4t)+1): a load touches 8 lines, and the 32 lanes' 4-byte stores fill one
+                // 128-byte core matrix, no bank conflict
+                const int c = (warp - 4) * 8 + (lane >> 2), j = lane & 3;
                 const bool valid = c < ncol;
-                const int cidx = valid ? S.cols[w][c].x : 0;
-                float4 v[2][4];
+                const float4* x4 =
+                    reinterpret_cast<const float4*>(coef + it.src + (int64_t)(valid ? S.cols[w][c].x : 0) * P);
+                float4 v[8];
 #pragma unroll
-                for (int q = 0; q < 2; ++q) {
-                    const int j = (pt >> 6) + 4 * q;
-                    const float4* x4 = reinterpret_cast<const float4*>(coef + it.src + (int64_t)cidx * P + 8 * j);
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) v[q][e] = valid ? __ldg(x4 + e) : make_float4(0.f, 0.f, 0.f, 0.f);
-                }
+                for (int t = 0; t < 8; ++t) v[t] = valid ? __ldg(x4 + j + 4 * t) : make_float4(0.f, 0.f, 0.f, 0.f);
                 if (valid) {
 #pragma unroll
-                    for (int q = 0; q < 2; ++q) {
-                        const int j = (pt >> 6) + 4 * q;
-                        uint4 rh, rl, ih, il;
-                        uint32_t* prh = &rh.x;
-                        uint32_t* prl = &rl.x;
-                        uint32_t* pih = &ih.x;
-                        uint32_t* pil = &il.x;
-#pragma unroll
-                        for (int e = 0; e < 4; ++e) {
-                            const __nv_bfloat162 hr = __floats2bfloat162_rn(v[q][e].x, v[q][e].z);
-                            const __nv_bfloat162 hi = __floats2bfloat162_rn(-v[q][e].y, -v[q][e].w);
-                            const float2 br = __bfloat1622float2(hr), bi = __bfloat1622float2(hi);
-                            const __nv_bfloat162 lr = __floats2bfloat162_rn(v[q][e].x - br.x, v[q][e].z - br.y);
-                            const __nv_bfloat162 li = __floats2bfloat162_rn(-v[q][e].y - bi.x, -v[q][e].w - bi.y);
-                            prh[e] = *reinterpret_cast<const uint32_t*>(&hr);
-                            prl[e] = *reinterpret_cast<const uint32_t*>(&lr);
-                            pih[e] = *reinterpret_cast<const uint32_t*>(&hi);
-                            pil[e] = *reinterpret_cast<const uint32_t*>(&li);
-                        }
-                        const uint32_t o_re = core_index(c, 8 * j), o_im = core_index(c, P + 8 * j);
-                        *reinterpret_cast<uint4*>(bh + o_re) = rh;
-                        *reinterpret_cast<uint4*>(bl + o_re) = rl;
-                        *reinterpret_cast<uint4*>(bh + o_im) = ih;
-                        *reinterpret_cast<uint4*>(bl + o_im) = il;
+                    for (int t = 0; t < 8; ++t) {
+                        const __nv_bfloat162 hr = __floats2bfloat162_rn(v[t].x, v[t].z);
+                        const __nv_bfloat162 hi = __floats2bfloat162_rn(-v[t].y, -v[t].w);
+                        const float2 br = __bfloat1622float2(hr), bi = __bfloat1622float2(hi);
+                        const __nv_bfloat162 lr = __floats2bfloat162_rn(v[t].x - br.x, v[t].z - br.y);
+                        const __nv_bfloat162 li = __floats2bfloat162_rn(-v[t].y - bi.x, -v[t].w - bi.y);
+                        const int k = 2 * (j + 4 * t);
+                        const uint32_t o_re = core_index(c, k), o_im = core_index(c, P + k);
+                        *reinterpret_cast<__nv_bfloat162*>(bh + o_re) = hr;
+                        *reinterpret_cast<__nv_bfloat162*>(bl + o_re) = lr;
+                        *reinterpret_cast<__nv_bfloat162*>(bh + o_im) = hi;
+                        *reinterpret_cast<__nv_bfloat162*>(bl + o_im) = li;
                     }
                 }
             } else {
@@ -420,6 +406,10 @@ __global__ void __launch_bounds__(kThreads, 1)
         // every lane commits one group per item and confirms the reads of its previous
         // item before that item's stage is handed back.
         const int q = warp - kIssuerWarp;
+        // Columns per reduction at most: the bulk engine overlaps several operations, so the
+        // contiguous 32 KiB of a batched item (one box pair, rhs columns) goes out as 2 KiB
+        // pieces; single right-hand-side runs are short anyway.
+        const int opc = rhs > 1 ? 4 : kN;
         int prev = -1;
         if ((P & 1) == 0) {
             for (int w = q; w < nitems; w += kIssuers) {
@@ -437,9 +427,10 @@ __global__ void __launch_bounds__(kThreads, 1)
                     const int dc = S.cols[w][c].y;
                     uint32_t bytes = 8u * (uint32_t)P;
                     if (2 * P == kM) {
-                        if (c > 0 && S.cols[w][c - 1].y == dc - 1) continue;  // inside a run
+                        // a new operation at a run break, and every opc columns inside a run
+                        if (c > 0 && S.cols[w][c - 1].y == dc - 1 && c % opc != 0) continue;
                         int run = 1;
-                        while (c + run < ncol && S.cols[w][c + run].y == dc + run) ++run;
+                        while (c + run < ncol && (c + run) % opc != 0 && S.cols[w][c + run].y == dc + run) ++run;
                         bytes *= (uint32_t)run;
                     }
                     asm volatile("cp.reduce.async.bulk.global.shared::cta.bulk_group.add.f32 [%0], [%1], %2;" ::"l"(
