@@ -967,17 +967,33 @@ __global__ void __launch_bounds__(256) k_p2p_b(const int32_t* __restrict__ leaf_
             sj[s_off[q] + e] = j0 + e;
         }
     }
+    __syncthreads();  // staged positions and indices visible
     const int nself = s_off[1], out0 = __ldg(leaf_start + b);
-    const int tt = tid & 31, rg = tid >> 5;
+    // thread (tt, rg): targets tt + 16a (a < 2, or < 4 for more than 32 targets), right-hand
+    // sides rg + 16q (q < 4); per source 2-4 G loads and 4 density loads for 8-16 complex MACs
+    const int tt = tid & 15, rg = tid >> 4;
+    constexpr int kPre = kBChunk * kBMax / 256;  // densities per thread per chunk
     for (int t0 = 0; t0 < nself; t0 += 64) {
         const int nt = min(64, nself - t0);
         const bool two = nt > 32;  // uniform over the block
-        float2 acc0[8], acc1[8];
+        float2 acc[4][4];
 #pragma unroll
-        for (int q = 0; q < 8; ++q) acc0[q] = acc1[q] = make_float2(0.f, 0.f);
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[a][q] = make_float2(0.f, 0.f);
+        float2 pre[kPre];
+        auto fetch = [&](int s0) {
+            const int cnt = min(kBChunk, total - s0);
+#pragma unroll
+            for (int q = 0; q < kPre; ++q) {
+                const int e = tid + 256 * q, s = e / kBMax, r = e % kBMax;
+                pre[q] = (s < cnt && r < R) ? __ldg(sig + (int64_t)sj[s0 + s] * R + r) : make_float2(0.f, 0.f);
+            }
+        };
+        fetch(0);
         for (int s0 = 0; s0 < total; s0 += kBChunk) {
             const int cnt = min(kBChunk, total - s0);
-            __syncthreads();  // staging done / previous chunk consumed
+            __syncthreads();  // previous chunk consumed
             for (int e = tid; e < kBChunk * 64; e += 256) {
                 const int s = e >> 6, t = e & 63;
                 float2 g = make_float2(0.f, 0.f);
@@ -997,32 +1013,37 @@ __global__ void __launch_bounds__(256) k_p2p_b(const int32_t* __restrict__ leaf_
                 }
                 G[e] = g;
             }
-            for (int e = tid; e < kBChunk * kBMax; e += 256) {
-                const int s = e / kBMax, r = e % kBMax;
-                Sg[e] = (s < cnt && r < R) ? __ldg(sig + (int64_t)sj[s0 + s] * R + r) : make_float2(0.f, 0.f);
-            }
-            __syncthreads();
-            for (int s = 0; s < cnt; ++s) {
-                const float2 g0 = G[s * 64 + tt];
-                const float2 g1 = two ? G[s * 64 + tt + 32] : make_float2(0.f, 0.f);
 #pragma unroll
-                for (int q = 0; q < 8; ++q) {
-                    const float2 v = Sg[s * kBMax + rg + 8 * q];
-                    acc0[q].x = fmaf(g0.x, v.x, fmaf(-g0.y, v.y, acc0[q].x));
-                    acc0[q].y = fmaf(g0.x, v.y, fmaf(g0.y, v.x, acc0[q].y));
-                    if (two) {
-                        acc1[q].x = fmaf(g1.x, v.x, fmaf(-g1.y, v.y, acc1[q].x));
-                        acc1[q].y = fmaf(g1.x, v.y, fmaf(g1.y, v.x, acc1[q].y));
+            for (int q = 0; q < kPre; ++q) Sg[tid + 256 * q] = pre[q];
+            __syncthreads();
+            if (s0 + kBChunk < total) fetch(s0 + kBChunk);  // overlaps the multiply below
+            for (int s = 0; s < cnt; ++s) {
+                float2 v[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) v[q] = Sg[s * kBMax + rg + 16 * q];
+#pragma unroll
+                for (int a = 0; a < 4; ++a) {
+                    if (a >= 2 && !two) break;
+                    const float2 g = G[s * 64 + tt + 16 * a];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        acc[a][q].x = fmaf(g.x, v[q].x, fmaf(-g.y, v[q].y, acc[a][q].x));
+                        acc[a][q].y = fmaf(g.x, v[q].y, fmaf(g.y, v[q].x, acc[a][q].y));
                     }
                 }
             }
         }
+        // potentials through shared memory (G and Sg are one 64 x 64 tile), then coalesced
+        __syncthreads();
+        float2* T = G;
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            const int r = rg + 8 * q;
-            if (r >= R) continue;
-            if (tt < nt) phi[(int64_t)(out0 + t0 + tt) * R + r] = acc0[q];
-            if (two && tt + 32 < nt) phi[(int64_t)(out0 + t0 + tt + 32) * R + r] = acc1[q];
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) T[(tt + 16 * a) * kBMax + rg + 16 * q] = acc[a][q];
+        __syncthreads();
+        for (int e = tid; e < nt * R; e += 256) {
+            const int t = e / R, r = e % R;
+            phi[(int64_t)(out0 + t0) * R + e] = T[t * kBMax + r];
         }
     }
 }
@@ -1200,6 +1221,69 @@ void batch_setup(hfmm_plan* P, int R, cudaStream_t st) {
         }
     }
     start[hi.size()] = (int64_t)items.size();
+    // M2L on the tensor cores: order the items by (level, tile of kTile target boxes, operator,
+    // target) so that the blocks running at one time cover one tile of targets and all its
+    // offsets; the tile's local expansions and its neighbourhood's multipoles (R times the
+    // single right-hand-side sizes) then stay in L2 while they are reused.
+    const int gmax = m2l_tc_max_group();
+    std::vector<int4> groups;
+    {
+        constexpr int kTile = 256;
+        struct Key {
+            int64_t dst_base;
+            int tile, opi;
+            int32_t dst;
+            int64_t item;
+            int P;
+        };
+        std::vector<Key> keys;
+        for (int64_t g = 0; g < P->n_tc_groups; ++g) {
+            const int4 sg = P->host_groups[g];
+            for (int64_t b = start[sg.x]; b < start[sg.x + sg.y]; ++b) {
+                const int32_t dst = P->host_cols[items[b].cols].y;
+                keys.push_back({items[b].dst, dst / kTile, sg.z, dst, b, sg.w});
+            }
+        }
+        std::stable_sort(keys.begin(), keys.end(), [](const Key& a, const Key& b) {
+            if (a.dst_base != b.dst_base) return a.dst_base < b.dst_base;
+            if (a.tile != b.tile) return a.tile < b.tile;
+            if (a.opi != b.opi) return a.opi < b.opi;
+            return a.dst < b.dst;
+        });
+        // the M2L tensor-core items go first, in this order; the rest keep theirs
+        std::vector<TransItem> tc_items;
+        tc_items.reserve(keys.size());
+        for (size_t q = 0; q < keys.size(); ++q) {
+            tc_items.push_back(items[keys[q].item]);
+            if (q == 0 || keys[q].dst_base != keys[q - 1].dst_base || keys[q].tile != keys[q - 1].tile ||
+                keys[q].opi != keys[q - 1].opi || groups.back().y == gmax)
+                groups.push_back(make_int4((int)q, 1, keys[q].opi, keys[q].P));
+            else
+                ++groups.back().y;
+        }
+        B.n_tc_m2l = (int64_t)groups.size();
+        // append the remaining items after the reordered block, shifting every range
+        const int64_t ntc = (int64_t)tc_items.size();
+        std::vector<char> is_tc(items.size(), 0);
+        for (const Key& k : keys) is_tc[k.item] = 1;
+        std::vector<int64_t> remap(items.size() + 1, 0);
+        int64_t pos = ntc;
+        for (size_t q = 0; q < items.size(); ++q) {
+            remap[q] = is_tc[q] ? -1 : pos;
+            if (!is_tc[q]) {
+                tc_items.push_back(items[q]);
+                ++pos;
+            }
+        }
+        remap[items.size()] = pos;
+        // start[] maps single items to batched items; send non-M2L-tensor-core ranges through remap
+        for (size_t q = 0; q < start.size(); ++q) {
+            int64_t b = start[q];
+            while (b < (int64_t)items.size() && is_tc[b]) ++b;  // a range never begins inside the M2L block
+            start[q] = remap[b];
+        }
+        items.swap(tc_items);
+    }
     const int L = P->L;
     B.m2m_items.assign(L + 2, {0, 0});
     B.l2l_items.assign(L + 2, {0, 0});
@@ -1209,9 +1293,6 @@ void batch_setup(hfmm_plan* P, int R, cudaStream_t st) {
         B.l2l_items[l] = {start[P->l2l_items_begin[l]], start[P->l2l_items_end[l]]};
     B.m2l_simt.clear();
     for (const SimtRange& r : P->m2l_simt) B.m2l_simt.push_back({start[r.begin], start[r.end], r.pout_max, R});
-    // tensor-core groups: each single-column group becomes runs of up to m2l_tc_max_group() items
-    const int gmax = m2l_tc_max_group();
-    std::vector<int4> groups;
     auto regroup = [&](int64_t g0, int64_t g1) {
         const int64_t before = (int64_t)groups.size();
         for (int64_t g = g0; g < g1; ++g) {
@@ -1221,7 +1302,6 @@ void batch_setup(hfmm_plan* P, int R, cudaStream_t st) {
         }
         return std::make_pair(before, (int64_t)groups.size());
     };
-    B.n_tc_m2l = regroup(0, P->n_tc_groups).second;
     B.m2m_tc.assign(L + 2, {0, 0});
     B.l2l_tc.assign(L + 2, {0, 0});
     for (int l = 0; l <= L && l < (int)P->m2m_tc.size(); ++l) B.m2m_tc[l] = regroup(P->m2m_tc[l].first, P->m2m_tc[l].second);

@@ -155,6 +155,7 @@ struct hfmm_plan {
     DBuf<TransItem> items;
     DBuf<int2> item_cols;
     std::vector<TransItem> host_items;  // host copies, for the batched work lists
+    std::vector<int2> host_cols;
     std::vector<int4> host_groups;
     std::vector<int64_t> m2m_items_begin, m2m_items_end;  // per level l (parents at l)
     std::vector<int64_t> l2l_items_begin, l2l_items_end;  // per level l (children at l)

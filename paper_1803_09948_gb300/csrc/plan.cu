@@ -570,6 +570,7 @@ static void build_plan(hfmm_plan* P, const double* V, int64_t nv, const int32_t*
         P->items.upload(items, cnt, st);
         P->item_cols.upload(cols, cnt, st);
         P->host_items = std::move(items);
+        P->host_cols = std::move(cols);
         P->host_groups = std::move(groups);
     }
 
