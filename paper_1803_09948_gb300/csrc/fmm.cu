@@ -242,14 +242,21 @@ __global__ void __launch_bounds__(128) k_p2p_staged(const int32_t* __restrict__ 
 
 // ============================================================== FP32 special functions
 // out[n] = j_n(x) / s^n, n = 0..p
+// Reciprocals for the small-argument series of j_n (uploaded with the Legendre tables):
+// c_jser[n][q] = 1 / (q (2n + 2q + 1)), c_inv_odd[n] = 1 / (2n + 1).
+constexpr int kJTerms = 24;
+__constant__ float c_jser[HFMM_PMAX + 1][kJTerms];
+__constant__ float c_inv_odd[HFMM_PMAX + 1];
+
 __device__ static void f_jn_scaled(int p, float x, float s, float* out) {
     if (x < 2.0f) {
+        // j_n(x) / s^n = (x/s)^n / (2n+1)!! * sum_q prod_{i<=q} (-x^2/2) / (i (2n+2i+1))
         float lead = 1.0f, xs = x / s, h = -0.5f * x * x;
         for (int n = 0; n <= p; ++n) {
-            if (n) lead *= xs / (float)(2 * n + 1);
+            if (n) lead *= xs * c_inv_odd[n];
             float term = 1.0f, sum = 1.0f;
-            for (int q = 1; q < 24; ++q) {
-                term *= h / (float)(q * (2 * n + 2 * q + 1));
+            for (int q = 1; q < kJTerms; ++q) {
+                term *= h * c_jser[n][q];
                 sum += term;
                 if (fabsf(term) < 1e-8f * fabsf(sum)) break;
             }
@@ -341,6 +348,13 @@ void upload_legendre_tables() {
     HFMM_CUDA(cudaMemcpyToSymbol(c_leg_a, a.data(), sizeof(float) * kLegH));
     HFMM_CUDA(cudaMemcpyToSymbol(c_leg_b, b.data(), sizeof(float) * kLegH));
     HFMM_CUDA(cudaMemcpyToSymbol(c_leg_qmm, q.data(), sizeof(float) * (HFMM_PMAX + 1)));
+    std::vector<float> js((HFMM_PMAX + 1) * kJTerms, 0.f), io(HFMM_PMAX + 1, 0.f);
+    for (int n = 0; n <= HFMM_PMAX; ++n) {
+        io[n] = (float)(1.0 / (2.0 * n + 1.0));
+        for (int t = 1; t < kJTerms; ++t) js[n * kJTerms + t] = (float)(1.0 / ((double)t * (2.0 * n + 2.0 * t + 1.0)));
+    }
+    HFMM_CUDA(cudaMemcpyToSymbol(c_jser, js.data(), sizeof(float) * js.size()));
+    HFMM_CUDA(cudaMemcpyToSymbol(c_inv_odd, io.data(), sizeof(float) * io.size()));
     if (dev < 64) done[dev] = true;
 }
 
