@@ -248,20 +248,23 @@ constexpr int kJTerms = 24;
 __constant__ float c_jser[HFMM_PMAX + 1][kJTerms];
 __constant__ float c_inv_odd[HFMM_PMAX + 1];
 
+// j_n(x) / s^n for x < 2: (x/s)^n / (2n+1)!! * sum_q prod_{i<=q} (-x^2/2) / (i (2n+2i+1))
+__device__ __forceinline__ float f_jn_series(int n, float x, float s) {
+    float lead = 1.0f;
+    const float xs = x / s, h = -0.5f * x * x;
+    for (int i = 1; i <= n; ++i) lead *= xs * c_inv_odd[i];
+    float term = 1.0f, sum = 1.0f;
+    for (int q = 1; q < kJTerms; ++q) {
+        term *= h * c_jser[n][q];
+        sum += term;
+        if (fabsf(term) < 1e-8f * fabsf(sum)) break;
+    }
+    return lead * sum;
+}
+
 __device__ static void f_jn_scaled(int p, float x, float s, float* out) {
     if (x < 2.0f) {
-        // j_n(x) / s^n = (x/s)^n / (2n+1)!! * sum_q prod_{i<=q} (-x^2/2) / (i (2n+2i+1))
-        float lead = 1.0f, xs = x / s, h = -0.5f * x * x;
-        for (int n = 0; n <= p; ++n) {
-            if (n) lead *= xs * c_inv_odd[n];
-            float term = 1.0f, sum = 1.0f;
-            for (int q = 1; q < kJTerms; ++q) {
-                term *= h * c_jser[n][q];
-                sum += term;
-                if (fabsf(term) < 1e-8f * fabsf(sum)) break;
-            }
-            out[n] = lead * sum;
-        }
+        for (int n = 0; n <= p; ++n) out[n] = f_jn_series(n, x, s);
         return;
     }
     int top = p + 16 + (int)x;
@@ -376,6 +379,7 @@ __global__ void __launch_bounds__(128) k_p2m(const int32_t* __restrict__ leaf_st
     float* B = rad + kChunk * (p + 1);        // [kChunk][H]
     float* E = B + kChunk * H;                // [kChunk][p+1][4]
     float* geo = E + kChunk * (p + 1) * 4;    // [kChunk][4]: cos t, sin t, cos phi, sin phi
+    float* rr = geo + kChunk * 4;             // [kChunk]: k r
     const int32_t b0 = leaf_start[leaf], b1 = leaf_start[leaf + 1];
     // two coefficients per thread per pass; orders above 14 take more passes
     for (int cg = 0; cg < P; cg += 256) {
@@ -399,13 +403,26 @@ __global__ void __launch_bounds__(128) k_p2m(const int32_t* __restrict__ leaf_st
                 const int j = threadIdx.x;
                 const float4 y = pts[j0 + j];
                 const Dir d = make_dir(y.x, y.y, y.z);
-                float jr[HFMM_PMAX + 1];
-                f_jn_scaled(p, d.r, s, jr);
-                for (int q = 0; q <= p; ++q) rad[j * (p + 1) + q] = jr[q];
                 geo[4 * j + 0] = d.ct;
                 geo[4 * j + 1] = d.st;
                 geo[4 * j + 2] = d.ex;
                 geo[4 * j + 3] = d.ey;
+                rr[j] = d.r;
+            }
+            __syncthreads();
+            // radial functions, one (order, point) per task; a point with k r >= 2 (large
+            // leaves at high frequency) takes the whole recurrence in its order-0 task
+            for (int task = threadIdx.x; task < (p + 1) * kChunk; task += blockDim.x) {
+                const int n = task / kChunk, j = task % kChunk;
+                if (j >= cnt) continue;
+                const float x = rr[j];
+                if (x < 2.0f) {
+                    rad[j * (p + 1) + n] = f_jn_series(n, x, s);
+                } else if (n == 0) {
+                    float jr[HFMM_PMAX + 1];
+                    f_jn_scaled(p, x, s, jr);
+                    for (int q = 0; q <= p; ++q) rad[j * (p + 1) + q] = jr[q];
+                }
             }
             __syncthreads();
             for (int task = threadIdx.x; task < (p + 1) * kChunk; task += blockDim.x) {
@@ -457,7 +474,7 @@ __global__ void __launch_bounds__(128) k_p2m(const int32_t* __restrict__ leaf_st
 
 size_t p2m_smem_bytes(int p) {
     const int H = (p + 1) * (p + 2) / 2;
-    return sizeof(float) * (32 * (p + 1) + 32 * H + 32 * (p + 1) * 4 + 128);
+    return sizeof(float) * (32 * (p + 1) + 32 * H + 32 * (p + 1) * 4 + 128 + 32);
 }
 
 // ============================================================== L2P
