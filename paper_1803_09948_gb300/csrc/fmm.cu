@@ -1416,4 +1416,40 @@ void run_matvec_batched(hfmm_plan* P, const float2* density, float2* potential, 
     HFMM_CUDA(cudaGetLastError());
 }
 
+// R right-hand sides (2..64) in one batched matvec, replayed from a CUDA graph captured on
+// the plan's own stream (the caller's stream may be the legacy default stream, which cannot
+// be captured) and re-captured when the buffers change.
+void batched_matvec(hfmm_plan* P, const float2* d, float2* o, int R, cudaStream_t st) {
+    BatchState& B = P->batch;
+    batch_setup(P, R, st);
+    if (!B.cap_stream) HFMM_CUDA(cudaStreamCreateWithFlags(&B.cap_stream, cudaStreamNonBlocking));
+    if (!B.graph || B.g_in != (const void*)d || B.g_out != (void*)o) {
+        if (B.graph) {
+            HFMM_CUDA(cudaGraphExecDestroy(B.graph));
+            B.graph = nullptr;
+        }
+        const int64_t l0 = P->launches;
+        cudaGraph_t g = nullptr;
+        HFMM_CUDA(cudaStreamBeginCapture(B.cap_stream, cudaStreamCaptureModeThreadLocal));
+        try {
+            run_matvec_batched(P, d, o, B.cap_stream);
+        } catch (...) {
+            cudaStreamEndCapture(B.cap_stream, &g);
+            if (g) cudaGraphDestroy(g);
+            P->launches = l0;
+            throw;
+        }
+        HFMM_CUDA(cudaStreamEndCapture(B.cap_stream, &g));
+        const cudaError_t e = cudaGraphInstantiate(&B.graph, g, 0);
+        cudaGraphDestroy(g);
+        HFMM_CUDA(e);
+        B.g_launches = P->launches - l0;
+        P->launches = l0;
+        B.g_in = d;
+        B.g_out = o;
+    }
+    HFMM_CUDA(cudaGraphLaunch(B.graph, st));
+    P->launches += B.g_launches;
+}
+
 }  // namespace hfmm

@@ -369,4 +369,303 @@ int run_gmres(hfmm_plan* P, const void* rhs, void* x_out, int* iters, double* re
     return converged ? HFMM_OK : HFMM_NOT_CONVERGED;
 }
 
+// ============================================================== R systems in lockstep
+// Vectors hold R right-hand sides, [r][N] double-float; kernels take the right-hand side
+// from blockIdx.y (or .z) and otherwise do what their single right-hand-side versions do.
+
+// partial[(r * nvec + i) * RG + blk] = sum over the block's rows of conj(V_i[r]) w[r]
+__global__ void __launch_bounds__(RB) k_dots_bdf(int64_t N, int R, const float4* __restrict__ V, int nvec,
+                                                 const float4* __restrict__ w, double2* __restrict__ partial) {
+    __shared__ double2 sh[RB / 32];
+    const int r = blockIdx.z, i0 = blockIdx.y * kDotVecs;
+    const int nv = min(kDotVecs, nvec - i0);
+    const float4* wr = w + (int64_t)r * N;
+    Acc re[kDotVecs], im[kDotVecs];
+    for (int64_t n = (int64_t)blockIdx.x * RB + threadIdx.x; n < N; n += (int64_t)RG * RB) {
+        const float4 b = wr[n];
+#pragma unroll
+        for (int c = 0; c < kDotVecs; ++c) {
+            if (c >= nv) break;
+            const float4 a = V[((int64_t)(i0 + c) * R + r) * N + n];
+            re[c].add_prod(a.x, a.z, b.x, b.z);
+            re[c].add_prod(a.y, a.w, b.y, b.w);
+            im[c].add_prod(a.x, a.z, b.y, b.w);
+            im[c].add_prod(-a.y, -a.w, b.x, b.z);
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < kDotVecs; ++c) {
+        if (c >= nv) break;
+        const double2 s = block_sum2(make_double2(re[c].value(), im[c].value()), sh);
+        if (threadIdx.x == 0) partial[((int64_t)r * nvec + i0 + c) * RG + blockIdx.x] = s;
+    }
+}
+
+// partial[r * RG + blk] = sum |w[r]|^2 over the block's rows
+__global__ void __launch_bounds__(RB) k_norm2_bdf(int64_t N, const float4* __restrict__ w,
+                                                  double2* __restrict__ partial) {
+    __shared__ double2 sh[RB / 32];
+    const float4* wr = w + (int64_t)blockIdx.y * N;
+    Acc a;
+    for (int64_t n = (int64_t)blockIdx.x * RB + threadIdx.x; n < N; n += (int64_t)RG * RB) {
+        const float4 b = wr[n];
+        a.add_prod(b.x, b.z, b.x, b.z);
+        a.add_prod(b.y, b.w, b.y, b.w);
+    }
+    const double2 s = block_sum2(make_double2(a.value(), 0.0), sh);
+    if (threadIdx.x == 0) partial[(int64_t)blockIdx.y * RG + blockIdx.x] = s;
+}
+
+// x[r] += sign * sum_i c[r][i] V_i[r]   (c: double-float complex, [R][nvec])
+__global__ void k_axpy_bdf(int64_t N, int R, const float4* __restrict__ V, int nvec, const float4* __restrict__ cdf,
+                           float sign, float4* __restrict__ x) {
+    extern __shared__ float4 hs[];
+    const int r = blockIdx.y;
+    for (int q = threadIdx.x; q < nvec; q += blockDim.x) hs[q] = cdf[(int64_t)r * nvec + q];
+    __syncthreads();
+    const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    Acc ar, ai;
+    for (int i = 0; i < nvec; ++i) {
+        const float4 a = V[((int64_t)i * R + r) * N + n], h = hs[i];
+        ar.add_prod(h.x, h.z, a.x, a.z);
+        ar.add_prod(-h.y, -h.w, a.y, a.w);
+        ai.add_prod(h.x, h.z, a.y, a.w);
+        ai.add_prod(h.y, h.w, a.x, a.z);
+    }
+    float4* xr = x + (int64_t)r * N;
+    float4 o = xr[n];
+    float sh, sl;
+    two_sum(ar.s, ar.c, sh, sl);
+    df_add(o.x, o.z, sign * sh, sign * sl, o.x, o.z);
+    two_sum(ai.s, ai.c, sh, sl);
+    df_add(o.y, o.w, sign * sh, sign * sl, o.y, o.w);
+    xr[n] = o;
+}
+
+// b[r] = s_r a[r], s_r = scale[r].x + scale[r].y
+__global__ void k_scale_bdf(int64_t N, const float4* __restrict__ a, const float2* __restrict__ scale,
+                            float4* __restrict__ b) {
+    const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    const int r = blockIdx.y;
+    const float sh = scale[r].x, sl = scale[r].y;
+    const float4 v = a[(int64_t)r * N + n];
+    float4 o;
+    {
+        const float p = __fmul_rn(v.x, sh);
+        const float q = __fmaf_rn(v.x, sl, __fmaf_rn(v.z, sh, __fmaf_rn(v.x, sh, -p)));
+        fast_two_sum(p, q, o.x, o.z);
+    }
+    {
+        const float p = __fmul_rn(v.y, sh);
+        const float q = __fmaf_rn(v.y, sl, __fmaf_rn(v.w, sh, __fmaf_rn(v.y, sh, -p)));
+        fast_two_sum(p, q, o.y, o.w);
+    }
+    b[(int64_t)r * N + n] = o;
+}
+
+namespace {
+struct BCtx {
+    hfmm_plan* P;
+    cudaStream_t st;
+    int64_t N;
+    int R;
+    unsigned nb;
+    double2* partial;  // RG * R * (m + 2)
+    double2* small;    // R * (m + 2)
+    float4* coeff;     // R * (m + 2) double-float coefficients
+    float2* scales;    // R double-float scale factors
+
+    void count(int n = 1) { P->launches += n; }
+    int64_t RN() const { return (int64_t)R * N; }
+    unsigned nbRN() const { return (unsigned)((RN() + 255) / 256); }
+    void matvec(const float4* in, float4* out) {
+        k_df_to_c64<<<nbRN(), 256, 0, st>>>(RN(), in, P->bin.p);
+        batched_matvec(P, P->bin.p, P->bout.p, R, st);
+        k_c64_to_df<<<nbRN(), 256, 0, st>>>(RN(), P->bout.p, out);
+        count(2);
+    }
+    std::vector<double> norms(const float4* w) {
+        k_norm2_bdf<<<dim3(RG, R), RB, 0, st>>>(N, w, partial);
+        k_reduce<<<R, RB, 0, st>>>(partial, small);
+        count(2);
+        std::vector<double2> h(R);
+        HFMM_CUDA(cudaMemcpyAsync(h.data(), small, sizeof(double2) * R, cudaMemcpyDeviceToHost, st));
+        HFMM_CUDA(cudaStreamSynchronize(st));
+        std::vector<double> out(R);
+        for (int r = 0; r < R; ++r) out[r] = std::sqrt(h[r].x);
+        return out;
+    }
+    // b[r] = s[r] a[r] (s on the host, FP64)
+    void scale(const float4* a, const std::vector<double>& s, float4* b) {
+        std::vector<float2> sf(R);
+        for (int r = 0; r < R; ++r) split_df(s[r], sf[r].x, sf[r].y);
+        HFMM_CUDA(cudaMemcpyAsync(scales, sf.data(), sizeof(float2) * R, cudaMemcpyHostToDevice, st));
+        k_scale_bdf<<<dim3(nb, R), 256, 0, st>>>(N, a, scales, b);
+        count();
+    }
+    // x[r] += sign * V[0..nvec)[r] c[r]
+    void axpy(const float4* V, int nvec, const std::vector<std::vector<cd>>& c, float sign, float4* x) {
+        std::vector<float4> cf((size_t)R * nvec);
+        for (int r = 0; r < R; ++r)
+            for (int i = 0; i < nvec; ++i) {
+                float rh, rl, ih, il;
+                const cd v = i < (int)c[r].size() ? c[r][i] : cd(0);
+                split_df(v.real(), rh, rl);
+                split_df(v.imag(), ih, il);
+                cf[(size_t)r * nvec + i] = make_float4(rh, ih, rl, il);
+            }
+        HFMM_CUDA(cudaMemcpyAsync(coeff, cf.data(), sizeof(float4) * cf.size(), cudaMemcpyHostToDevice, st));
+        k_axpy_bdf<<<dim3(nb, R), 256, sizeof(float4) * nvec, st>>>(N, R, V, nvec, coeff, sign, x);
+        count();
+    }
+    // h[r] = V[0..nvec)[r]^H w[r], then w[r] -= V[r] h[r]; adds into hsum
+    void cgs_pass(const float4* V, int nvec, float4* w, std::vector<std::vector<cd>>& hsum) {
+        k_dots_bdf<<<dim3(RG, (nvec + kDotVecs - 1) / kDotVecs, R), RB, 0, st>>>(N, R, V, nvec, w, partial);
+        k_reduce<<<R * nvec, RB, 0, st>>>(partial, small);
+        count(2);
+        std::vector<double2> h((size_t)R * nvec);
+        HFMM_CUDA(cudaMemcpyAsync(h.data(), small, sizeof(double2) * h.size(), cudaMemcpyDeviceToHost, st));
+        HFMM_CUDA(cudaStreamSynchronize(st));
+        std::vector<std::vector<cd>> hc(R, std::vector<cd>(nvec));
+        for (int r = 0; r < R; ++r)
+            for (int i = 0; i < nvec; ++i) {
+                hc[r][i] = cd(h[(size_t)r * nvec + i].x, h[(size_t)r * nvec + i].y);
+                hsum[r][i] += hc[r][i];
+            }
+        axpy(V, nvec, hc, -1.f, w);
+    }
+};
+}  // namespace
+
+int run_gmres_batched(hfmm_plan* P, const float2* rhs, float2* x_out, int R, int* iters, double* relres,
+                      cudaStream_t st) {
+    const int64_t N = P->N;
+    const int m = P->cfg.restart;
+    const double tol = P->cfg.tol;
+    const int maxit = P->cfg.max_iter;
+    const int64_t RN = (int64_t)R * N;
+    if (P->bkry_m != m || P->bkry_R != R) {
+        P->bkry.alloc((size_t)(m + 1) * RN, nullptr);
+        P->bgw.alloc(RN, nullptr);
+        P->bgx.alloc(RN, nullptr);
+        P->bgb.alloc(RN, nullptr);
+        P->bin.alloc(RN, nullptr);
+        P->bout.alloc(RN, nullptr);
+        P->bred.alloc((size_t)2 * RG * R * (m + 2) + 2 * (size_t)R * (m + 2) + 2 * (size_t)R * (m + 2) + 2 * R,
+                      nullptr);
+        P->bkry_m = m;
+        P->bkry_R = R;
+    }
+    double2* red = (double2*)P->bred.p;
+    double2* small = red + (size_t)RG * R * (m + 2);
+    float4* coeff = reinterpret_cast<float4*>(small + (size_t)R * (m + 2));
+    float2* scales = reinterpret_cast<float2*>(coeff + (size_t)R * (m + 2));
+    BCtx c{P, st, N, R, (unsigned)((N + 255) / 256), red, small, coeff, scales};
+    float4* V = P->bkry.p;
+    float4 *w = P->bgw.p, *xg = P->bgx.p, *bg = P->bgb.p;
+    k_c64_to_df<<<c.nbRN(), 256, 0, st>>>(RN, rhs, bg);
+    c.count();
+    HFMM_CUDA(cudaMemsetAsync(xg, 0, sizeof(float4) * RN, st));
+    const std::vector<double> bnorm = c.norms(bg);
+    std::vector<double> beta = bnorm;
+    std::vector<char> done(R, 0);  // converged (or zero right-hand side)
+    for (int r = 0; r < R; ++r) {
+        iters[r] = 0;
+        relres[r] = 0.0;
+        if (bnorm[r] == 0.0) done[r] = 1;
+    }
+    HFMM_CUDA(cudaMemcpyAsync(w, bg, sizeof(float4) * RN, cudaMemcpyDeviceToDevice, st));
+    int it = 0;
+    auto all_done = [&]() {
+        for (int r = 0; r < R; ++r)
+            if (!done[r]) return false;
+        return true;
+    };
+    while (it < maxit && !all_done()) {
+        // V_0[r] = r0 / beta (zero for the finished right-hand sides, which then stay inert)
+        std::vector<double> s0(R);
+        for (int r = 0; r < R; ++r) s0[r] = done[r] ? 0.0 : 1.0 / beta[r];
+        c.scale(w, s0, V);
+        std::vector<std::vector<cd>> H(R, std::vector<cd>((size_t)(m + 1) * m, cd(0))), cs(R, std::vector<cd>(m)),
+            sn(R, std::vector<cd>(m)), g(R, std::vector<cd>(m + 1, cd(0)));
+        std::vector<int> jdone(R, 0);
+        std::vector<char> active(R);
+        for (int r = 0; r < R; ++r) {
+            g[r][0] = done[r] ? 0.0 : beta[r];
+            active[r] = !done[r];
+        }
+        for (int j = 0; j < m && it < maxit; ++j) {
+            c.matvec(V + (int64_t)j * RN, w);
+            std::vector<std::vector<cd>> h(R, std::vector<cd>(j + 2, cd(0)));
+            c.cgs_pass(V, j + 1, w, h);
+            c.cgs_pass(V, j + 1, w, h);
+            const std::vector<double> hn = c.norms(w);
+            std::vector<double> sc(R);
+            for (int r = 0; r < R; ++r) sc[r] = (active[r] && hn[r] > 0.0) ? 1.0 / hn[r] : 0.0;
+            c.scale(w, sc, V + (int64_t)(j + 1) * RN);
+            ++it;
+            bool any = false;
+            for (int r = 0; r < R; ++r) {
+                if (!active[r]) continue;
+                auto& hr = h[r];
+                hr[j + 1] = hn[r];
+                for (int i = 0; i < j; ++i) {
+                    const cd t = std::conj(cs[r][i]) * hr[i] + std::conj(sn[r][i]) * hr[i + 1];
+                    hr[i + 1] = -sn[r][i] * hr[i] + cs[r][i] * hr[i + 1];
+                    hr[i] = t;
+                }
+                const double den = std::sqrt(std::norm(hr[j]) + std::norm(hr[j + 1]));
+                if (den == 0.0) {
+                    cs[r][j] = 1.0;
+                    sn[r][j] = 0.0;
+                } else {
+                    cs[r][j] = hr[j] / den;
+                    sn[r][j] = hr[j + 1] / den;
+                }
+                hr[j] = std::conj(cs[r][j]) * hr[j] + std::conj(sn[r][j]) * hr[j + 1];
+                hr[j + 1] = 0.0;
+                g[r][j + 1] = -sn[r][j] * g[r][j];
+                g[r][j] = std::conj(cs[r][j]) * g[r][j];
+                for (int i = 0; i <= j; ++i) H[r][(size_t)i * m + j] = hr[i];
+                jdone[r] = j + 1;
+                iters[r] = it;
+                if (std::abs(g[r][j + 1]) / bnorm[r] <= tol || hn[r] == 0.0) active[r] = 0;  // stop its process
+                any = any || active[r];
+            }
+            if (!any) break;
+        }
+        // y_r = H_r^{-1} g_r (FP64), x[r] += V[r] y_r
+        std::vector<std::vector<cd>> y(R);
+        int jmax = 0;
+        for (int r = 0; r < R; ++r) {
+            const int jd = done[r] ? 0 : jdone[r];
+            y[r].assign(jd, cd(0));
+            for (int i = jd - 1; i >= 0; --i) {
+                cd s = g[r][i];
+                for (int q = i + 1; q < jd; ++q) s -= H[r][(size_t)i * m + q] * y[r][q];
+                y[r][i] = s / H[r][(size_t)i * m + i];
+            }
+            jmax = std::max(jmax, jd);
+        }
+        if (jmax > 0) c.axpy(V, jmax, y, 1.f, xg);
+        // true residuals r = b - A x
+        c.matvec(xg, w);
+        k_sub_df<<<c.nbRN(), 256, 0, st>>>(RN, bg, w, w);
+        c.count();
+        beta = c.norms(w);
+        for (int r = 0; r < R; ++r) {
+            if (bnorm[r] == 0.0) continue;
+            relres[r] = beta[r] / bnorm[r];
+            if (relres[r] <= tol) done[r] = 1;
+        }
+    }
+    k_df_to_c64<<<c.nbRN(), 256, 0, st>>>(RN, xg, x_out);
+    c.count();
+    HFMM_CUDA(cudaGetLastError());
+    HFMM_CUDA(cudaStreamSynchronize(st));
+    return all_done() ? HFMM_OK : HFMM_NOT_CONVERGED;
+}
+
 }  // namespace hfmm

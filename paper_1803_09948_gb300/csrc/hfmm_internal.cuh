@@ -177,6 +177,11 @@ struct hfmm_plan {
     DBuf<float4> gw, gx, gb;   // work vector, iterate, right-hand side (double-float complex)
     DBuf<double> gred;         // reduction scratch
     int kry_m = 0;
+    // batched GMRES workspace: (restart + 1) x R x N basis, work vectors, complex64 staging
+    DBuf<float4> bkry, bgw, bgx, bgb;
+    DBuf<float2> bin, bout;
+    DBuf<double> bred;
+    int bkry_m = 0, bkry_R = 0;
     int64_t launches = 0;       // kernels launched by this plan
     double cost[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // see hfmm_plan_costs
     cudaEvent_t* stage_ev = nullptr;  // set by hfmm_matvec_timed: events after each stage
@@ -259,6 +264,12 @@ void m2l_tc_launch(const int4* groups, int64_t ngroups, const TransItem* items, 
 
 // ---------------------------------------------------------------- GMRES
 int run_gmres(hfmm_plan* P, const void* rhs, void* x, int* iters, double* relres, cudaStream_t st);
+// R (2..64) systems with the same operator in lockstep: one batched matvec per iteration,
+// an independent Arnoldi process per right-hand side. rhs, x: device complex64 [R][N].
+int run_gmres_batched(hfmm_plan* P, const float2* rhs, float2* x, int R, int* iters, double* relres,
+                      cudaStream_t st);
+// the batched matvec through the plan's captured graph (density, potential: complex64 [R][N])
+void batched_matvec(hfmm_plan* P, const float2* d, float2* o, int R, cudaStream_t st);
 
 // host special functions (plan building only)
 void host_jn_scaled(int nmax, double z, double s, double* out);

@@ -716,42 +716,6 @@ int hfmm_plan_info(const hfmm_plan* P, int* depth, int* orders, int64_t* n_leave
     return HFMM_OK;
 }
 
-// R right-hand sides (2..64) in one batched matvec, replayed from a CUDA graph captured on
-// the plan's own stream (the caller's stream may be the legacy default stream, which cannot
-// be captured) and re-captured when the buffers change.
-static void batched_matvec(hfmm_plan* P, const float2* d, float2* o, int R, cudaStream_t st) {
-    BatchState& B = P->batch;
-    batch_setup(P, R, st);
-    if (!B.cap_stream) HFMM_CUDA(cudaStreamCreateWithFlags(&B.cap_stream, cudaStreamNonBlocking));
-    if (!B.graph || B.g_in != (const void*)d || B.g_out != (void*)o) {
-        if (B.graph) {
-            HFMM_CUDA(cudaGraphExecDestroy(B.graph));
-            B.graph = nullptr;
-        }
-        const int64_t l0 = P->launches;
-        cudaGraph_t g = nullptr;
-        HFMM_CUDA(cudaStreamBeginCapture(B.cap_stream, cudaStreamCaptureModeThreadLocal));
-        try {
-            run_matvec_batched(P, d, o, B.cap_stream);
-        } catch (...) {
-            cudaStreamEndCapture(B.cap_stream, &g);
-            if (g) cudaGraphDestroy(g);
-            P->launches = l0;
-            throw;
-        }
-        HFMM_CUDA(cudaStreamEndCapture(B.cap_stream, &g));
-        const cudaError_t e = cudaGraphInstantiate(&B.graph, g, 0);
-        cudaGraphDestroy(g);
-        HFMM_CUDA(e);
-        B.g_launches = P->launches - l0;
-        P->launches = l0;
-        B.g_in = d;
-        B.g_out = o;
-    }
-    HFMM_CUDA(cudaGraphLaunch(B.graph, st));
-    P->launches += B.g_launches;
-}
-
 int hfmm_matvec_parts(hfmm_plan* P, const void* density, void* potential, int nrhs, int parts, void* stream) {
     if (!P || !density || !potential || nrhs < 1 || parts < 0 || parts > 7) return HFMM_E_INVALID;
     HFMM_GUARD_BEGIN
@@ -864,13 +828,29 @@ int hfmm_solve(hfmm_plan* P, const void* rhs, void* x_out, int nrhs, int* iters_
     HFMM_GUARD_BEGIN
     cudaStream_t st = (cudaStream_t)stream;
     int status = HFMM_OK;
-    for (int r = 0; r < nrhs; ++r) {
+    for (int r0 = 0; r0 < nrhs;) {
+        const int R = std::min(nrhs - r0, 64);
+        const float2* b = (const float2*)rhs + (int64_t)r0 * P->N;
+        float2* x = (float2*)x_out + (int64_t)r0 * P->N;
+        if (R > 1 && batch_supported(P, R)) {  // R solves in lockstep on batched matvecs
+            std::vector<int> it(R, 0);
+            std::vector<double> rr(R, 0.0);
+            const int s = run_gmres_batched(P, b, x, R, it.data(), rr.data(), st);
+            if (s != HFMM_OK) status = s;
+            for (int q = 0; q < R; ++q) {
+                if (iters_out) iters_out[r0 + q] = it[q];
+                if (relres_out) relres_out[r0 + q] = rr[q];
+            }
+            r0 += R;
+            continue;
+        }
         int it = 0;
         double rr = 0.0;
-        int s = run_gmres(P, (const float2*)rhs + (int64_t)r * P->N, (float2*)x_out + (int64_t)r * P->N, &it, &rr, st);
+        const int s = run_gmres(P, b, x, &it, &rr, st);
         if (s != HFMM_OK) status = s;
-        if (iters_out) iters_out[r] = it;
-        if (relres_out) relres_out[r] = rr;
+        if (iters_out) iters_out[r0] = it;
+        if (relres_out) relres_out[r0] = rr;
+        ++r0;
     }
     return status;
     HFMM_GUARD_END

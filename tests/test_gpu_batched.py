@@ -134,3 +134,64 @@ def test_batched_planewaves_491k_sampled_rows():
             assert _rel(got[r][rows], ref) < 1e-4
     finally:
         plan.close()
+
+
+def _dense_setup(V, F, k):
+    X, _, _ = oracle.points(V, F)
+    Z = oracle.dense_Z(V, F, k, oracle.near_radius(V, F, 1.0))
+    return X, Z
+
+
+def test_batched_solve_against_dense_solutions(small):
+    """hfmm_solve with 5 right-hand sides runs 5 GMRES(30) processes in lockstep on
+    batched matvecs. Each solution meets the single-RHS solve's criteria: true residual
+    under the oracle's dense operator <= 2e-4, distance to the dense-LU solution <= 1e-2
+    (cond(Z) ~ 60); the second right-hand side is zero (zero solution, 0 iterations)."""
+    V, F = small
+    plan = pkg.Plan(V, F, 1.0, p_fixed=8, leaf_max=64, restart=30)
+    try:
+        dirs = np.asarray(synthetic.fibonacci_directions(5, seed=2)).reshape(5, 3)
+        b = torch.empty(5 * plan.n, dtype=torch.complex64, device="cuda")
+        plan.rhs_planewave(dirs, b)
+        b.view(5, plan.n)[1].zero_()
+        x = torch.full_like(b, complex(np.nan, np.nan))
+        st, its, rr = plan.solve(b, x, 5)
+        assert st == pkg.HFMM_OK
+        torch.cuda.synchronize()
+        xs = x.cpu().numpy().astype(np.complex128).reshape(5, plan.n)
+        bs = b.cpu().numpy().astype(np.complex128).reshape(5, plan.n)
+        assert its[1] == 0 and np.all(xs[1] == 0)
+        X, Z = _dense_setup(V, F, 1.0)
+        for r in (0, 2, 3, 4):
+            assert rr[r] <= 1e-4 and 0 < its[r] < 100
+            assert _rel(Z @ xs[r], bs[r]) < 2e-4
+            assert _rel(xs[r], np.linalg.solve(Z, bs[r])) < 1e-2
+    finally:
+        plan.close()
+
+
+def test_batched_solve_matches_single_solves_tight():
+    """At p = 12 and tolerance 5e-7 the lockstep solves and one-at-a-time solves of the
+    same right-hand sides agree to 1e-4, and each is within 1e-4 of the dense-LU solution."""
+    V, F = synthetic.sphere_mesh(2)
+    plan = pkg.Plan(V, F, 1.0, p_fixed=12, tol=5e-7, leaf_max=32)
+    try:
+        dirs = np.asarray(synthetic.fibonacci_directions(3, seed=4)).reshape(3, 3)
+        b = torch.empty(3 * plan.n, dtype=torch.complex64, device="cuda")
+        plan.rhs_planewave(dirs, b)
+        xb = torch.empty_like(b)
+        st, its, rr = plan.solve(b, xb, 3)
+        assert st == pkg.HFMM_OK
+        X, Z = _dense_setup(V, F, 1.0)
+        bs = b.cpu().numpy().astype(np.complex128).reshape(3, plan.n)
+        xbs = xb.cpu().numpy().astype(np.complex128).reshape(3, plan.n)
+        for r in range(3):
+            b1 = b.view(3, plan.n)[r].clone()
+            x1 = torch.empty_like(b1)
+            s1, _, _ = plan.solve(b1, x1)
+            assert s1 == pkg.HFMM_OK
+            x1h = x1.cpu().numpy().astype(np.complex128)
+            assert _rel(xbs[r], x1h) < 1e-4
+            assert _rel(xbs[r], np.linalg.solve(Z, bs[r])) < 1e-4
+    finally:
+        plan.close()
