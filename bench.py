@@ -264,6 +264,31 @@ def run_batched(args):
     e2e_ms = e0.elapsed_time(e1)
     got = h_out.numpy().astype(np.complex128).reshape(R, N)
     S = h_in.numpy().astype(np.complex128).reshape(R, N)
+    # R solves in lockstep (GMRES per right-hand side on shared batched matvecs), own timed region
+    solve = None
+    if args.solves > 0:
+        xs = torch.empty_like(b)
+        plan.solve(b, xs, R)  # warm-up (allocates the Krylov bases)
+        lat, its_all, rr_all = [], None, None
+        for _ in range(args.solves):
+            barrier()
+            t1 = time.perf_counter()
+            stt, its_all, rr_all = plan.solve(b, xs, R)
+            torch.cuda.synchronize()
+            lat.append(time.perf_counter() - t1)
+        x1 = torch.empty(N, dtype=torch.complex64, device="cuda")
+        plan.solve(b1, x1)
+        barrier()
+        t1 = time.perf_counter()
+        plan.solve(b1, x1)
+        torch.cuda.synchronize()
+        single_solve_ms = 1e3 * (time.perf_counter() - t1)
+        solve = {"solves_per_s": R * len(lat) / sum(lat), "ms_per_batch": 1e3 * statistics.mean(lat),
+                 "single_rhs_solve_ms": single_solve_ms,
+                 "nrhs": R, "iterations_max": int(max(its_all)), "iterations_min": int(min(its_all)),
+                 "true_relres_max": float(max(rr_all)), "restart": restart, "tol": 1e-4,
+                 "status": "converged" if stt == 0 else "not converged",
+                 "rhs": f"{R} plane waves (seeded Fibonacci directions)"}
     acc, cpu = None, None
     if rank == 0 and not args.no_cpu_baseline:
         picks = sorted({0, R // 3, (2 * R) // 3, R - 1})
@@ -289,6 +314,7 @@ def run_batched(args):
                        "l2": "inputs larger than L2 (batched expansions alone exceed it)"},
             "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99)),
                            "mean": statistics.mean(step_ms)},
+            "solve": solve,
             "single_rhs_ms": single_ms,
             "speedup_per_rhs_vs_single": single_ms / (total_ms / args.steps / R),
             "e2e": {"value": args.steps * R / (e2e_ms / 1e3), "unit": "matvec/s", "h2d_bytes_per_step": 8 * N * R,
