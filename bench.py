@@ -178,6 +178,47 @@ def run_reference(args):
     }))
 
 
+def run_serving(args):
+    """Serving: seeded requests with Poisson arrivals (20 per second), sphere / ellipsoid /
+    star geodesic meshes with N log-uniform in [10k, serve-nmax], k uniform in
+    [1, serve-kmax], 1..16 right-hand sides; admitted by an 80 % device-memory budget."""
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    import synthetic
+    from paper_1803_09948_gb300 import serving
+
+    torch.cuda.set_device(0)
+    __graft_entry__.build()
+    specs = synthetic.serving_requests(args.serve, seed=0, rate=20.0, n_max=args.serve_nmax,
+                                       k_range=(1.0, args.serve_kmax))
+    reqs = []
+    for sp in specs:  # meshes come with the requests: built before the clock starts
+        V, F = synthetic.serving_shape(sp["shape"], sp["nu"], sp["seed"])
+        dirs = np.asarray(synthetic.fibonacci_directions(sp["nrhs"], seed=sp["seed"] % 100000)).reshape(-1, 3)
+        reqs.append(dict(sp, V=V, F=F, dirs=dirs))
+    eng = serving.ServingEngine(workers=args.serve_workers, restart=30, tol=1e-4)
+    clocks = ClockSampler(0)
+    clocks.start()
+    records, summ = eng.run(reqs)
+    clk = clocks.stop()
+    print(json.dumps({
+        "metric": METRIC, "value": summ["solves_per_s"], "unit": "solves/s", "n_gpus": 1,
+        "steps": len(reqs), "warmup": 0, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "fp32 (P2P, M2L, tree passes); fp64-class GMRES", "data": "synthetic",
+        "config": {"workload": f"serving: {len(reqs)} requests, Poisson arrivals 20/s, sphere / ellipsoid (2,1,1) / "
+                               f"star geodesic meshes, N log-uniform in [10k, {args.serve_nmax}], k uniform in "
+                               f"[1, {args.serve_kmax}], 1-16 plane-wave right-hand sides, GMRES(30) to 1e-4",
+                   "workers": args.serve_workers, "budget": "80% of device memory"},
+        "latency_s": {"p50": summ["latency_p50_s"], "p99": summ["latency_p99_s"], "mean": summ["latency_mean_s"]},
+        "serving": summ,
+        "requests": [{k_: r.get(k_) for k_ in ("id", "n_points", "nrhs", "status", "latency_s", "wait_s", "build_s",
+                                               "solve_s")} for r in sorted(records, key=lambda r: r["id"])],
+        "clocks": clk,
+    }))
+
+
 def run_batched(args):
     """Batched right-hand sides: one step = one matvec of args.nrhs plane-wave right-hand sides
     (seeded Fibonacci directions), all in one captured CUDA graph; value counts right-hand sides."""
@@ -341,6 +382,10 @@ def main():
     ap.add_argument("--solves", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--simt", action="store_true", help="M2L on FP32 SIMT cores only (the plain form)")
+    ap.add_argument("--serve", type=int, default=0, help="> 0: serving workload with this many requests")
+    ap.add_argument("--serve-nmax", type=int, default=1_000_000)
+    ap.add_argument("--serve-kmax", type=float, default=30.0)
+    ap.add_argument("--serve-workers", type=int, default=2)
     ap.add_argument("--nrhs", type=int, default=1,
                     help="> 1: batched plane-wave right-hand sides in one graph-captured matvec per step")
     args = ap.parse_args()
@@ -348,6 +393,8 @@ def main():
         return run_reference(args)
     if args.nrhs > 1:
         return run_batched(args)
+    if args.serve > 0:
+        return run_serving(args)
 
     import numpy as np
     import torch

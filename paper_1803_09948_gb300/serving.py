@@ -1,0 +1,210 @@
+"""Serving loop for scattering solves.
+
+Requests (a surface mesh, a wavenumber k and one or more incident directions)
+arrive over time; each is solved with the FMM-accelerated GMRES of the library:
+its plan (octree, translation operators, near-field correction) and Krylov
+basis are built on the device when the request is admitted, stay resident
+until its solve has finished, and are then released.
+
+  * Admission: a request is started only while the device memory reserved by
+    the requests in flight, plus its own estimate, stays within the budget
+    (by default 80 % of the device's memory); requests wait in arrival order.
+    A request whose estimate alone exceeds the budget is rejected.
+  * Concurrency: `workers` host threads, each with its own CUDA stream, so the
+    plan building of one request (host octree and lists, device operator and
+    correction kernels) overlaps the solves of others.
+  * Multi-RHS requests use the library's lockstep solver (one batched,
+    graph-captured matvec per GMRES iteration for all directions).
+
+Latency of a request = completion (its solution copied back to the host)
+minus arrival. `ServingEngine.run` returns per-request records and a summary
+with p50 / p99 latency and solves per second (right-hand sides solved per
+second of wall time from the first arrival to the last completion).
+"""
+from __future__ import annotations
+
+import queue
+import threading
+import time
+
+import numpy as np
+
+
+def estimate_bytes(n_points: int, nrhs: int, restart: int) -> int:
+    """Device memory of one request: plan (about 1.2 KB per point: sorted points,
+    the near-field correction, expansions, operators) plus the Krylov basis and
+    work vectors ((restart + 1) + 4 double-float vectors per right-hand side, 16 B per
+    point each) plus, for several right-hand sides, the batched matvec buffers."""
+    per_point = 1200 + 16 * nrhs * (restart + 5)
+    if nrhs > 1:
+        per_point += 200 * nrhs
+    return int(n_points * per_point + (64 << 20))
+
+
+class Admission:
+    """Device-memory budget shared by the workers; grants in request order."""
+
+    def __init__(self, budget: int):
+        self.budget = int(budget)
+        self.in_use = 0
+        self.peak = 0
+        self._cv = threading.Condition()
+        self._next = 0  # ticket served next (FIFO among waiting requests)
+        self._tickets = 0
+
+    def ticket(self) -> int:
+        with self._cv:
+            t = self._tickets
+            self._tickets += 1
+            return t
+
+    def acquire(self, ticket: int, nbytes: int) -> bool:
+        """Blocks until it is this ticket's turn and nbytes fit; False if they never can."""
+        with self._cv:
+            while ticket != self._next:
+                self._cv.wait()
+            if nbytes > self.budget:
+                self._next += 1
+                self._cv.notify_all()
+                return False
+            while self.in_use + nbytes > self.budget:
+                self._cv.wait()
+            self.in_use += nbytes
+            self.peak = max(self.peak, self.in_use)
+            self._next += 1
+            self._cv.notify_all()
+            return True
+
+    def release(self, nbytes: int):
+        with self._cv:
+            self.in_use -= nbytes
+            self._cv.notify_all()
+
+
+def gpu_executor(restart: int = 30, tol: float = 1e-4):
+    """Executor that solves a request with the library on the calling thread's stream.
+    Returns a function(request, stream) -> dict of timings and results."""
+    import torch
+
+    from . import Plan
+
+    def run(req, stream):
+        t0 = time.perf_counter()
+        with torch.cuda.stream(stream):
+            plan = Plan(req["V"], req["F"], req["k"], stream=stream, restart=restart, tol=tol)
+            try:
+                torch.cuda.synchronize()  # plan ready (its build is part of the request's time)
+                t1 = time.perf_counter()
+                R, N = req["nrhs"], plan.n
+                b = torch.empty(R * N, dtype=torch.complex64, device="cuda")
+                plan.rhs_planewave(np.asarray(req["dirs"]).reshape(R, 3), b, stream=stream)
+                x = torch.empty_like(b)
+                status, its, rr = plan.solve(b, x, R, stream=stream)
+                x_host = x.to("cpu", non_blocking=False)  # the response
+                t2 = time.perf_counter()
+                return {"status": int(status), "iterations": [int(v) for v in its],
+                        "relres": [float(v) for v in rr], "n_points": N, "build_s": t1 - t0,
+                        "solve_s": t2 - t1, "device_bytes": plan.info()["device_bytes"],
+                        "response_bytes": x_host.numel() * 8}
+            finally:
+                plan.close()
+
+    return run
+
+
+class ServingEngine:
+    def __init__(self, executor=None, workers: int = 2, budget_bytes: int | None = None,
+                 budget_frac: float = 0.8, restart: int = 30, tol: float = 1e-4, stream_factory=None):
+        if budget_bytes is None:
+            import torch
+
+            budget_bytes = int(budget_frac * torch.cuda.mem_get_info()[1])
+        self.admission = Admission(budget_bytes)
+        self.workers = int(workers)
+        self.restart = int(restart)
+        self.executor = executor if executor is not None else gpu_executor(restart, tol)
+        if stream_factory is None:
+            def stream_factory():
+                import torch
+
+                return torch.cuda.Stream()
+        self.stream_factory = stream_factory
+
+    def run(self, requests):
+        """requests: dicts with arrival_s, V, F, k, nrhs, dirs (and anything else, passed
+        through). Blocks until all are served; returns (records, summary)."""
+        reqs = sorted(requests, key=lambda r: r["arrival_s"])
+        ready: queue.Queue = queue.Queue()
+        records = []
+        rec_lock = threading.Lock()
+        t0 = time.perf_counter()
+
+        def client():
+            for r in reqs:
+                delay = t0 + r["arrival_s"] - time.perf_counter()
+                if delay > 0:
+                    time.sleep(delay)
+                ready.put((self.admission.ticket(), time.perf_counter(), r))
+            for _ in range(self.workers):
+                ready.put(None)
+
+        def worker():
+            stream = self.stream_factory()
+            while True:
+                item = ready.get()
+                if item is None:
+                    return
+                ticket, t_arrive, r = item
+                est = estimate_bytes(len(r["F"]) * 3, r["nrhs"], self.restart)
+                rec = {"id": r.get("id"), "arrival_s": t_arrive - t0, "nrhs": r["nrhs"], "estimate_bytes": est}
+                if not self.admission.acquire(ticket, est):
+                    rec.update(status="rejected", done_s=time.perf_counter() - t0)
+                else:
+                    t_start = time.perf_counter()
+                    try:
+                        out = self.executor(r, stream)
+                        rec.update(out)
+                        rec["status"] = "ok" if out.get("status", 0) == 0 else "not converged"
+                    except Exception as e:  # the request fails; the server goes on
+                        rec.update(status="error", error=str(e))
+                    finally:
+                        self.admission.release(est)
+                    t_done = time.perf_counter()
+                    rec.update(start_s=t_start - t0, done_s=t_done - t0, wait_s=t_start - t_arrive,
+                               latency_s=t_done - t_arrive)
+                with rec_lock:
+                    records.append(rec)
+
+        threads = [threading.Thread(target=client)] + [threading.Thread(target=worker) for _ in range(self.workers)]
+        for t in threads:
+            t.start()
+        for t in threads:
+            t.join()
+        return records, summarize(records, self.admission)
+
+
+def summarize(records, admission=None):
+    served = [r for r in records if r["status"] in ("ok", "not converged")]
+    lat = np.array([r["latency_s"] for r in served]) if served else np.zeros(0)
+    first = min((r["arrival_s"] for r in records), default=0.0)
+    last = max((r["done_s"] for r in records), default=0.0)
+    span = max(last - first, 1e-9)
+    solved = sum(r["nrhs"] for r in records if r["status"] == "ok")
+    out = {
+        "requests": len(records), "ok": sum(r["status"] == "ok" for r in records),
+        "not_converged": sum(r["status"] == "not converged" for r in records),
+        "rejected": sum(r["status"] == "rejected" for r in records),
+        "errors": sum(r["status"] == "error" for r in records),
+        "solves": solved, "makespan_s": span, "solves_per_s": solved / span,
+        "requests_per_s": len(served) / span,
+        "latency_p50_s": float(np.percentile(lat, 50)) if lat.size else None,
+        "latency_p99_s": float(np.percentile(lat, 99)) if lat.size else None,
+        "latency_mean_s": float(lat.mean()) if lat.size else None,
+        "wait_mean_s": float(np.mean([r["wait_s"] for r in served])) if served else None,
+        "build_mean_s": float(np.mean([r["build_s"] for r in served if "build_s" in r])) if served else None,
+        "solve_mean_s": float(np.mean([r["solve_s"] for r in served if "solve_s" in r])) if served else None,
+    }
+    if admission is not None:
+        out["budget_bytes"] = admission.budget
+        out["peak_reserved_bytes"] = admission.peak
+    return out

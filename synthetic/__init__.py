@@ -10,6 +10,9 @@ from .meshes import (  # noqa: F401
     sphere_mesh,
     ellipsoid_mesh,
     star_mesh,
+    geodesic_sphere,
+    serving_shape,
+    serving_requests,
     workload_mesh,
     WORKLOADS,
 )

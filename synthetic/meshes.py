@@ -140,6 +140,79 @@ def star_mesh(level: int, seed: int, amplitude: float = 0.2):
     return v * (1.0 + amplitude * s)[:, None], f
 
 
+def geodesic_sphere(nu: int):
+    """Unit sphere from the icosahedron with every face cut into nu^2 triangles
+    (geodesic frequency nu): 20 nu^2 triangles, 10 nu^2 + 2 vertices."""
+    if nu < 1:
+        raise ValueError("frequency must be at least 1")
+    v0, f0 = _icosahedron()
+    # barycentric grid of one face: (i, j) with i + j <= nu
+    ii, jj = np.meshgrid(np.arange(nu + 1), np.arange(nu + 1), indexing="ij")
+    keep = ii + jj <= nu
+    ii, jj = ii[keep], jj[keep]
+    lid = -np.ones((nu + 1, nu + 1), dtype=np.int64)
+    lid[ii, jj] = np.arange(ii.size)
+    up = [(i, j) for i in range(nu) for j in range(nu - i)]
+    dn = [(i, j) for i in range(nu) for j in range(nu - i - 1)]
+    tri_local = np.array([[lid[i, j], lid[i + 1, j], lid[i, j + 1]] for i, j in up]
+                         + [[lid[i + 1, j], lid[i + 1, j + 1], lid[i, j + 1]] for i, j in dn], dtype=np.int64)
+    verts, faces = [], []
+    for a, b, c in f0:
+        p = (v0[a][None, :] * (nu - ii - jj)[:, None] + v0[b][None, :] * ii[:, None]
+             + v0[c][None, :] * jj[:, None]) / nu
+        faces.append(tri_local + sum(x.shape[0] for x in verts))
+        verts.append(p)
+    v = np.concatenate(verts, axis=0)
+    f = np.concatenate(faces, axis=0)
+    # points on shared edges appear once per face: merge them (exact grid positions)
+    key = np.round(v * (8 * nu), 0).astype(np.int64)
+    _, first, inv = np.unique(key, axis=0, return_index=True, return_inverse=True)
+    v = v[first]
+    f = inv.reshape(-1)[f]
+    v /= np.linalg.norm(v, axis=1, keepdims=True)
+    return v, f.astype(np.int32)
+
+
+def serving_shape(kind: str, nu: int, seed: int, amplitude: float = 0.2):
+    """A request's scatterer: 'sphere', 'ellipsoid' (semi-axes 2, 1, 1) or 'star'
+    (r = 1 + amplitude S / max|S|, S a seeded degree-1..3 function as in star_mesh),
+    on a geodesic mesh of frequency nu (N = 60 nu^2 quadrature points)."""
+    v, f = geodesic_sphere(nu)
+    if kind == "sphere":
+        return v, f
+    if kind == "ellipsoid":
+        return v * np.array([2.0, 1.0, 1.0]), f
+    if kind == "star":
+        rng = np.random.default_rng(seed)
+        exps = [(a, b, c) for a in range(4) for b in range(4) for c in range(4) if 1 <= a + b + c <= 3]
+        coef = rng.standard_normal(len(exps))
+        s = np.zeros(v.shape[0])
+        for w, (a, b, c) in zip(coef, exps):
+            s += w * v[:, 0] ** a * v[:, 1] ** b * v[:, 2] ** c
+        s /= np.max(np.abs(s))
+        return v * (1.0 + amplitude * s)[:, None], f
+    raise ValueError(f"unknown shape {kind!r}")
+
+
+def serving_requests(n: int, seed: int = 0, rate: float = 20.0, n_min: int = 10_000, n_max: int = 1_000_000,
+                     k_range=(1.0, 30.0), nrhs_max: int = 16):
+    """n request specifications for the serving workload: Poisson arrivals at `rate`
+    per second, shape uniform over sphere / ellipsoid / star, N log-uniform in
+    [n_min, n_max] (rounded to a geodesic frequency, N = 60 nu^2), k uniform in
+    k_range, 1..nrhs_max right-hand sides (incident directions seeded per request)."""
+    rng = np.random.default_rng(seed)
+    t = np.cumsum(rng.exponential(1.0 / rate, size=n))
+    shapes = ["sphere", "ellipsoid", "star"]
+    out = []
+    for q in range(n):
+        target = float(np.exp(rng.uniform(np.log(n_min), np.log(n_max))))
+        nu = max(1, int(round((target / 60.0) ** 0.5)))
+        out.append({"id": q, "arrival_s": float(t[q]), "shape": shapes[int(rng.integers(3))], "nu": nu,
+                    "n_points": 60 * nu * nu, "k": float(rng.uniform(*k_range)),
+                    "nrhs": int(rng.integers(1, nrhs_max + 1)), "seed": int(rng.integers(2 ** 31))})
+    return out
+
+
 # Named workloads: (description, builder).  Triangle counts follow the
 # configurations the benchmarks and parity tests use.
 WORKLOADS = {
