@@ -354,6 +354,46 @@ void build_projection_ops(const ProjectionJob& job, double k, cudaStream_t st) {
     HFMM_CUDA(cudaStreamSynchronize(st));  // scratch buffers are freed on return
 }
 
+// ============================================================== M2L operators by reflection
+// Reflecting the whole configuration in a coordinate plane maps the basis functions
+// b_{n,m} = (radial) Q_n^|m|(cos t) e^{i m phi} onto signed basis functions of the same
+// degree: x -> -x gives (-1)^m b_{n,-m}, y -> -y gives b_{n,-m}, z -> -z gives
+// (-1)^{n+m} b_{n,m}. Both expansion kinds transform alike, so for a composition R of such
+// flips  T(R d)[c][c'] = s(c) s(c') T(d)[mu(c)][mu(c')],  with s the product of the signs
+// and mu(m) = -m when exactly one of the x, y flips is present. Only the offsets with
+// non-negative components are projected; the others follow exactly.
+__global__ void k_expand_reflections(const float2* __restrict__ canon, int P, int nops, const int4* __restrict__ map,
+                                     float2* __restrict__ out) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int op = blockIdx.y;
+    if (e >= (int64_t)P * P || op >= nops) return;
+    const int4 mp = map[op];  // (canonical operator, flip x, flip y, flip z)
+    const int c = (int)(e / P), cp = (int)(e % P);
+    auto xf = [&](int q, int& mu, int& sgn) {
+        int n = (int)sqrtf((float)q);
+        while (n * n > q) --n;
+        while ((n + 1) * (n + 1) <= q) ++n;
+        const int m = q - n * n - n;
+        sgn = 1;
+        if (mp.y && (m & 1)) sgn = -sgn;
+        if (mp.w && ((n + m) & 1)) sgn = -sgn;
+        const int m2 = (mp.y != mp.z) ? -m : m;
+        mu = n * n + n + m2;
+    };
+    int mu, s1, mu2, s2;
+    xf(c, mu, s1);
+    xf(cp, mu2, s2);
+    const float2 v = canon[(int64_t)mp.x * P * P + (int64_t)mu * P + mu2];
+    const float sg = (float)(s1 * s2);
+    out[(int64_t)op * P * P + e] = make_float2(sg * v.x, sg * v.y);
+}
+
+void expand_m2l_reflections(const float2* canon, int P, int nops, const int4* map, float2* out, cudaStream_t st) {
+    const int64_t n = (int64_t)P * P;
+    k_expand_reflections<<<dim3((unsigned)((n + 255) / 256), (unsigned)nops), 256, 0, st>>>(canon, P, nops, map, out);
+    HFMM_CUDA(cudaGetLastError());
+}
+
 // ============================================================== self / near correction
 struct d3 {
     double x, y, z;

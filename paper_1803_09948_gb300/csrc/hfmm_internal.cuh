@@ -232,6 +232,9 @@ struct ProjectionJob {
     float2* out2;      // device: nops x [Pf][Pb]
 };
 void build_projection_ops(const ProjectionJob& job, double k, cudaStream_t st);
+// out[op] = the operator of offset op from canonical operators by coordinate reflections;
+// map[op] = (canonical index, flip x, flip y, flip z) (device)
+void expand_m2l_reflections(const float2* canon, int P, int nops, const int4* map, float2* out, cudaStream_t st);
 
 struct CorrInputs {
     const double* x64s;     // sorted FP64 points (N x 3)

@@ -359,6 +359,28 @@ static void build_plan(hfmm_plan* P, const double* V, int64_t nv, const int32_t*
             d0_unit.push_back(dy);
             d0_unit.push_back(dz);
         }
+        // canonical offsets (non-negative components) and each slot's reflections of one
+        std::vector<double> canon_unit;
+        std::vector<int4> refl(316);
+        {
+            int cidx[64];
+            for (int q = 0; q < 64; ++q) cidx[q] = -1;
+            int nc = 0;
+            for (int q = 0; q < 316; ++q) {
+                const int dx = (int)d0_unit[3 * q], dy = (int)d0_unit[3 * q + 1], dz = (int)d0_unit[3 * q + 2];
+                const int key = std::abs(dx) * 16 + std::abs(dy) * 4 + std::abs(dz);
+                if (cidx[key] < 0) {
+                    cidx[key] = nc++;
+                    canon_unit.push_back(std::abs(dx));
+                    canon_unit.push_back(std::abs(dy));
+                    canon_unit.push_back(std::abs(dz));
+                }
+                refl[q] = make_int4(cidx[key], dx < 0, dy < 0, dz < 0);
+            }
+        }
+        const int ncanon = (int)(canon_unit.size() / 3);
+        DBuf<int4> d_refl;
+        d_refl.upload(refl, nullptr, st);
         for (int l = 2; l <= L; ++l) {
             const LevelInfo& li = P->lev[l];
             double a = 0.5 * std::sqrt(3.0) * li.side;
@@ -369,13 +391,17 @@ static void build_plan(hfmm_plan* P, const double* V, int64_t nv, const int32_t*
             job.rho = choose_rho(k, a, li.p);
             job.nth = job.pb + (job.pf + 1) / 2 + 16;
             job.nph = 2 * job.nth + 2;
-            job.nops = 316;
-            std::vector<double> d0(d0_unit);
+            job.nops = ncanon;
+            std::vector<double> d0(canon_unit);
             for (double& v : d0) v *= li.side;  // c_source - c_target
             job.d0 = d0.data();
-            job.out = P->ops.p + li.m2l_op;
+            DBuf<float2> canon;
+            canon.alloc((size_t)ncanon * li.P * li.P, nullptr);
+            job.out = canon.p;
             job.out2 = nullptr;
             build_projection_ops(job, k, st);
+            expand_m2l_reflections(canon.p, li.P, 316, d_refl.p, P->ops.p + li.m2l_op, st);
+            HFMM_CUDA(cudaStreamSynchronize(st));  // canon is freed at the end of this scope
             if (l >= 3) {
                 const LevelInfo& lp = P->lev[l - 1];
                 ProjectionJob pj{};
