@@ -161,6 +161,22 @@ int hfmm_solve(hfmm_plan* plan, const void* rhs, void* x_out, int nrhs, int* ite
                double* relres_out, void* stream);
 
 /*
+ * Mixed-precision iterative refinement for one right-hand side (the paper's
+ * GMRES solve taken to a tighter residual; configuration "refinement to
+ * 1e-6"): x_0 = 0; repeat  r = b - A_outer x  (formed in double-float, FP64-class),
+ * stop when |r| <= tol_outer |b|, solve A_inner d = r by GMRES on the inner plan
+ * (its own restart and tolerance), x += d (double-float).  `inner` and `outer`
+ * are plans of the same mesh and wavenumber (same N, user point order); the
+ * outer plan should be the more accurate operator (higher order, FP32 SIMT M2L).
+ * rhs, x_out: device complex64 [N].  outer_iters / inner_iters / relres_out
+ * (HOST, may be NULL): refinement steps, GMRES iterations summed over the inner
+ * solves, final |r| / |b| with the outer operator.  Returns HFMM_NOT_CONVERGED
+ * if max_outer steps do not reach tol_outer, HFMM_E_INVALID on mismatched plans.
+ */
+int hfmm_solve_refined(hfmm_plan* inner, hfmm_plan* outer, const void* rhs, void* x_out, double tol_outer,
+                       int max_outer, int* outer_iters, int* inner_iters, double* relres_out, void* stream);
+
+/*
  * hfmm_matvec for one right-hand side with CUDA events recorded on `stream`
  * between the stages; returns after completion.  stage_ms (HOST,
  * HFMM_NUM_STAGES floats) receives the device time of: 0 density prep, 1 near

@@ -28,8 +28,8 @@ HFMM_E_OVERFLOW = -6
 EXPORTED = [
     "hfmm_default_config", "hfmm_plan_create", "hfmm_plan_destroy", "hfmm_num_points", "hfmm_points",
     "hfmm_plan_info", "hfmm_matvec", "hfmm_matvec_parts", "hfmm_direct", "hfmm_rhs_planewave",
-    "hfmm_solve", "hfmm_status_string", "hfmm_last_error", "hfmm_matvec_timed", "hfmm_launch_count",
-    "hfmm_plan_costs", "hfmm_point_sum_noalloc", "hfmm_device_status",
+    "hfmm_solve", "hfmm_solve_refined", "hfmm_status_string", "hfmm_last_error", "hfmm_matvec_timed",
+    "hfmm_launch_count", "hfmm_plan_costs", "hfmm_point_sum_noalloc", "hfmm_device_status",
 ]
 HFMM_NOALLOC_MAX_POINTS = 262144
 STAGES = ["prep", "p2p", "p2m", "m2m", "m2l_simt", "m2l", "l2l", "l2p", "corr", "output"]
@@ -83,6 +83,8 @@ def lib():
         L.hfmm_direct.argtypes = [vp, vp, vp, ctypes.c_int, vp]
         L.hfmm_rhs_planewave.argtypes = [vp, dp, ctypes.c_int, vp, vp]
         L.hfmm_solve.argtypes = [vp, vp, vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), dp, vp]
+        L.hfmm_solve_refined.argtypes = [vp, vp, vp, vp, ctypes.c_double, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                         ctypes.POINTER(ctypes.c_int), dp, vp]
         L.hfmm_status_string.argtypes = [ctypes.c_int]
         L.hfmm_status_string.restype = ctypes.c_char_p
         L.hfmm_matvec_timed.argtypes = [vp, vp, vp, ctypes.POINTER(ctypes.c_float), vp]
@@ -278,6 +280,19 @@ def hfmm_solve(plan, rhs, x_out, nrhs=1, stream=None):
     return st, list(its), list(rr)
 
 
+def hfmm_solve_refined(inner, outer, rhs, x_out, tol=1e-6, max_outer=10, stream=None):
+    """Mixed-precision refinement: GMRES on `inner`, residuals with `outer` in double-float.
+    Returns (status, refinement steps, inner GMRES iterations, final relative residual)."""
+    n = hfmm_num_points(inner)
+    _vec(rhs, n, 1, "rhs")
+    _vec(x_out, n, 1, "x_out")
+    oi, ii, rr = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+    st = _check(lib().hfmm_solve_refined(inner, outer, _ptr(rhs), _ptr(x_out), float(tol), int(max_outer),
+                                         ctypes.byref(oi), ctypes.byref(ii), ctypes.byref(rr), _stream(stream)),
+                "hfmm_solve_refined")
+    return st, oi.value, ii.value, rr.value
+
+
 class Plan:
     """Owning wrapper: Plan(vertices, tris, k, **config) ... plan.close()."""
 
@@ -336,3 +351,7 @@ class Plan:
 
     def solve(self, rhs, x_out, nrhs=1, stream=None):
         return hfmm_solve(self.handle, rhs, x_out, nrhs, stream)
+
+    def solve_refined(self, outer, rhs, x_out, tol=1e-6, max_outer=10, stream=None):
+        """GMRES on this plan inside a refinement loop whose residuals use `outer`."""
+        return hfmm_solve_refined(self.handle, outer.handle, rhs, x_out, tol, max_outer, stream)

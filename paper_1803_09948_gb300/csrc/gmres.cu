@@ -668,4 +668,83 @@ int run_gmres_batched(hfmm_plan* P, const float2* rhs, float2* x_out, int R, int
     return all_done() ? HFMM_OK : HFMM_NOT_CONVERGED;
 }
 
+// ============================================================== mixed-precision refinement
+// x += d (complex64 correction into a double-float iterate)
+__global__ void k_add_c64_to_df(int64_t N, const float2* __restrict__ d, float4* __restrict__ x) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    float4 o = x[i];
+    const float2 v = d[i];
+    df_add(o.x, o.z, v.x, 0.f, o.x, o.z);
+    df_add(o.y, o.w, v.y, 0.f, o.y, o.w);
+    x[i] = o;
+}
+
+int run_refinement(hfmm_plan* Pi, hfmm_plan* Po, const float2* rhs, float2* x_out, double tol, int max_outer,
+                   int* outer_iters, int* inner_iters, double* relres, cudaStream_t st) {
+    const int64_t N = Pi->N;
+    const unsigned nb = (unsigned)((N + 255) / 256);
+    if (!Pi->rb.p || Pi->rb.n != (size_t)N) {
+        Pi->rb.alloc(N, nullptr);
+        Pi->rx.alloc(N, nullptr);
+        Pi->rr.alloc(N, nullptr);
+        Pi->r32.alloc(N, nullptr);
+        Pi->d32.alloc(N, nullptr);
+        Pi->rred.alloc((size_t)2 * RG + 2, nullptr);
+    }
+    double2* partial = (double2*)Pi->rred.p;
+    double2* small = partial + RG;
+    auto norm = [&](const float4* w) {
+        k_norm2_df<<<RG, RB, 0, st>>>(N, w, partial);
+        k_reduce<<<1, RB, 0, st>>>(partial, small);
+        Pi->launches += 2;
+        double2 h;
+        HFMM_CUDA(cudaMemcpyAsync(&h, small, sizeof(double2), cudaMemcpyDeviceToHost, st));
+        HFMM_CUDA(cudaStreamSynchronize(st));
+        return std::sqrt(h.x);
+    };
+    // A_outer applied to the iterate (its FP32 rounding; the FMM computes in FP32)
+    auto outer_residual = [&]() {
+        launch_density_prep(Po, Pi->rx.p, VecKind::DoubleFloat, Po->sig.p, st);
+        run_matvec_sorted(Po, 7, st);
+        launch_output(Po, Po->phi.p, Pi->rr.p, VecKind::DoubleFloat, st);
+        k_sub_df<<<nb, 256, 0, st>>>(N, Pi->rb.p, Pi->rr.p, Pi->rr.p);
+        Pi->launches += 1;
+        return norm(Pi->rr.p);
+    };
+    k_c64_to_df<<<nb, 256, 0, st>>>(N, rhs, Pi->rb.p);
+    HFMM_CUDA(cudaMemsetAsync(Pi->rx.p, 0, sizeof(float4) * N, st));
+    Pi->launches += 1;
+    const double bnorm = norm(Pi->rb.p);
+    int outer = 0, inner = 0;
+    double rel = 0.0;
+    if (bnorm > 0.0) {
+        HFMM_CUDA(cudaMemcpyAsync(Pi->rr.p, Pi->rb.p, sizeof(float4) * N, cudaMemcpyDeviceToDevice, st));
+        rel = 1.0;
+        while (rel > tol && outer < max_outer) {
+            // inner solve on the residual (rounded to FP32), correction added in double-float
+            k_df_to_c64<<<nb, 256, 0, st>>>(N, Pi->rr.p, Pi->r32.p);
+            Pi->launches += 1;
+            int it = 0;
+            double rr_in = 0.0;
+            run_gmres(Pi, Pi->r32.p, Pi->d32.p, &it, &rr_in, st);  // a stalled inner solve still helps
+            inner += it;
+            k_add_c64_to_df<<<nb, 256, 0, st>>>(N, Pi->d32.p, Pi->rx.p);
+            Pi->launches += 1;
+            ++outer;
+            rel = outer_residual() / bnorm;
+        }
+    } else {
+        HFMM_CUDA(cudaMemsetAsync(Pi->rx.p, 0, sizeof(float4) * N, st));
+    }
+    k_df_to_c64<<<nb, 256, 0, st>>>(N, Pi->rx.p, x_out);
+    Pi->launches += 1;
+    HFMM_CUDA(cudaGetLastError());
+    HFMM_CUDA(cudaStreamSynchronize(st));
+    if (outer_iters) *outer_iters = outer;
+    if (inner_iters) *inner_iters = inner;
+    if (relres) *relres = rel;
+    return rel <= tol ? HFMM_OK : HFMM_NOT_CONVERGED;
+}
+
 }  // namespace hfmm

@@ -182,6 +182,10 @@ struct hfmm_plan {
     DBuf<float2> bin, bout;
     DBuf<double> bred;
     int bkry_m = 0, bkry_R = 0;
+    // refinement workspace: right-hand side, iterate, residual (double-float), FP32 staging
+    DBuf<float4> rb, rx, rr;
+    DBuf<float2> r32, d32;
+    DBuf<double> rred;
     int64_t launches = 0;       // kernels launched by this plan
     double cost[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // see hfmm_plan_costs
     cudaEvent_t* stage_ev = nullptr;  // set by hfmm_matvec_timed: events after each stage
@@ -271,6 +275,8 @@ int run_gmres(hfmm_plan* P, const void* rhs, void* x, int* iters, double* relres
 // an independent Arnoldi process per right-hand side. rhs, x: device complex64 [R][N].
 int run_gmres_batched(hfmm_plan* P, const float2* rhs, float2* x, int R, int* iters, double* relres,
                       cudaStream_t st);
+int run_refinement(hfmm_plan* inner, hfmm_plan* outer, const float2* rhs, float2* x, double tol, int max_outer,
+                   int* outer_iters, int* inner_iters, double* relres, cudaStream_t st);
 // the batched matvec through the plan's captured graph (density, potential: complex64 [R][N])
 void batched_matvec(hfmm_plan* P, const float2* d, float2* o, int R, cudaStream_t st);
 

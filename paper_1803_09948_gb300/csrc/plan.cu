@@ -848,6 +848,19 @@ int hfmm_rhs_planewave(hfmm_plan* P, const double* dirs, int nrhs, void* rhs_out
     HFMM_GUARD_END
 }
 
+int hfmm_solve_refined(hfmm_plan* inner, hfmm_plan* outer, const void* rhs, void* x_out, double tol_outer,
+                       int max_outer, int* outer_iters, int* inner_iters, double* relres_out, void* stream) {
+    if (!inner || !outer || !rhs || !x_out || !(tol_outer > 0.0) || max_outer < 1) return HFMM_E_INVALID;
+    if (inner->N != outer->N || inner->k != outer->k) {
+        hfmm_set_last_error("hfmm_solve_refined: the inner and outer plans differ in N or k");
+        return HFMM_E_INVALID;
+    }
+    HFMM_GUARD_BEGIN
+    return run_refinement(inner, outer, (const float2*)rhs, (float2*)x_out, tol_outer, max_outer, outer_iters,
+                          inner_iters, relres_out, (cudaStream_t)stream);
+    HFMM_GUARD_END
+}
+
 int hfmm_solve(hfmm_plan* P, const void* rhs, void* x_out, int nrhs, int* iters_out, double* relres_out,
                void* stream) {
     if (!P || !rhs || !x_out || nrhs < 1) return HFMM_E_INVALID;
