@@ -297,3 +297,36 @@ def mie_surface_q(X, k, a=1.0, d=(0.0, 0.0, 1.0), nmax=None):
         hn = spherical_jn(n, ka) + 1j * spherical_yn(n, ka)
         q += (1j ** n) * (2 * n + 1) * eval_legendre(n, ct) / hn
     return -(1j / (k * a * a)) * q
+
+
+def field_direct(X, W, k, sigma, targets):
+    """Off-surface single-layer potential by its definition (point rule of Eq. 10 with
+    the targets apart from the points):  u(t) = sum_j W_j exp(i k |t - x_j|) / (4 pi |t - x_j|) sigma_j."""
+    X, W, T = _f64(X).reshape(-1, 3), _f64(W), _f64(targets).reshape(-1, 3)
+    s = _c128(sigma) * W
+    out = np.zeros(T.shape[0], dtype=np.complex128)
+    for a in range(0, T.shape[0], 64):
+        R = np.linalg.norm(T[a:a + 64, None, :] - X[None, :, :], axis=2)
+        out[a:a + 64] = (np.exp(1j * k * R) / (4.0 * np.pi * R)) @ s
+    return out
+
+
+def mie_scattered(T, k, a=1.0, d=(0.0, 0.0, 1.0), nmax=None):
+    """Exact scattered field outside the sound-soft sphere of radius a hit by exp(i k d.x):
+    p_s(r, theta) = -sum_n i^n (2n+1) j_n(ka) / h_n(ka) h_n(kr) P_n(cos theta)  (h = h^(1))."""
+    from scipy.special import eval_legendre, spherical_jn, spherical_yn
+
+    T = np.asarray(T, dtype=np.float64).reshape(-1, 3)
+    d = np.asarray(d, dtype=np.float64)
+    d = d / np.linalg.norm(d)
+    r = np.linalg.norm(T, axis=1)
+    ct = (T @ d) / r
+    ka = k * a
+    if nmax is None:
+        nmax = int(ka + 10 * max(1.0, ka) ** (1.0 / 3.0) + 10)
+    p = np.zeros(T.shape[0], dtype=np.complex128)
+    for n in range(nmax + 1):
+        ha = spherical_jn(n, ka) + 1j * spherical_yn(n, ka)
+        hr = spherical_jn(n, k * r) + 1j * spherical_yn(n, k * r)
+        p -= (1j ** n) * (2 * n + 1) * spherical_jn(n, ka) / ha * hr * eval_legendre(n, ct)
+    return p

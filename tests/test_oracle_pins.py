@@ -339,3 +339,41 @@ def test_solution_converges_to_mie_series():
         qm = oracle.mie_surface_q(X, 1.0)
         errs.append(np.linalg.norm(q - qm) / np.linalg.norm(qm))
     assert errs[1] < 1e-2 and errs[1] < errs[0] / 2
+
+
+def test_mie_scattered_cancels_the_incident_wave_on_the_sphere():
+    """Sound-soft boundary condition: p_inc + p_s = 0 at r = a, for several k and directions."""
+    rng = np.random.default_rng(3)
+    for k in (0.5, 2.0, 7.0):
+        U = rng.standard_normal((40, 3))
+        U /= np.linalg.norm(U, axis=1, keepdims=True)
+        d = np.array([0.3, -0.4, 0.866])
+        d /= np.linalg.norm(d)
+        ps = oracle.mie_scattered(1.5 * U, k, a=1.5, d=d)
+        pinc = np.exp(1j * k * (1.5 * U) @ d)
+        assert np.max(np.abs(ps + pinc)) < 1e-10
+
+
+def test_mie_scattered_outgoing_at_large_distance():
+    """Radiation condition: r p_s e^{-ikr} tends to a function of direction only."""
+    U = np.array([[0.0, 0.6, 0.8]])
+    k = 3.0
+    f1 = oracle.mie_scattered(200.0 * U, k) * 200.0 * np.exp(-1j * k * 200.0)
+    f2 = oracle.mie_scattered(400.0 * U, k) * 400.0 * np.exp(-1j * k * 400.0)
+    assert abs(f1[0] - f2[0]) < 2e-2 * abs(f2[0])
+
+
+def test_field_direct_single_source_and_reciprocity():
+    """One source: the Green's function itself; two point sets: u_A(B) . s_B = u_B(A) . s_A."""
+    k = 1.7
+    X = np.array([[0.1, -0.2, 0.3]])
+    T = np.array([[2.0, 1.0, -0.5], [0.0, 0.0, 4.0]])
+    u = oracle.field_direct(X, [2.0], k, [0.5 - 0.25j], T)
+    R = np.linalg.norm(T - X, axis=1)
+    assert np.allclose(u, 2.0 * (0.5 - 0.25j) * np.exp(1j * k * R) / (4 * np.pi * R), rtol=1e-14)
+    rng = np.random.default_rng(5)
+    A, B = rng.standard_normal((7, 3)), rng.standard_normal((5, 3)) + 5.0
+    sa, sb = rng.standard_normal(7) + 1j * rng.standard_normal(7), rng.standard_normal(5) + 1j * rng.standard_normal(5)
+    uab = oracle.field_direct(A, np.ones(7), k, sa, B)
+    uba = oracle.field_direct(B, np.ones(5), k, sb, A)
+    assert abs(np.dot(uab, sb) - np.dot(uba, sa)) < 1e-12 * abs(np.dot(uab, sb))
