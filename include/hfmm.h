@@ -161,6 +161,20 @@ int hfmm_solve(hfmm_plan* plan, const void* rhs, void* x_out, int nrhs, int* ite
                double* relres_out, void* stream);
 
 /*
+ * Off-surface evaluation (the paper's scattered field at observation points,
+ * Sec. 6.4): field[t] = sum_j w_j exp(i k |t - x_j|) / (4 pi |t - x_j|) density_j,
+ * the single-layer potential of the density at n_targets points t away from the
+ * surface (the point rule: accurate for targets farther than about one mean edge
+ * length from the surface).  density: device complex64 [N], user order;
+ * targets: HOST doubles [n_targets][3]; field_out: device complex64
+ * [n_targets].  Direct summation on the device (all pairs, FP32 arithmetic on
+ * positions split into FP32 hi + lo).  For the sound-soft scattering problem the
+ * scattered field is -field of the solved density.  Stream-ordered.
+ */
+int hfmm_field(hfmm_plan* plan, const void* density, const double* targets, int64_t n_targets, void* field_out,
+               void* stream);
+
+/*
  * Mixed-precision iterative refinement for one right-hand side (the paper's
  * GMRES solve taken to a tighter residual; configuration "refinement to
  * 1e-6"): x_0 = 0; repeat  r = b - A_outer x  (formed in double-float, FP64-class),

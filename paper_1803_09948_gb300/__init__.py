@@ -29,7 +29,7 @@ EXPORTED = [
     "hfmm_default_config", "hfmm_plan_create", "hfmm_plan_destroy", "hfmm_num_points", "hfmm_points",
     "hfmm_plan_info", "hfmm_matvec", "hfmm_matvec_parts", "hfmm_direct", "hfmm_rhs_planewave",
     "hfmm_solve", "hfmm_solve_refined", "hfmm_status_string", "hfmm_last_error", "hfmm_matvec_timed",
-    "hfmm_launch_count", "hfmm_plan_costs", "hfmm_point_sum_noalloc", "hfmm_device_status",
+    "hfmm_launch_count", "hfmm_plan_costs", "hfmm_point_sum_noalloc", "hfmm_device_status", "hfmm_field",
 ]
 HFMM_NOALLOC_MAX_POINTS = 262144
 STAGES = ["prep", "p2p", "p2m", "m2m", "m2l_simt", "m2l", "l2l", "l2p", "corr", "output"]
@@ -83,6 +83,7 @@ def lib():
         L.hfmm_direct.argtypes = [vp, vp, vp, ctypes.c_int, vp]
         L.hfmm_rhs_planewave.argtypes = [vp, dp, ctypes.c_int, vp, vp]
         L.hfmm_solve.argtypes = [vp, vp, vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), dp, vp]
+        L.hfmm_field.argtypes = [vp, vp, dp, i64, vp, vp]
         L.hfmm_solve_refined.argtypes = [vp, vp, vp, vp, ctypes.c_double, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                          ctypes.POINTER(ctypes.c_int), dp, vp]
         L.hfmm_status_string.argtypes = [ctypes.c_int]
@@ -280,6 +281,16 @@ def hfmm_solve(plan, rhs, x_out, nrhs=1, stream=None):
     return st, list(its), list(rr)
 
 
+def hfmm_field(plan, density, targets, field_out, stream=None):
+    """Single-layer potential of `density` at off-surface `targets` (host array [n][3])."""
+    n = hfmm_num_points(plan)
+    _vec(density, n, 1, "density")
+    T = np.ascontiguousarray(np.asarray(targets, dtype=np.float64).reshape(-1, 3))
+    _vec(field_out, T.shape[0], 1, "field_out")
+    _check(lib().hfmm_field(plan, _ptr(density), T.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), T.shape[0],
+                            _ptr(field_out), _stream(stream)), "hfmm_field")
+
+
 def hfmm_solve_refined(inner, outer, rhs, x_out, tol=1e-6, max_outer=10, stream=None):
     """Mixed-precision refinement: GMRES on `inner`, residuals with `outer` in double-float.
     Returns (status, refinement steps, inner GMRES iterations, final relative residual)."""
@@ -351,6 +362,9 @@ class Plan:
 
     def solve(self, rhs, x_out, nrhs=1, stream=None):
         return hfmm_solve(self.handle, rhs, x_out, nrhs, stream)
+
+    def field(self, density, targets, field_out, stream=None):
+        hfmm_field(self.handle, density, targets, field_out, stream)
 
     def solve_refined(self, outer, rhs, x_out, tol=1e-6, max_outer=10, stream=None):
         """GMRES on this plan inside a refinement loop whose residuals use `outer`."""

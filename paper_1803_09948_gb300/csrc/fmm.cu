@@ -1452,4 +1452,79 @@ void batched_matvec(hfmm_plan* P, const float2* d, float2* o, int R, cudaStream_
     P->launches += B.g_launches;
 }
 
+// ============================================================== off-surface evaluation
+// Sources staged as FP32 hi + lo positions (relative to the mesh's bounding-box centre) and
+// the strength w sigma / (4 pi); a source-target difference (t_hi - s_hi) + (t_lo - s_lo) is
+// then exact to ~1e-14 before the FP32 distance is formed.
+__global__ void k_field_stage(int64_t N, const double* __restrict__ x64, const double* __restrict__ w,
+                              const float2* __restrict__ density, double cx, double cy, double cz,
+                              float4* __restrict__ hi, float4* __restrict__ lo) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const double x = x64[3 * i] - cx, y = x64[3 * i + 1] - cy, z = x64[3 * i + 2] - cz;
+    const float xh = (float)x, yh = (float)y, zh = (float)z;
+    const double sc = w[i] / (4.0 * 3.14159265358979323846);
+    const float2 d = density[i];
+    hi[i] = make_float4(xh, yh, zh, (float)(sc * d.x));
+    lo[i] = make_float4((float)(x - xh), (float)(y - yh), (float)(z - zh), (float)(sc * d.y));
+}
+
+__global__ void __launch_bounds__(256) k_field(int64_t nt, const double* __restrict__ tg, double cx, double cy,
+                                               double cz, int64_t N, const float4* __restrict__ hi,
+                                               const float4* __restrict__ lo, float k, float2* __restrict__ out) {
+    __shared__ float4 sh[256], sl[256];
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    float th[3] = {0.f, 0.f, 0.f}, tl[3] = {0.f, 0.f, 0.f};
+    if (t < nt) {
+        const double p[3] = {tg[3 * t] - cx, tg[3 * t + 1] - cy, tg[3 * t + 2] - cz};
+        for (int d = 0; d < 3; ++d) {
+            th[d] = (float)p[d];
+            tl[d] = (float)(p[d] - (double)th[d]);
+        }
+    }
+    float ar = 0.f, ai = 0.f;
+    for (int64_t j0 = 0; j0 < N; j0 += 256) {
+        const int64_t j = j0 + threadIdx.x;
+        if (j < N) {
+            sh[threadIdx.x] = hi[j];
+            sl[threadIdx.x] = lo[j];
+        }
+        __syncthreads();
+        const int cnt = (N - j0 < 256) ? (int)(N - j0) : 256;
+        for (int q = 0; q < cnt; ++q) {
+            const float4 a = sh[q], b = sl[q];
+            const float dx = (th[0] - a.x) + (tl[0] - b.x);
+            const float dy = (th[1] - a.y) + (tl[1] - b.y);
+            const float dz = (th[2] - a.z) + (tl[2] - b.z);
+            const float r = sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+            float sn, cs;
+            sincosf(k * r, &sn, &cs);
+            const float ir = 1.f / r;
+            const float re = cs * ir, im = sn * ir;
+            ar = fmaf(a.w, re, fmaf(-b.w, im, ar));
+            ai = fmaf(a.w, im, fmaf(b.w, re, ai));
+        }
+        __syncthreads();
+    }
+    if (t < nt) out[t] = make_float2(ar, ai);
+}
+
+void run_field(hfmm_plan* P, const float2* density, const double* targets, int64_t nt, float2* out,
+               cudaStream_t st) {
+    const int64_t N = P->N;
+    if (!P->w_user.p) {
+        P->w_user.upload(P->host_w, nullptr, st);
+        P->fsrc_hi.alloc(N, nullptr);
+        P->fsrc_lo.alloc(N, nullptr);
+    }
+    const double cx = P->lo[0] + 0.5 * P->D, cy = P->lo[1] + 0.5 * P->D, cz = P->lo[2] + 0.5 * P->D;
+    k_field_stage<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(N, P->x64.p, P->w_user.p, density, cx, cy, cz,
+                                                               P->fsrc_hi.p, P->fsrc_lo.p);
+    if (nt > 0)
+        k_field<<<(unsigned)((nt + 255) / 256), 256, 0, st>>>(nt, targets, cx, cy, cz, N, P->fsrc_hi.p,
+                                                              P->fsrc_lo.p, (float)P->k, out);
+    P->launches += 2;
+    HFMM_CUDA(cudaGetLastError());
+}
+
 }  // namespace hfmm

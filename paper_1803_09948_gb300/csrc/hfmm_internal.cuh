@@ -182,6 +182,9 @@ struct hfmm_plan {
     DBuf<float2> bin, bout;
     DBuf<double> bred;
     int bkry_m = 0, bkry_R = 0;
+    // off-surface evaluation: staged sources (position hi, position lo, strength)
+    DBuf<float4> fsrc_hi, fsrc_lo;
+    DBuf<double> w_user;
     // refinement workspace: right-hand side, iterate, residual (double-float), FP32 staging
     DBuf<float4> rb, rx, rr;
     DBuf<float2> r32, d32;
@@ -212,6 +215,8 @@ void run_matvec_sorted(hfmm_plan* P, int parts, cudaStream_t st);
 // records stage event q (if timing is active)
 void mark_stage(hfmm_plan* P, int q, cudaStream_t st);
 void run_direct_sorted(hfmm_plan* P, cudaStream_t st);
+// field at targets (device doubles [n][3]) of the density (device complex64, user order)
+void run_field(hfmm_plan* P, const float2* density, const double* targets, int64_t nt, float2* out, cudaStream_t st);
 // Batched matvec for R right-hand sides (BatchState): whether this plan supports it,
 // building the work lists and buffers, and one matvec (density, potential: device
 // complex64, N x R column-major, user order).

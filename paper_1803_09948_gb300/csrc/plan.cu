@@ -848,6 +848,22 @@ int hfmm_rhs_planewave(hfmm_plan* P, const double* dirs, int nrhs, void* rhs_out
     HFMM_GUARD_END
 }
 
+int hfmm_field(hfmm_plan* P, const void* density, const double* targets, int64_t n_targets, void* field_out,
+               void* stream) {
+    if (!P || !density || (n_targets > 0 && (!targets || !field_out)) || n_targets < 0) return HFMM_E_INVALID;
+    for (int64_t t = 0; t < 3 * n_targets; ++t)
+        if (!std::isfinite(targets[t])) return HFMM_E_INVALID;
+    HFMM_GUARD_BEGIN
+    cudaStream_t st = (cudaStream_t)stream;
+    std::vector<double> tg(targets, targets + 3 * n_targets);
+    DBuf<double> d_tg;
+    d_tg.upload(tg, nullptr, st);
+    run_field(P, (const float2*)density, d_tg.p, n_targets, (float2*)field_out, st);
+    HFMM_CUDA(cudaStreamSynchronize(st));  // the target buffer is freed on return
+    return HFMM_OK;
+    HFMM_GUARD_END
+}
+
 int hfmm_solve_refined(hfmm_plan* inner, hfmm_plan* outer, const void* rhs, void* x_out, double tol_outer,
                        int max_outer, int* outer_iters, int* inner_iters, double* relres_out, void* stream) {
     if (!inner || !outer || !rhs || !x_out || !(tol_outer > 0.0) || max_outer < 1) return HFMM_E_INVALID;
