@@ -155,7 +155,9 @@ constexpr int kEpilogue = 128;     // threads draining TMEM (warps 0..3, one per
 constexpr int kMmaWarp = (kEpilogue + kProducers) / 32;  // TMEM owner and MMA issuer
 constexpr int kIssuerWarp = kMmaWarp + 1;                // first output-issuing warp
 constexpr int kThreads = kEpilogue + kProducers + 32 + 32 * kIssuers;
-static_assert(kOutStages == 2 * kIssuers, "each issuer cycles through two output stages");
+// the epilogue reuses the stage of item w - kOutStages, which its issuer frees after
+// committing its next item w - kOutStages + kIssuers: that item must precede w
+static_assert(kOutStages > kIssuers, "output stages must outnumber the issuers");
 
 struct TcSmem {
     __nv_bfloat16 b[kStages][2][kN * kK];   // gathered multipoles: hi, lo per stage
