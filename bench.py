@@ -31,6 +31,7 @@ WORKLOADS = {
     "sphere_655360": ("sphere_655360", 20.0, {}, 50),
     "sphere_1280": ("sphere_1280", 1.0, {"p_fixed": 8}, 30),
     "sphere_163840": ("sphere_163840", 10.0, {}, 50),
+    "sphere_40960": ("sphere_40960", 10.0, {}, 50),
     # GMRES(50) stagnates near 5e-4 on this body at k = 30; GMRES(200) converges
     "ellipsoid_1310720": ("ellipsoid_1310720", 30.0, {}, 200),
 }

@@ -218,6 +218,8 @@ def serving_requests(n: int, seed: int = 0, rate: float = 20.0, n_min: int = 10_
 WORKLOADS = {
     # 20 * 4**3 = 1,280 triangles -> N = 3,840 points
     "sphere_1280": ("unit sphere, icosphere level 3", lambda: sphere_mesh(3)),
+    # 20 * 4**5 * 2 = 40,960 triangles -> N = 122,880 points (small batched case for profiling)
+    "sphere_40960": ("unit sphere, icosphere level 5 + longest-edge bisection", lambda: sphere_mesh(5, True)),
     # 20 * 4**6 * 2 = 163,840 triangles -> N = 491,520 points
     "sphere_163840": ("unit sphere, icosphere level 6 + longest-edge bisection", lambda: sphere_mesh(6, True)),
     # 20 * 4**7 * 2 = 655,360 triangles -> N = 1,966,080 points
