@@ -548,6 +548,10 @@ __global__ void __launch_bounds__(128) k_translate(const TransItem* __restrict__
     int ncol = it.ncol, Pin = it.pin, Pout = it.pout;
     const int r0 = TR * (int)blockIdx.y;
     if (r0 >= Pout) return;  // uniform over the block: items of a lower order in the same launch
+    // blockIdx.z: a range of K (launched only for accumulating items, whose outputs are reductions)
+    const int kchunk = ((Pin + (int)gridDim.z - 1) / (int)gridDim.z + KS - 1) / KS * KS;
+    const int kb = kchunk * (int)blockIdx.z, ke = min(Pin, kb + kchunk);
+    if (kb >= ke) return;
     if (tid < TC) {
         int2 v = make_int2(0, 0);
         if (tid < ncol) {
@@ -577,18 +581,18 @@ __global__ void __launch_bounds__(128) k_translate(const TransItem* __restrict__
         for (int q = 0; q < NT; ++q) {
             const int e = tid + 128 * q, rr = e / KS, kk = e % KS;
             const int r = r0 + rr, kq = k0 + kk;
-            rT[q] = (r < Pout && kq < Pin) ? __ldg(T + (int64_t)r * Pin + kq) : make_float2(0.f, 0.f);
+            rT[q] = (r < Pout && kq < ke) ? __ldg(T + (int64_t)r * Pin + kq) : make_float2(0.f, 0.f);
         }
 #pragma unroll
         for (int q = 0; q < NX; ++q) {
             const int e = tid + 128 * q, cc = e / KS, kk = e % KS;
             const int kq = k0 + kk;
-            rX[q] = (e < KS * TC && cc < ncol && kq < Pin) ? __ldg(coef + it.src + (int64_t)sc[cc].x * Pin + kq)
-                                                           : make_float2(0.f, 0.f);
+            rX[q] = (e < KS * TC && cc < ncol && kq < ke) ? __ldg(coef + it.src + (int64_t)sc[cc].x * Pin + kq)
+                                                          : make_float2(0.f, 0.f);
         }
     };
-    fetch(0);
-    for (int k0 = 0; k0 < Pin; k0 += KS) {
+    fetch(kb);
+    for (int k0 = kb; k0 < ke; k0 += KS) {
 #pragma unroll
         for (int q = 0; q < NT; ++q) {
             const int e = tid + 128 * q;
@@ -600,7 +604,7 @@ __global__ void __launch_bounds__(128) k_translate(const TransItem* __restrict__
             if (e < KS * TC) sX[e % KS][e / KS] = rX[q];
         }
         __syncthreads();
-        if (k0 + KS < Pin) fetch(k0 + KS);
+        if (k0 + KS < ke) fetch(k0 + KS);
 #pragma unroll 8
         for (int kk = 0; kk < KS; ++kk) {
             float2 a[4], b[4];
@@ -651,11 +655,29 @@ __global__ void __launch_bounds__(256) k_corr(int64_t N, const int64_t* __restri
     float ar = 0.f, ai = 0.f;
     if (active) {
         const int64_t e0 = __ldg(ptr + row), e1 = __ldg(ptr + row + 1);
-        for (int64_t e = e0 + sub; e < e1; e += kCorrLanes) {
+        int64_t e = e0 + sub;
+        // four nonzeros per lane per pass: their loads are all in flight together
+        for (; e + 3 * kCorrLanes < e1; e += 4 * kCorrLanes) {
+            int32_t c[4];
+            float2 v[4], g[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                c[q] = __ldg(col + e + q * kCorrLanes);
+                v[q] = __ldg(val + e + q * kCorrLanes);
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) g[q] = __ldg(sig + c[q]);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                ar = fmaf(v[q].x, g[q].x, fmaf(-v[q].y, g[q].y, ar));
+                ai = fmaf(v[q].x, g[q].y, fmaf(v[q].y, g[q].x, ai));
+            }
+        }
+        for (; e < e1; e += kCorrLanes) {
             const float2 v = __ldg(val + e);
-            const float2 s = __ldg(sig + __ldg(col + e));
-            ar = fmaf(v.x, s.x, fmaf(-v.y, s.y, ar));
-            ai = fmaf(v.x, s.y, fmaf(v.y, s.x, ai));
+            const float2 g = __ldg(sig + __ldg(col + e));
+            ar = fmaf(v.x, g.x, fmaf(-v.y, g.y, ar));
+            ai = fmaf(v.x, g.y, fmaf(v.y, g.x, ai));
         }
     }
 #pragma unroll
@@ -741,12 +763,13 @@ void mark_stage(hfmm_plan* P, int q, cudaStream_t st) {
     if (P->stage_ev) HFMM_CUDA(cudaEventRecord(P->stage_ev[q], st));
 }
 
-// Items [b, e) of at most `width` columns (64, 16 or 8) and output order <= pout_max.
+// Items [b, e) of at most `width` columns (64, 16 or 8) and output order <= pout_max; kparts > 1
+// splits K across blocks and needs accumulating (atomic) items.
 static void launch_translate(hfmm_plan* P, const TransItem* items, float2* coef, int rhs, int64_t b, int64_t e,
-                             int pout_max, int width, cudaStream_t st) {
+                             int pout_max, int width, cudaStream_t st, int kparts = 1) {
     if (e <= b) return;
     const int rows = width > 16 ? 32 : width > 8 ? 128 : 256;
-    const dim3 grid((unsigned)(e - b), (unsigned)((pout_max + rows - 1) / rows));
+    const dim3 grid((unsigned)(e - b), (unsigned)((pout_max + rows - 1) / rows), (unsigned)kparts);
     if (width > 16)
         k_translate<16><<<grid, 128, 0, st>>>(items, b, P->item_cols.p, P->ops.p, coef, rhs);
     else if (width > 8)
@@ -818,8 +841,9 @@ void run_matvec_sorted(hfmm_plan* P, int parts, cudaStream_t st) {
         }
     mark_stage(P, 4, st);
     if (far)
-        for (const SimtRange& r : P->m2l_simt)
-            launch_translate(P, P->items.p, P->coef.p, 1, r.begin, r.end, r.pout_max, r.width, st);
+        for (const SimtRange& r : P->m2l_simt)  // high orders: K in 2-3 parts for more blocks in flight
+            launch_translate(P, P->items.p, P->coef.p, 1, r.begin, r.end, r.pout_max, r.width, st,
+                             r.pout_max >= 200 ? 3 : r.pout_max >= 100 ? 2 : 1);
     mark_stage(P, 5, st);
     if (far) {
         if (P->n_tc_groups > 0) {
