@@ -1,4 +1,5 @@
-// Plan-time FP64 kernels: translation operators and the sparse self/near correction.
+// Plan-time kernels: translation operators (FP64) and the sparse self/near correction
+// (FP64 geometry, FP32 quadrature nodes).
 //
 // Translation operators (Sec. 2.3, Eq. 11-14).  Expansions use the addition theorem
 //   G(x,y) = i k sum_{n,m} h_n(k r_x) Y_nm(x^) j_n(k r_y) conj(Y_nm(y^)),  r_y < r_x,
@@ -15,8 +16,8 @@
 // Self/near correction (Sec. 2.2, Listing 1): for target x_i and each triangle in
 // its singular set, int_T G(x_i,y) L_a(y) dS_y by a Duffy-type collapse about the
 // point of T nearest to x_i, with a sinh grading of the edge coordinate (and of
-// the radius when x_i is off the triangle), minus the point-rule term that the
-// FMM already added.
+// the radius when x_i is off the triangle), minus the point-rule term (FP64) that
+// the FMM already added.
 #include <cmath>
 #include <cstdio>
 #include <vector>
@@ -429,9 +430,18 @@ __device__ static d3 closest_on_triangle(d3 p, d3 a, d3 b, d3 c) {
     return a + (vb * den) * ab + (vc * den) * ac;
 }
 
+__device__ __forceinline__ float3 f3(d3 a) { return make_float3((float)a.x, (float)a.y, (float)a.z); }
+
 // out[a] = int_T G(x,y) (2 lambda_a(y) - 1/3) dS_y
+//
+// The geometry of each sub-triangle (nearest point, edge frame, the limits of the
+// sinh-graded edge coordinate) is taken in FP64; the 3 nq^2 quadrature nodes run in
+// FP32 in coordinates relative to x (lengths of the order of the mesh size, so the
+// node positions keep FP32's relative precision), each row of nq nodes summed in FP32
+// and the rows in FP64.  Every node term is positive apart from the phase, so the
+// integrals carry about 1e-6 relative error against 1e-7 for FP32 storage.
 __device__ static void tri_integrals(d3 x, d3 v0, d3 v1, d3 v2, double k, bool self, int nq,
-                                     const double* gx, const double* gw, double2 out[3]) {
+                                     const float* gx, const float* gw, double2 out[3]) {
     d3 nn = cross(v1 - v0, v2 - v0);
     double twoA = nrm(nn);
     d3 nh = (1.0 / twoA) * nn;
@@ -443,7 +453,11 @@ __device__ static void tri_integrals(d3 x, d3 v0, d3 v1, d3 v2, double k, bool s
     double delta = self ? 0.0 : nrm(x - pc);
     d3 vv[3] = {v0, v1, v2};
     double acc_r[3] = {0, 0, 0}, acc_i[3] = {0, 0, 0};
-    const double inv4pi = 1.0 / (4.0 * kPi);
+    // node-loop constants: positions relative to x, barycentric gradients
+    const float3 pcx = f3(pc - x), pcv = f3(pc - v0);
+    const float3 gf[3] = {f3(g[0]), f3(g[1]), f3(g[2])};
+    const float kf = (float)k, deltaf = (float)delta;
+    const float inv4pi = (float)(1.0 / (4.0 * kPi));
     for (int e = 0; e < 3; ++e) {
         d3 a = vv[e], b = vv[(e + 1) % 3];
         d3 ed = b - a;
@@ -455,37 +469,49 @@ __device__ static void tri_integrals(d3 x, d3 v0, d3 v1, d3 v2, double k, bool s
         double de = nrm(perp);
         if (de <= 1e-12 * len) continue;  // pc on this edge: empty sub-triangle
         double s0 = asinh(lm / de), s1 = asinh(lp / de);
+        const float s0f = (float)s0, dsf = (float)(s1 - s0), def = (float)de;
+        const float3 pf = f3(perp), lf = f3(lh);
         for (int iq = 0; iq < nq; ++iq) {
-            double s = s0 + (s1 - s0) * gx[iq];
-            double ws = (s1 - s0) * gw[iq];
-            double l = de * sinh(s);
-            d3 E = perp + l * lh;
-            double En = nrm(E);  // = de cosh(s) = dl/ds
-            double tmax_tau = delta > 0.0 ? asinh(En / delta) : 1.0;
+            const float s = s0f + dsf * gx[iq];
+            const float ws = dsf * gw[iq];
+            const float l = def * sinhf(s);
+            const float3 E = make_float3(pf.x + l * lf.x, pf.y + l * lf.y, pf.z + l * lf.z);
+            const float En = sqrtf(E.x * E.x + E.y * E.y + E.z * E.z);  // = de cosh(s) = dl/ds
+            const float tmax_tau = delta > 0.0 ? asinhf(En / deltaf) : 1.0f;
+            const float rowc = def * En * ws;
+            float rr[3] = {0.f, 0.f, 0.f}, ri[3] = {0.f, 0.f, 0.f};
             for (int jq = 0; jq < nq; ++jq) {
-                double t, wt;
+                float t, wt;
                 if (delta > 0.0) {
-                    double tau = tmax_tau * gx[jq];
-                    t = (delta / En) * sinh(tau);
-                    wt = tmax_tau * gw[jq] * (delta / En) * cosh(tau);
+                    const float tau = tmax_tau * gx[jq];
+                    const float q = deltaf / En;
+                    t = q * sinhf(tau);
+                    wt = tmax_tau * gw[jq] * q * coshf(tau);
                 } else {
                     t = gx[jq];
                     wt = gw[jq];
                 }
-                d3 y = pc + t * E;
-                double R = nrm(x - y);
+                // y - x and y - v0 for y = pc + t E
+                const float3 yx = make_float3(pcx.x + t * E.x, pcx.y + t * E.y, pcx.z + t * E.z);
+                const float3 yv = make_float3(pcv.x + t * E.x, pcv.y + t * E.y, pcv.z + t * E.z);
+                const float R = sqrtf(yx.x * yx.x + yx.y * yx.y + yx.z * yx.z);
                 // dS = t * de * dl * dt = t * de * En * ds * dt
-                double jac = t * de * En * ws * wt;
-                double sn, cs;
-                sincos(k * R, &sn, &cs);
-                double f = jac * inv4pi / R;
-                d3 yv = y - v0;
-                double lam[3] = {1.0 + dot(g[0], yv), dot(g[1], yv), dot(g[2], yv)};
+                float sn, cs;
+                sincosf(kf * R, &sn, &cs);
+                const float f = t * rowc * wt * inv4pi / R;
+                const float lam[3] = {1.0f + gf[0].x * yv.x + gf[0].y * yv.y + gf[0].z * yv.z,
+                                      gf[1].x * yv.x + gf[1].y * yv.y + gf[1].z * yv.z,
+                                      gf[2].x * yv.x + gf[2].y * yv.y + gf[2].z * yv.z};
+#pragma unroll
                 for (int q = 0; q < 3; ++q) {
-                    double L = 2.0 * lam[q] - 1.0 / 3.0;
-                    acc_r[q] += f * cs * L;
-                    acc_i[q] += f * sn * L;
+                    const float L = 2.0f * lam[q] - (1.0f / 3.0f);
+                    rr[q] += f * cs * L;
+                    ri[q] += f * sn * L;
                 }
+            }
+            for (int q = 0; q < 3; ++q) {
+                acc_r[q] += (double)rr[q];
+                acc_i[q] += (double)ri[q];
             }
         }
     }
@@ -566,6 +592,12 @@ __global__ void k_corr_count(CorrInputs in, int64_t* __restrict__ rowptr, int* _
 __global__ void k_corr_fill(CorrInputs in, const double* __restrict__ gx, const double* __restrict__ gw,
                             const int64_t* __restrict__ rowptr, int32_t* __restrict__ col,
                             float2* __restrict__ val, int* __restrict__ overflow) {
+    __shared__ float sgx[64], sgw[64];  // the rule on [0, 1] (quad_order <= 64)
+    for (int q = threadIdx.x; q < in.quad_order; q += blockDim.x) {
+        sgx[q] = (float)gx[q];
+        sgw[q] = (float)gw[q];
+    }
+    __syncthreads();
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= in.N) return;
     int32_t list[HFMM_NEAR_CAP];
@@ -581,7 +613,7 @@ __global__ void k_corr_fill(CorrInputs in, const double* __restrict__ gx, const 
             v[a] = mk(in.V[3 * (int64_t)vi], in.V[3 * (int64_t)vi + 1], in.V[3 * (int64_t)vi + 2]);
         }
         double2 I3[3];
-        tri_integrals(x, v[0], v[1], v[2], in.k, n == own, in.quad_order, gx, gw, I3);
+        tri_integrals(x, v[0], v[1], v[2], in.k, n == own, in.quad_order, sgx, sgw, I3);
         for (int a = 0; a < 3; ++a) {
             int32_t js = in.iperm[3 * (int64_t)n + a];
             double re = I3[a].x, im = I3[a].y;

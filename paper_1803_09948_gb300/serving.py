@@ -81,9 +81,10 @@ class Admission:
             self._cv.notify_all()
 
 
-def gpu_executor(restart: int = 30, tol: float = 1e-4):
+def gpu_executor(restart: int = 30, tol: float = 1e-4, keep_solution: bool = False):
     """Executor that solves a request with the library on the calling thread's stream.
-    Returns a function(request, stream) -> dict of timings and results."""
+    Returns a function(request, stream) -> dict of timings and results (with the
+    solutions, [nrhs][N] complex64 on the host, under "x" when keep_solution)."""
     import torch
 
     from . import Plan
@@ -102,10 +103,13 @@ def gpu_executor(restart: int = 30, tol: float = 1e-4):
                 status, its, rr = plan.solve(b, x, R, stream=stream)
                 x_host = x.to("cpu", non_blocking=False)  # the response
                 t2 = time.perf_counter()
-                return {"status": int(status), "iterations": [int(v) for v in its],
-                        "relres": [float(v) for v in rr], "n_points": N, "build_s": t1 - t0,
-                        "solve_s": t2 - t1, "device_bytes": plan.info()["device_bytes"],
-                        "response_bytes": x_host.numel() * 8}
+                out = {"status": int(status), "iterations": [int(v) for v in its],
+                       "relres": [float(v) for v in rr], "n_points": N, "build_s": t1 - t0,
+                       "solve_s": t2 - t1, "device_bytes": plan.info()["device_bytes"],
+                       "response_bytes": x_host.numel() * 8}
+                if keep_solution:
+                    out["x"] = x_host.numpy().reshape(R, N)
+                return out
             finally:
                 plan.close()
 
