@@ -264,6 +264,36 @@ struct CorrInputs {
 // Returns nnz; fills P->corr_ptr / corr_col / corr_val.
 int64_t build_correction(hfmm_plan* P, const CorrInputs& in, cudaStream_t st);
 
+// ---------------------------------------------------------------- octree on the device
+// Morton keys (20 bits per axis) of the user-order points x (N x 3) in the cube
+// [lo, lo + 2^20 / scale)^3, sorted stably: keys_sorted[i], perm[i] = user index.
+void tree_sort_points(const double* x, int64_t N, const double lo[3], double scale, uint64_t* keys_sorted,
+                      int32_t* perm, cudaStream_t st);
+struct LeafData {      // per sorted point i (leaf_ijk per leaf)
+    float4* pts;       // k (x - leaf centre)
+    float* wscale;     // k w / (4 pi)
+    int32_t* pt_leaf;  // leaf index
+    int4* pt_ijk;      // integer leaf coordinates at the leaf level
+    double* x64s;      // sorted FP64 points (N x 3)
+    double* w64s;      // sorted FP64 weights
+    int32_t* tri_s;    // triangle of the point
+    int32_t* iperm;    // user -> sorted (written at iperm[perm[i]])
+    int4* leaf_ijk;    // integer coordinates of each leaf
+};
+void tree_leaf_data(const double* x, const double* w, const int32_t* tri, const int32_t* perm, const uint64_t* leaf_key,
+                    const int32_t* leaf_start, int64_t nleaf, int64_t N, const double lo[3], double side, double k,
+                    const LeafData& out, cudaStream_t st);
+// 27-box neighbour lists of the leaves (self included, order dx, dy, dz); also returns
+// the host copy of the list offsets and each leaf's neighbourhood point count.
+void tree_leaf_neighbours(const uint64_t* leaf_key, const int32_t* leaf_start, int64_t nleaf, int L,
+                          DBuf<int32_t>& nbr_ptr, DBuf<int32_t>& nbr, std::vector<int32_t>& h_ptr,
+                          std::vector<int64_t>& h_hood, size_t* bytes, cudaStream_t st);
+// M2L interaction pairs (source box, target box) of one level with nbox sorted keys,
+// bucketed by offset slot (slot[343] maps an offset in [-3,3]^3 to 0..315): bucket g is
+// pairs[bstart[g] .. bstart[g+1]), targets ascending.  Returns the pair count.
+int64_t tree_m2l_lists(const uint64_t* key, int64_t nbox, int l, const int16_t* slot, std::vector<int2>& pairs,
+                       std::vector<int64_t>& bstart, cudaStream_t st);
+
 // ---------------------------------------------------------------- tensor-core M2L
 size_t m2l_tc_op_elems();  // BF16 elements per packed operator (hi + lo)
 int m2l_tc_max_group();    // work items per tensor-core block

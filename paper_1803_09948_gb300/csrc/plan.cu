@@ -3,6 +3,9 @@
 // A plan holds, on the device: Morton-sorted points and weights, the uniform
 // octree (leaves, neighbour lists, interaction lists grouped by translation
 // offset), all translation operators, and the sparse self/near correction.
+// The sort, the per-point leaf data, the neighbour and interaction lists, the
+// operators and the correction are built by device kernels; the host keeps the
+// per-level box tables and turns the lists into work items.
 // Sec. 2.2 (discretisation, singular treatment), Sec. 2.3 (octree, sweeps),
 // Sec. 3.1-3.2 (Morton order, cell = index + count).
 #include <algorithm>
@@ -21,33 +24,6 @@ using namespace hfmm;
 static thread_local std::string g_last_error;
 
 void hfmm_set_last_error(const std::string& msg) { g_last_error = msg; }
-
-static inline uint64_t spread3_h(uint64_t v) {
-    v &= 0x1fffff;
-    v = (v | v << 32) & 0x1f00000000ffffull;
-    v = (v | v << 16) & 0x1f0000ff0000ffull;
-    v = (v | v << 8) & 0x100f00f00f00f00full;
-    v = (v | v << 4) & 0x10c30c30c30c30c3ull;
-    v = (v | v << 2) & 0x1249249249249249ull;
-    return v;
-}
-static inline uint64_t morton_h(uint64_t x, uint64_t y, uint64_t z) {
-    return (spread3_h(x) << 2) | (spread3_h(y) << 1) | spread3_h(z);
-}
-static inline uint64_t compact3_h(uint64_t v) {
-    v &= 0x1249249249249249ull;
-    v = (v ^ (v >> 2)) & 0x10c30c30c30c30c3ull;
-    v = (v ^ (v >> 4)) & 0x100f00f00f00f00full;
-    v = (v ^ (v >> 8)) & 0x1f0000ff0000ffull;
-    v = (v ^ (v >> 16)) & 0x1f00000000ffffull;
-    v = (v ^ (v >> 32)) & 0x1fffff;
-    return v;
-}
-static inline void demorton_h(uint64_t k, int64_t* c) {
-    c[0] = (int64_t)compact3_h(k >> 2);
-    c[1] = (int64_t)compact3_h(k >> 1);
-    c[2] = (int64_t)compact3_h(k);
-}
 
 static int64_t find_sorted(const std::vector<uint64_t>& keys, uint64_t key) {
     auto it = std::lower_bound(keys.begin(), keys.end(), key);
@@ -85,23 +61,36 @@ struct HostLevel {
     std::vector<int32_t> start;  // nbox + 1
 };
 
+// (source, destination) column pairs grouped by operator: bucket g is
+// pairs[start[g] .. start[g + 1])
 struct PairBuckets {
-    std::vector<std::vector<int2>> b;
-    explicit PairBuckets(int n) : b(n) {}
+    std::vector<int2> pairs;
+    std::vector<int64_t> start;
+    int64_t size(size_t g) const { return start[g + 1] - start[g]; }
+    static PairBuckets from(const std::vector<std::vector<int2>>& b) {
+        PairBuckets pb;
+        pb.start.assign(b.size() + 1, 0);
+        for (size_t g = 0; g < b.size(); ++g) {
+            pb.pairs.insert(pb.pairs.end(), b[g].begin(), b[g].end());
+            pb.start[g + 1] = (int64_t)pb.pairs.size();
+        }
+        return pb;
+    }
 };
 
 void emit_items(const PairBuckets& pb, const std::vector<int64_t>& op_of_bucket, int64_t src, int64_t dst, int pin,
                 int pout, int atomic, std::vector<TransItem>& items, std::vector<int2>& cols,
                 int width = HFMM_TRANS_NB) {
-    for (size_t g = 0; g < pb.b.size(); ++g) {
-        const auto& v = pb.b[g];
-        for (size_t c0 = 0; c0 < v.size(); c0 += width) {
+    for (size_t g = 0; g + 1 < pb.start.size(); ++g) {
+        const int2* v = pb.pairs.data() + pb.start[g];
+        const int64_t nv = pb.size(g);
+        for (int64_t c0 = 0; c0 < nv; c0 += width) {
             TransItem it{};
             it.op = op_of_bucket[g];
             it.src = src;
             it.dst = dst;
             it.cols = (int32_t)cols.size();
-            it.ncol = (int16_t)std::min<size_t>(width, v.size() - c0);
+            it.ncol = (int16_t)std::min<int64_t>(width, nv - c0);
             it.pin = (int16_t)pin;
             it.pout = (int16_t)pout;
             it.atomic = (int16_t)atomic;
@@ -170,24 +159,25 @@ static void build_plan(hfmm_plan* P, const double* V, int64_t nv, const int32_t*
     for (int d = 0; d < 3; ++d) P->lo[d] = 0.5 * (mn[d] + mx[d]) - 0.5 * D;
     const int LMAX = 20;
     const double scale20 = std::ldexp(1.0, LMAX) / D;
-    std::vector<std::pair<uint64_t, int32_t>> kv(N);
-    for (int64_t i = 0; i < N; ++i) {
-        uint64_t c[3];
-        for (int d = 0; d < 3; ++d) {
-            int64_t q = (int64_t)std::floor((X[3 * i + d] - P->lo[d]) * scale20);
-            q = std::max<int64_t>(0, std::min<int64_t>(q, ((int64_t)1 << LMAX) - 1));
-            c[d] = (uint64_t)q;
-        }
-        kv[i] = {morton_h(c[0], c[1], c[2]), (int32_t)i};
-    }
-    std::sort(kv.begin(), kv.end());
+    size_t* cnt = &P->dev_bytes;
+    // Morton keys and their stable sort on the device; the sorted keys come back for
+    // the level tables (a few bytes per box), the permutation stays on the device
+    P->x64.upload(X, cnt, st);
+    DBuf<uint64_t> d_keys;
+    d_keys.alloc(N, nullptr);
+    P->perm.alloc(N, cnt);
+    tree_sort_points(P->x64.p, N, P->lo, scale20, d_keys.p, P->perm.p, st);
+    std::vector<uint64_t> skeys(N);
+    HFMM_CUDA(cudaMemcpyAsync(skeys.data(), d_keys.p, sizeof(uint64_t) * N, cudaMemcpyDeviceToHost, st));
+    HFMM_CUDA(cudaStreamSynchronize(st));
+    d_keys.release();
     int L = cfg.depth;
     if (L <= 0) {
         for (L = 0; L < LMAX; ++L) {
             int sh = 3 * (LMAX - L);
             int64_t run = 0, best = 0;
             for (int64_t i = 0; i < N; ++i) {
-                run = (i > 0 && (kv[i].first >> sh) == (kv[i - 1].first >> sh)) ? run + 1 : 1;
+                run = (i > 0 && (skeys[i] >> sh) == (skeys[i - 1] >> sh)) ? run + 1 : 1;
                 best = std::max(best, run);
             }
             if (best <= cfg.leaf_max) break;
@@ -199,8 +189,8 @@ static void build_plan(hfmm_plan* P, const double* V, int64_t nv, const int32_t*
     for (int l = 0; l <= L; ++l) {
         int sh = 3 * (LMAX - l);
         for (int64_t i = 0; i < N; ++i) {
-            uint64_t key = kv[i].first >> sh;
-            if (i == 0 || key != (kv[i - 1].first >> sh)) {
+            uint64_t key = skeys[i] >> sh;
+            if (i == 0 || key != (skeys[i - 1] >> sh)) {
                 lv[l].key.push_back(key);
                 lv[l].start.push_back((int32_t)i);
             }
@@ -216,89 +206,51 @@ static void build_plan(hfmm_plan* P, const double* V, int64_t nv, const int32_t*
         P->lev[l].s = std::min(1.0, k * 0.5 * std::sqrt(3.0) * P->lev[l].side);
     }
     // ---------------------------------------------------------- sorted point data
-    std::vector<int32_t> perm(N), iperm(N), pt_leaf(N);
-    for (int64_t i = 0; i < N; ++i) {
-        perm[i] = kv[i].second;
-        iperm[kv[i].second] = (int32_t)i;
-    }
     const HostLevel& leaves = lv[L];
     int64_t nleaf = (int64_t)leaves.key.size();
     P->nleaf = nleaf;
     const double sideL = P->lev[L].side;
-    std::vector<float4> pts(N);
-    std::vector<float> wscale(N);
-    std::vector<int4> leaf_ijk(nleaf), pt_ijk(N);
-    std::vector<double> x64s(3 * N), w64s(N);
-    std::vector<int32_t> tri_s(N);
-    const double kPi = 3.14159265358979323846;
-    for (int64_t b = 0; b < nleaf; ++b) {
-        int64_t c[3];
-        demorton_h(leaves.key[b], c);
-        leaf_ijk[b] = make_int4((int)c[0], (int)c[1], (int)c[2], 0);
-        double ctr[3];
-        for (int d = 0; d < 3; ++d) ctr[d] = P->lo[d] + ((double)c[d] + 0.5) * sideL;
-        for (int32_t i = leaves.start[b]; i < leaves.start[b + 1]; ++i) {
-            int32_t u = perm[i];
-            pts[i] = make_float4((float)(k * (X[3 * u] - ctr[0])), (float)(k * (X[3 * u + 1] - ctr[1])),
-                                 (float)(k * (X[3 * u + 2] - ctr[2])), 0.f);
-            wscale[i] = (float)(k * W[u] / (4.0 * kPi));
-            pt_leaf[i] = (int32_t)b;
-            pt_ijk[i] = leaf_ijk[b];
-            for (int d = 0; d < 3; ++d) x64s[3 * i + d] = X[3 * u + d];
-            w64s[i] = W[u];
-            tri_s[i] = T[u];
-        }
-    }
+    upload_legendre_tables();
+    DBuf<double> d_w, d_x64s, d_w64s, d_V;
+    DBuf<int32_t> d_t, d_tri, d_F, d_sstart;
+    DBuf<uint64_t> d_leafkey, d_skey;
+    DBuf<int4> d_pt_ijk;
+    d_w.upload(W, nullptr, st);
+    d_t.upload(T, nullptr, st);
+    d_leafkey.upload(leaves.key, nullptr, st);
+    P->leaf_start.upload(leaves.start, cnt, st);
+    P->pts.alloc(N, cnt);
+    P->iperm.alloc(N, cnt);
+    P->wscale.alloc(N, cnt);
+    P->pt_leaf.alloc(N, cnt);
+    P->leaf_ijk.alloc(nleaf, cnt);
+    d_x64s.alloc(3 * N, nullptr);
+    d_w64s.alloc(N, nullptr);
+    d_tri.alloc(N, nullptr);
+    d_pt_ijk.alloc(N, nullptr);
+    LeafData ld{P->pts.p, P->wscale.p, P->pt_leaf.p, d_pt_ijk.p, d_x64s.p, d_w64s.p, d_tri.p, P->iperm.p, P->leaf_ijk.p};
+    tree_leaf_data(P->x64.p, d_w.p, d_t.p, P->perm.p, d_leafkey.p, P->leaf_start.p, nleaf, N, P->lo, sideL, k, ld, st);
     // neighbour lists (27 boxes, self included) and target tiles
-    std::vector<int32_t> nbr_ptr(nleaf + 1, 0), nbr;
+    std::vector<int32_t> nbr_ptr;
+    std::vector<int64_t> hood;
+    tree_leaf_neighbours(d_leafkey.p, P->leaf_start.p, nleaf, L, P->nbr_ptr, P->nbr, nbr_ptr, hood, cnt, st);
     std::vector<int4> tiles;
-    int64_t nl = (int64_t)1 << L;
-    for (int64_t b = 0; b < nleaf; ++b) {
-        int4 c = leaf_ijk[b];
-        for (int dx = -1; dx <= 1; ++dx)
-            for (int dy = -1; dy <= 1; ++dy)
-                for (int dz = -1; dz <= 1; ++dz) {
-                    int64_t x = c.x + dx, y = c.y + dy, z = c.z + dz;
-                    if (x < 0 || y < 0 || z < 0 || x >= nl || y >= nl || z >= nl) continue;
-                    int64_t s = find_sorted(leaves.key, morton_h(x, y, z));
-                    if (s >= 0) nbr.push_back((int32_t)s);
-                }
-        nbr_ptr[b + 1] = (int32_t)nbr.size();
+    for (int64_t b = 0; b < nleaf; ++b)
         for (int32_t i0 = leaves.start[b]; i0 < leaves.start[b + 1]; i0 += kP2PTile)
             tiles.push_back(make_int4((int)b, i0, std::min(kP2PTile, leaves.start[b + 1] - i0), 0));
-    }
     P->ntiles = (int64_t)tiles.size();
     double pairs = 0.0;
-    for (int64_t b = 0; b < nleaf; ++b) {
-        double nt_b = leaves.start[b + 1] - leaves.start[b];
-        for (int32_t q = nbr_ptr[b]; q < nbr_ptr[b + 1]; ++q)
-            pairs += nt_b * (double)(leaves.start[nbr[q] + 1] - leaves.start[nbr[q]]);
-    }
-    P->cost[0] = pairs - (double)N;
     int64_t cap = 0;
     for (int64_t b = 0; b < nleaf; ++b) {
-        int64_t tot = 0;
-        for (int32_t q = nbr_ptr[b]; q < nbr_ptr[b + 1]; ++q)
-            tot += leaves.start[nbr[q] + 1] - leaves.start[nbr[q]];
-        cap = std::max(cap, tot);
+        pairs += (double)(leaves.start[b + 1] - leaves.start[b]) * (double)hood[b];
+        cap = std::max(cap, hood[b]);
     }
+    P->cost[0] = pairs - (double)N;
     P->p2p_cap = (int)std::min<int64_t>(cap, 1 << 30);
     P->cost[4] = (double)N;
     P->p2p_shift = (float)(k * sideL);
     P->poly_p2p = 12.0 * (k * sideL) * (k * sideL) * 1.001 <= (double)HFMM_POLY_UMAX;
 
-    size_t* cnt = &P->dev_bytes;
-    upload_legendre_tables();
-    P->pts.upload(pts, cnt, st);
-    P->perm.upload(perm, cnt, st);
-    P->iperm.upload(iperm, cnt, st);
-    P->wscale.upload(wscale, cnt, st);
-    P->pt_leaf.upload(pt_leaf, cnt, st);
-    P->x64.upload(X, cnt, st);
-    P->leaf_start.upload(leaves.start, cnt, st);
-    P->leaf_ijk.upload(leaf_ijk, cnt, st);
-    P->nbr_ptr.upload(nbr_ptr, cnt, st);
-    P->nbr.upload(nbr, cnt, st);
     P->tiles.upload(tiles, cnt, st);
     P->sig.alloc(N, cnt);
     P->phi.alloc(N, cnt);
@@ -429,12 +381,13 @@ static void build_plan(hfmm_plan* P, const double* V, int64_t nv, const int32_t*
         std::vector<TransItem> items;
         std::vector<int2> cols;
         for (int l = L - 1; l >= 2; --l) {  // M2M: children at l+1 -> parents at l
-            PairBuckets pb(8);
+            std::vector<std::vector<int2>> b8(8);
             const HostLevel& ch = lv[l + 1];
             for (int64_t c = 0; c < (int64_t)ch.key.size(); ++c) {
                 int64_t par = find_sorted(lv[l].key, ch.key[c] >> 3);
-                pb.b[ch.key[c] & 7].push_back(make_int2((int)c, (int)par));
+                b8[ch.key[c] & 7].push_back(make_int2((int)c, (int)par));
             }
+            const PairBuckets pb = PairBuckets::from(b8);
             std::vector<int64_t> ops(8);
             for (int o = 0; o < 8; ++o) ops[o] = P->lev[l + 1].m2m_op + (int64_t)o * P->lev[l].P * P->lev[l + 1].P;
             P->m2m_items_begin[l] = (int64_t)items.size();
@@ -447,43 +400,29 @@ static void build_plan(hfmm_plan* P, const double* V, int64_t nv, const int32_t*
         std::vector<int64_t> lev_item_b(L + 1, 0), lev_item_e(L + 1, 0);
         std::vector<int> lev_width(L + 1, HFMM_TRANS_NB);
         std::vector<int64_t> lev_pairs(L + 1, 0);
+        std::vector<int16_t> slot16(slot, slot + 343);
+        DBuf<int16_t> d_slot;
+        d_slot.upload(slot16, nullptr, st);
         for (int l = 2; l <= L; ++l) {
             lev_item_b[l] = (int64_t)items.size();
-            PairBuckets pb(316);
-            const HostLevel& H = lv[l];
-            int64_t nlv = (int64_t)1 << l;
-            for (int64_t t = 0; t < (int64_t)H.key.size(); ++t) {
-                int64_t c[3];
-                demorton_h(H.key[t], c);
-                int64_t px = c[0] >> 1, py = c[1] >> 1, pz = c[2] >> 1;
-                for (int ex = -1; ex <= 1; ++ex)
-                    for (int ey = -1; ey <= 1; ++ey)
-                        for (int ez = -1; ez <= 1; ++ez) {
-                            int64_t qx = px + ex, qy = py + ey, qz = pz + ez;
-                            if (qx < 0 || qy < 0 || qz < 0 || 2 * qx >= nlv || 2 * qy >= nlv || 2 * qz >= nlv) continue;
-                            for (int o = 0; o < 8; ++o) {
-                                int64_t sx = 2 * qx + ((o >> 2) & 1), sy = 2 * qy + ((o >> 1) & 1), sz = 2 * qz + (o & 1);
-                                int64_t dx = sx - c[0], dy = sy - c[1], dz = sz - c[2];
-                                if (std::llabs(dx) <= 1 && std::llabs(dy) <= 1 && std::llabs(dz) <= 1) continue;
-                                int64_t s = find_sorted(H.key, morton_h(sx, sy, sz));
-                                if (s < 0) continue;
-                                int sl = slot[(dx + 3) * 49 + (dy + 3) * 7 + (dz + 3)];
-                                pb.b[sl].push_back(make_int2((int)s, (int)t));
-                                ++m2l_count;
-                                ++lev_pairs[l];
-                                P->cost[1] += (double)P->lev[l].P * P->lev[l].P;
-                            }
-                        }
-            }
+            // interaction lists (children of the parent's neighbours that are not
+            // neighbours), built on the device and bucketed by offset slot
+            PairBuckets pb;
+            DBuf<uint64_t> d_lkey;
+            d_lkey.upload(lv[l].key, nullptr, st);
+            const int64_t npair = tree_m2l_lists(d_lkey.p, (int64_t)lv[l].key.size(), l, d_slot.p, pb.pairs, pb.start, st);
+            m2l_count += npair;
+            lev_pairs[l] = npair;
+            P->cost[1] += (double)npair * P->lev[l].P * P->lev[l].P;
             std::vector<int64_t> ops(316);
             for (int o = 0; o < 316; ++o) ops[o] = P->lev[l].m2l_op + (int64_t)o * P->lev[l].P * P->lev[l].P;
             // SIMT levels with few targets per offset (the coarse ones) take narrow items
             int width = HFMM_TRANS_NB;
             if (!(cfg.m2l_tensor && P->lev[l].P <= 64)) {
                 int64_t busy = 0, pairs = 0;
-                for (const auto& v : pb.b) {
-                    busy += !v.empty();
-                    pairs += (int64_t)v.size();
+                for (size_t g = 0; g + 1 < pb.start.size(); ++g) {
+                    busy += pb.size(g) > 0;
+                    pairs += pb.size(g);
                 }
                 const int64_t mean = busy ? pairs / busy : 0;
                 width = mean <= 12 ? 8 : mean <= 28 ? 16 : HFMM_TRANS_NB;
@@ -495,12 +434,13 @@ static void build_plan(hfmm_plan* P, const double* V, int64_t nv, const int32_t*
         P->m2l_items_end = (int64_t)items.size();
         P->m2l_count = m2l_count;
         for (int l = 3; l <= L; ++l) {  // L2L: parents at l-1 -> children at l
-            PairBuckets pb(8);
+            std::vector<std::vector<int2>> b8(8);
             const HostLevel& ch = lv[l];
             for (int64_t c = 0; c < (int64_t)ch.key.size(); ++c) {
                 int64_t par = find_sorted(lv[l - 1].key, ch.key[c] >> 3);
-                pb.b[ch.key[c] & 7].push_back(make_int2((int)par, (int)c));
+                b8[ch.key[c] & 7].push_back(make_int2((int)par, (int)c));
             }
+            const PairBuckets pb = PairBuckets::from(b8);
             std::vector<int64_t> ops(8);
             for (int o = 0; o < 8; ++o) ops[o] = P->lev[l].pc_op + (int64_t)o * P->lev[l].P * P->lev[l - 1].P;
             P->l2l_items_begin[l] = (int64_t)items.size();
@@ -604,20 +544,12 @@ static void build_plan(hfmm_plan* P, const double* V, int64_t nv, const int32_t*
     int ls = L;
     while (ls > 0 && P->lev[ls].side < P->r_near) --ls;
     const HostLevel& S = lv[ls];
-    DBuf<double> d_x64s, d_w64s, d_V;
-    DBuf<int32_t> d_tri, d_F, d_sstart;
-    DBuf<uint64_t> d_skey;
-    DBuf<int4> d_pt_ijk;
-    d_x64s.upload(x64s, nullptr, st);
-    d_w64s.upload(w64s, nullptr, st);
     std::vector<double> Vh(V, V + 3 * nv);
     std::vector<int32_t> Fh(F, F + 3 * nt);
     d_V.upload(Vh, nullptr, st);
     d_F.upload(Fh, nullptr, st);
-    d_tri.upload(tri_s, nullptr, st);
     d_skey.upload(S.key, nullptr, st);
     d_sstart.upload(S.start, nullptr, st);
-    d_pt_ijk.upload(pt_ijk, nullptr, st);
     CorrInputs ci{};
     ci.x64s = d_x64s.p;
     ci.tri_s = d_tri.p;
