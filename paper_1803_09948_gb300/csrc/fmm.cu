@@ -524,6 +524,177 @@ __global__ void __launch_bounds__(128) k_l2p(int64_t N, const int32_t* __restric
     phi[i] = make_float2(o.x + accr, o.y + acci);
 }
 
+// ============================================================== P2M / L2P at fixed order
+// The leaf level's order is usually small (p <= 8, P <= 81): with p a template
+// parameter every loop unrolls and the radial functions stay in registers.
+constexpr int kFixedPMax = 8;
+
+// jt_n(k r) / s^n, n = 0..PP, into registers
+template <int PP>
+__device__ __forceinline__ void jn_fixed(float x, float s, float (&jr)[PP + 1]) {
+    if (x < 2.0f) {
+#pragma unroll
+        for (int n = 0; n <= PP; ++n) jr[n] = f_jn_series(n, x, s);
+    } else {  // large leaves at high frequency: the downward recurrence
+        float t[HFMM_PMAX + 1];
+        f_jn_scaled(PP, x, s, t);
+#pragma unroll
+        for (int n = 0; n <= PP; ++n) jr[n] = t[n];
+    }
+}
+
+// P2M, one warp per leaf (four leaves per block), the leaf's points in chunks of 32:
+//   lane j builds the basis of point j: jt_n Q_n^m (m >= 0) into column j of Bs and
+//   sh e^{-/+ i m phi} into column j of Es (row stride 33: lanes that read different
+//   rows at one point hit different banks);
+//   lane c then accumulates coefficients c, c + 32, ... over the chunk.
+template <int PP>
+__global__ void __launch_bounds__(128) k_p2m_w(int64_t nleaf, const int32_t* __restrict__ leaf_start,
+                                               const float4* __restrict__ pts, const float2* __restrict__ sig,
+                                               float s, float2* __restrict__ M) {
+    constexpr int P = (PP + 1) * (PP + 1), H = (PP + 1) * (PP + 2) / 2, NE = 2 * (PP + 1);
+    constexpr int NC = (P + 31) / 32;
+    __shared__ float Bs[4][H][33];
+    __shared__ float2 Es[4][NE][33];
+    const int wb = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t leaf = (int64_t)blockIdx.x * 4 + wb;
+    if (leaf >= nleaf) return;  // warps are independent: no block-wide barrier below
+    const int32_t b0 = leaf_start[leaf], b1 = leaf_start[leaf + 1];
+    int hh[NC], ee[NC];
+    float accr[NC], acci[NC];
+#pragma unroll
+    for (int q = 0; q < NC; ++q) {
+        const int c = min(lane + 32 * q, P - 1);
+        int n = 0;
+        while ((n + 1) * (n + 1) <= c) ++n;
+        const int m = c - n * n - n, am = m < 0 ? -m : m;
+        hh[q] = n * (n + 1) / 2 + am;
+        ee[q] = m < 0 ? PP + 1 + am : am;
+        accr[q] = acci[q] = 0.f;
+    }
+    for (int32_t j0 = b0; j0 < b1; j0 += 32) {
+        const int cnt = min(32, b1 - j0);
+        if (lane < cnt) {
+            const float4 y = pts[j0 + lane];
+            const float2 sg = sig[j0 + lane];
+            const Dir d = make_dir(y.x, y.y, y.z);
+            float jr[PP + 1];
+            jn_fixed<PP>(d.r, s, jr);
+            float stp = 1.f, er = 1.f, ei = 0.f;
+#pragma unroll
+            for (int m = 0; m <= PP; ++m) {
+                if (m > 0) {
+                    stp *= d.st;
+                    const float t = er * d.ex - ei * d.ey;
+                    ei = er * d.ey + ei * d.ex;
+                    er = t;
+                }
+                const float qmm = c_leg_qmm[m] * stp;
+                float qa = qmm, qb = 0.f;
+                Bs[wb][m * (m + 1) / 2 + m][lane] = jr[m] * qmm;
+#pragma unroll
+                for (int n = m + 1; n <= PP; ++n) {
+                    const int h = n * (n + 1) / 2 + m;
+                    const float qn = (n == m + 1) ? c_leg_a[h] * d.ct * qmm : c_leg_a[h] * (d.ct * qa - c_leg_b[h] * qb);
+                    qb = qa;
+                    qa = qn;
+                    Bs[wb][h][lane] = jr[n] * qn;
+                }
+                Es[wb][m][lane] = make_float2(sg.x * er + sg.y * ei, sg.y * er - sg.x * ei);           // sh e^{-i m phi}
+                Es[wb][PP + 1 + m][lane] = make_float2(sg.x * er - sg.y * ei, sg.y * er + sg.x * ei);  // sh e^{+i m phi}
+            }
+        }
+        __syncwarp();
+#pragma unroll
+        for (int q = 0; q < NC; ++q)
+            for (int t = 0; t < cnt; ++t) {
+                const float b = Bs[wb][hh[q]][t];
+                const float2 e = Es[wb][ee[q]][t];
+                accr[q] = fmaf(b, e.x, accr[q]);
+                acci[q] = fmaf(b, e.y, acci[q]);
+            }
+        __syncwarp();
+    }
+#pragma unroll
+    for (int q = 0; q < NC; ++q)
+        if (lane + 32 * q < P) M[leaf * P + lane + 32 * q] = make_float2(accr[q], acci[q]);
+}
+
+// L2P, one thread per point: phi += sum_nm L_nm jt_n(k r) Y_nm
+template <int PP>
+__global__ void __launch_bounds__(128) k_l2p_t(int64_t N, const int32_t* __restrict__ pt_leaf,
+                                               const float4* __restrict__ pts, float s, const float2* __restrict__ Lc,
+                                               float2* __restrict__ phi) {
+    constexpr int P = (PP + 1) * (PP + 1);
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const float2* L = Lc + (int64_t)pt_leaf[i] * P;
+    const float4 y = pts[i];
+    const Dir d = make_dir(y.x, y.y, y.z);
+    float jr[PP + 1];
+    jn_fixed<PP>(d.r, s, jr);
+    float accr = 0.f, acci = 0.f;
+    float stp = 1.f, er = 1.f, ei = 0.f;
+#pragma unroll
+    for (int m = 0; m <= PP; ++m) {
+        if (m > 0) {
+            stp *= d.st;
+            const float t = er * d.ex - ei * d.ey;
+            ei = er * d.ey + ei * d.ex;
+            er = t;
+        }
+        const float qmm = c_leg_qmm[m] * stp;
+        float qa = qmm, qb = 0.f;
+#pragma unroll
+        for (int n = m; n <= PP; ++n) {
+            float qn = qmm;
+            if (n > m) {
+                const int h = n * (n + 1) / 2 + m;
+                qn = (n == m + 1) ? c_leg_a[h] * d.ct * qmm : c_leg_a[h] * (d.ct * qa - c_leg_b[h] * qb);
+                qb = qa;
+                qa = qn;
+            }
+            const float bq = jr[n] * qn;
+            const float2 lp = __ldg(L + n * n + n + m);
+            // L_{n,m} b e^{+i m phi}
+            accr += bq * (lp.x * er - lp.y * ei);
+            acci += bq * (lp.x * ei + lp.y * er);
+            if (m > 0) {
+                const float2 lm = __ldg(L + n * n + n - m);
+                accr += bq * (lm.x * er + lm.y * ei);
+                acci += bq * (lm.y * er - lm.x * ei);
+            }
+        }
+    }
+    const float2 o = phi[i];
+    phi[i] = make_float2(o.x + accr, o.y + acci);
+}
+
+template <int PP>
+static void launch_p2m_l2p_fixed(bool p2m, const hfmm_plan* P, const LevelInfo& lv, cudaStream_t st) {
+    if (p2m)
+        k_p2m_w<PP><<<(unsigned)((P->nleaf + 3) / 4), 128, 0, st>>>(P->nleaf, P->leaf_start.p, P->pts.p, P->sig.p,
+                                                                    (float)lv.s, P->coef.p + lv.mofs);
+    else
+        k_l2p_t<PP><<<(unsigned)((P->N + 127) / 128), 128, 0, st>>>(P->N, P->pt_leaf.p, P->pts.p, (float)lv.s,
+                                                                    P->coef.p + lv.lofs, P->phi.p);
+}
+
+// P2M (p2m = true) or L2P at the leaf level at its fixed order; false if p > kFixedPMax
+static bool p2m_l2p_fixed(bool p2m, const hfmm_plan* P, const LevelInfo& lv, cudaStream_t st) {
+    switch (lv.p) {
+        case 1: launch_p2m_l2p_fixed<1>(p2m, P, lv, st); return true;
+        case 2: launch_p2m_l2p_fixed<2>(p2m, P, lv, st); return true;
+        case 3: launch_p2m_l2p_fixed<3>(p2m, P, lv, st); return true;
+        case 4: launch_p2m_l2p_fixed<4>(p2m, P, lv, st); return true;
+        case 5: launch_p2m_l2p_fixed<5>(p2m, P, lv, st); return true;
+        case 6: launch_p2m_l2p_fixed<6>(p2m, P, lv, st); return true;
+        case 7: launch_p2m_l2p_fixed<7>(p2m, P, lv, st); return true;
+        case 8: launch_p2m_l2p_fixed<8>(p2m, P, lv, st); return true;
+        default: return false;
+    }
+}
+
 // ============================================================== batched translations
 // Out[:, dst] += T * In[:, src] for the column pairs of one work item.
 // 128 threads; a block computes one output tile of 4 * (128 / CG) rows x 4 * CG
@@ -819,11 +990,13 @@ void run_matvec_sorted(hfmm_plan* P, int parts, cudaStream_t st) {
         // multipoles above the leaves and all locals accumulate: clear them
         HFMM_CUDA(cudaMemsetAsync(P->coef.p, 0, sizeof(float2) * P->coef_total, st));
         const LevelInfo& lv = P->lev[L];
-        const size_t smem = p2m_smem_bytes(lv.p);
-        if (smem > 48 * 1024)
-            HFMM_CUDA(cudaFuncSetAttribute(k_p2m, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        k_p2m<<<(unsigned)P->nleaf, 128, smem, st>>>(P->leaf_start.p, P->pts.p, P->sig.p, lv.p, (float)lv.s,
-                                                       P->coef.p + lv.mofs);
+        if (!p2m_l2p_fixed(true, P, lv, st)) {
+            const size_t smem = p2m_smem_bytes(lv.p);
+            if (smem > 48 * 1024)
+                HFMM_CUDA(cudaFuncSetAttribute(k_p2m, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            k_p2m<<<(unsigned)P->nleaf, 128, smem, st>>>(P->leaf_start.p, P->pts.p, P->sig.p, lv.p, (float)lv.s,
+                                                           P->coef.p + lv.mofs);
+        }
         ++P->launches;
     }
     mark_stage(P, 3, st);
@@ -868,8 +1041,9 @@ void run_matvec_sorted(hfmm_plan* P, int parts, cudaStream_t st) {
     mark_stage(P, 7, st);
     if (far) {
         const LevelInfo& lv = P->lev[L];
-        k_l2p<<<(unsigned)((N + 127) / 128), 128, 0, st>>>(N, P->pt_leaf.p, P->pts.p, lv.p, (float)lv.s,
-                                                           P->coef.p + lv.lofs, P->phi.p);
+        if (!p2m_l2p_fixed(false, P, lv, st))
+            k_l2p<<<(unsigned)((N + 127) / 128), 128, 0, st>>>(N, P->pt_leaf.p, P->pts.p, lv.p, (float)lv.s,
+                                                               P->coef.p + lv.lofs, P->phi.p);
         ++P->launches;
     }
     mark_stage(P, 8, st);
