@@ -243,6 +243,14 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         S.abort = 0;
     }
+    // the operator rows (epilogue warps: thread r holds row r, hi then lo) are requested
+    // first, so that their latency overlaps the item-list loads below
+    uint4 arow[16];
+    const uint4* asrc = reinterpret_cast<const uint4*>(aops + (int64_t)g.z * 2 * kM * kK) + (size_t)(tid & 127) * (kK / 8);
+    if (warp < 4) {
+#pragma unroll
+        for (int q = 0; q < 16; ++q) arow[q] = __ldg(asrc + q);
+    }
     {
         // the group's work items and column lists: one coalesced pass instead of a
         // dependent load per item later
@@ -271,21 +279,22 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (warp < 4) {
         // the group's operator into tensor memory: thread r writes row r (its lane),
         // hi into columns 0..63 and lo into 64..127, two BF16 per column
-        const uint4* src = reinterpret_cast<const uint4*>(aops + (int64_t)g.z * 2 * kM * kK);
         const uint32_t lane_base = S.tmem + ((uint32_t)(warp * 32) << 16);
 #pragma unroll 1
         for (int part = 0; part < 2; ++part) {
-            const uint4* row = src + (size_t)part * (kM * kK / 8) + (size_t)tid * (kK / 8);
-#pragma unroll 1
+            if (part == 1) {
+#pragma unroll
+                for (int q = 0; q < 16; ++q) arow[q] = __ldg(asrc + (kM * kK / 8) + q);
+            }
+#pragma unroll
             for (int cb = 0; cb < 4; ++cb) {
                 uint32_t v[16];
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
-                    const uint4 x = __ldg(row + 4 * cb + q);
-                    v[4 * q] = x.x;
-                    v[4 * q + 1] = x.y;
-                    v[4 * q + 2] = x.z;
-                    v[4 * q + 3] = x.w;
+                    v[4 * q] = arow[4 * cb + q].x;
+                    v[4 * q + 1] = arow[4 * cb + q].y;
+                    v[4 * q + 2] = arow[4 * cb + q].z;
+                    v[4 * q + 3] = arow[4 * cb + q].w;
                 }
                 tmem_st16(lane_base + (uint32_t)(part * 64 + cb * 16), v);
             }
