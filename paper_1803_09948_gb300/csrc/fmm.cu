@@ -9,6 +9,7 @@
 //   output         potential[perm(i)] = phi_i
 #include <algorithm>
 #include <cmath>
+#include <type_traits>
 
 #include "hfmm_internal.cuh"
 #include "kernel_poly.h"
@@ -1078,12 +1079,22 @@ constexpr int kBMaxP = 128;  // leaf expansion size the batched P2M / L2P kernel
 
 // Regular basis b_c(y) = jt_n(r) Q_n^|m|(cos t) e^{i m phi}, c = n^2 + n + m, of a point y
 // relative to its leaf centre (scaled by k):  L2P is sum_c L_c b_c,  P2M is sum_j s_j conj(b_c(y_j)).
+// PP >= 0: the order as a compile-time constant (p is then PP), loops unrolled and the
+// radial functions in registers; PP < 0: any order p
+template <int PP>
 __device__ void regular_basis(float4 y, int p, float s, float2* out) {
     const Dir d = make_dir(y.x, y.y, y.z);
-    float jr[HFMM_PMAX + 1];
-    f_jn_scaled(p, d.r, s, jr);
+    constexpr int kJ = PP >= 0 ? PP + 1 : HFMM_PMAX + 1;
+    float jr[kJ];
+    if constexpr (PP >= 0) {
+        p = PP;
+        jn_fixed<PP>(d.r, s, jr);
+    } else {
+        f_jn_scaled(p, d.r, s, jr);
+    }
     float stp = 1.f, er = 1.f, ei = 0.f;
-    for (int m = 0; m <= p; ++m) {
+#pragma unroll
+    for (int m = 0; m <= (PP >= 0 ? PP : p); ++m) {
         if (m > 0) {
             stp *= d.st;
             const float t = er * d.ex - ei * d.ey;
@@ -1092,7 +1103,8 @@ __device__ void regular_basis(float4 y, int p, float s, float2* out) {
         }
         const float qmm = c_leg_qmm[m] * stp;
         float qa = qmm, qb = 0.f;
-        for (int n = m; n <= p; ++n) {
+#pragma unroll
+        for (int n = m; n <= (PP >= 0 ? PP : p); ++n) {
             float qn = qmm;
             if (n > m) {
                 const int h = n * (n + 1) / 2 + m;
@@ -1284,6 +1296,7 @@ static size_t p2p_b_smem(int cap) {
 
 // M[leaf][r][c] = sum_j conj(b_c(y_j)) sig_b[j][r]; one block per leaf, 16 x 16 threads,
 // 4 coefficients x 4 right-hand sides each, coefficient tiles of 64
+template <int PP>
 __global__ void __launch_bounds__(256) k_p2m_b(const int32_t* __restrict__ leaf_start, const float4* __restrict__ pts,
                                                const float2* __restrict__ sig, int p, float s, int R,
                                                float2* __restrict__ M) {
@@ -1303,7 +1316,7 @@ __global__ void __launch_bounds__(256) k_p2m_b(const int32_t* __restrict__ leaf_
         for (int j0 = b0; j0 < b1; j0 += kBChunk) {
             const int cnt = min(kBChunk, b1 - j0);
             __syncthreads();
-            if (tid < cnt) regular_basis(pts[j0 + tid], p, s, Bs + tid * P);
+            if (tid < cnt) regular_basis<PP>(pts[j0 + tid], p, s, Bs + tid * P);
             for (int e = tid; e < kBChunk * kBMax; e += 256) {
                 const int j = e / kBMax, r = e % kBMax;
                 Ss[e] = (j < cnt && r < R) ? sig[(int64_t)(j0 + j) * R + r] : make_float2(0.f, 0.f);
@@ -1339,14 +1352,33 @@ __global__ void __launch_bounds__(256) k_p2m_b(const int32_t* __restrict__ leaf_
 
 static size_t p2m_b_smem(int P) { return sizeof(float2) * kBChunk * (P + kBMax); }
 
-// phi_b[j][r] += sum_c b_c(y_j) L[leaf][r][c]; one block per leaf; thread (point jj, rhs rg + 8q)
+// f(std::integral_constant<int, PP>) with PP = p for the fixed orders, -1 above them
+template <typename F>
+static void with_leaf_order(int p, F&& f) {
+    switch (p) {
+        case 1: f(std::integral_constant<int, 1>{}); break;
+        case 2: f(std::integral_constant<int, 2>{}); break;
+        case 3: f(std::integral_constant<int, 3>{}); break;
+        case 4: f(std::integral_constant<int, 4>{}); break;
+        case 5: f(std::integral_constant<int, 5>{}); break;
+        case 6: f(std::integral_constant<int, 6>{}); break;
+        case 7: f(std::integral_constant<int, 7>{}); break;
+        case 8: f(std::integral_constant<int, 8>{}); break;
+        default: f(std::integral_constant<int, -1>{}); break;
+    }
+}
+
+// phi_b[j][r] += sum_c b_c(y_j) L[leaf][r][c]; one block per leaf; thread (point jj, rhs rg + 8q).
+// A chunk's sums pass through shared memory (the basis buffer, rows of kBMax + 1) so that
+// the read-modify-write of phi_b runs along r, contiguous in memory.
+template <int PP>
 __global__ void __launch_bounds__(256) k_l2p_b(const int32_t* __restrict__ leaf_start, const float4* __restrict__ pts,
                                                int p, float s, int R, const float2* __restrict__ L,
                                                float2* __restrict__ phi) {
     extern __shared__ float2 smem_l2p[];
     const int P = (p + 1) * (p + 1), Pp = P + 1;
     float2* Ls = smem_l2p;          // [kBMax][P]
-    float2* Bs = Ls + kBMax * P;    // [kBChunk][P + 1]
+    float2* Bs = Ls + kBMax * P;    // [kBChunk][P + 1], then the chunk's sums [kBChunk][kBMax + 1]
     const int leaf = blockIdx.x, tid = threadIdx.x;
     const int b0 = leaf_start[leaf], b1 = leaf_start[leaf + 1];
     for (int e = tid; e < kBMax * P; e += 256)
@@ -1355,33 +1387,39 @@ __global__ void __launch_bounds__(256) k_l2p_b(const int32_t* __restrict__ leaf_
     for (int j0 = b0; j0 < b1; j0 += kBChunk) {
         const int cnt = min(kBChunk, b1 - j0);
         __syncthreads();
-        if (tid < cnt) regular_basis(pts[j0 + tid], p, s, Bs + tid * Pp);
+        if (tid < cnt) regular_basis<PP>(pts[j0 + tid], p, s, Bs + tid * Pp);
         __syncthreads();
-        if (jj >= cnt) continue;
         float2 acc[8];
 #pragma unroll
         for (int q = 0; q < 8; ++q) acc[q] = make_float2(0.f, 0.f);
-        for (int c = 0; c < P; ++c) {
-            const float2 bb = Bs[jj * Pp + c];
+        if (jj < cnt)
+            for (int c = 0; c < P; ++c) {
+                const float2 bb = Bs[jj * Pp + c];
 #pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                const float2 l = Ls[(rg + 8 * q) * P + c];
-                acc[q].x = fmaf(bb.x, l.x, fmaf(-bb.y, l.y, acc[q].x));
-                acc[q].y = fmaf(bb.x, l.y, fmaf(bb.y, l.x, acc[q].y));
+                for (int q = 0; q < 8; ++q) {
+                    const float2 l = Ls[(rg + 8 * q) * P + c];
+                    acc[q].x = fmaf(bb.x, l.x, fmaf(-bb.y, l.y, acc[q].x));
+                    acc[q].y = fmaf(bb.x, l.y, fmaf(bb.y, l.x, acc[q].y));
+                }
             }
-        }
+        __syncthreads();  // the basis is read: its buffer takes the sums
+        float2* Ts = Bs;
+        if (jj < cnt)
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            const int r = rg + 8 * q;
-            if (r >= R) continue;
-            float2* o = phi + (int64_t)(j0 + jj) * R + r;
-            const float2 v = *o;
-            *o = make_float2(v.x + acc[q].x, v.y + acc[q].y);
+            for (int q = 0; q < 8; ++q) Ts[jj * (kBMax + 1) + rg + 8 * q] = acc[q];
+        __syncthreads();
+        for (int e = tid; e < cnt * R; e += 256) {
+            const int j = e / R, r = e % R;
+            float2* o = phi + (int64_t)(j0 + j) * R + r;
+            const float2 v = *o, a = Ts[j * (kBMax + 1) + r];
+            *o = make_float2(v.x + a.x, v.y + a.y);
         }
     }
 }
 
-static size_t l2p_b_smem(int P) { return sizeof(float2) * ((size_t)kBMax * P + (size_t)kBChunk * (P + 1)); }
+static size_t l2p_b_smem(int P) {
+    return sizeof(float2) * ((size_t)kBMax * P + (size_t)kBChunk * (size_t)std::max(P + 1, kBMax + 1));
+}
 
 // phi_b[i][r] += sum_nz C_i,col sig_b[col][r]: one warp per row, lanes on right-hand sides
 __global__ void __launch_bounds__(256) k_corr_b(int64_t N, int R, const int64_t* __restrict__ ptr,
@@ -1545,8 +1583,11 @@ void batch_setup(hfmm_plan* P, int R, cudaStream_t st) {
     HFMM_CUDA(cudaFuncSetAttribute(k_p2p_b<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sp2p));
     if (L >= 2) {
         const int Pl = P->lev[L].P;
-        HFMM_CUDA(cudaFuncSetAttribute(k_p2m_b, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p2m_b_smem(Pl)));
-        HFMM_CUDA(cudaFuncSetAttribute(k_l2p_b, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)l2p_b_smem(Pl)));
+        with_leaf_order(P->lev[L].p, [&](auto pp) {
+            constexpr int PP = decltype(pp)::value;
+            HFMM_CUDA(cudaFuncSetAttribute(k_p2m_b<PP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p2m_b_smem(Pl)));
+            HFMM_CUDA(cudaFuncSetAttribute(k_l2p_b<PP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)l2p_b_smem(Pl)));
+        });
     }
 }
 
@@ -1568,8 +1609,10 @@ void run_matvec_batched(hfmm_plan* P, const float2* density, float2* potential, 
     if (L >= 2) {
         HFMM_CUDA(cudaMemsetAsync(B.coef.p, 0, sizeof(float2) * P->coef_total * R, st));
         const LevelInfo& lv = P->lev[L];
-        k_p2m_b<<<(unsigned)P->nleaf, 256, p2m_b_smem(lv.P), st>>>(P->leaf_start.p, P->pts.p, B.sig.p, lv.p,
-                                                                  (float)lv.s, R, B.coef.p + lv.mofs * R);
+        with_leaf_order(lv.p, [&](auto pp) {
+            k_p2m_b<decltype(pp)::value><<<(unsigned)P->nleaf, 256, p2m_b_smem(lv.P), st>>>(
+                P->leaf_start.p, P->pts.p, B.sig.p, lv.p, (float)lv.s, R, B.coef.p + lv.mofs * R);
+        });
         ++P->launches;
         for (int l = L - 1; l >= 2; --l) {
             const auto& g = B.m2m_tc[l];
@@ -1600,8 +1643,10 @@ void run_matvec_batched(hfmm_plan* P, const float2* density, float2* potential, 
                                  R, st);
             }
         }
-        k_l2p_b<<<(unsigned)P->nleaf, 256, l2p_b_smem(lv.P), st>>>(P->leaf_start.p, P->pts.p, lv.p, (float)lv.s, R,
-                                                                  B.coef.p + lv.lofs * R, B.phi.p);
+        with_leaf_order(lv.p, [&](auto pp) {
+            k_l2p_b<decltype(pp)::value><<<(unsigned)P->nleaf, 256, l2p_b_smem(lv.P), st>>>(
+                P->leaf_start.p, P->pts.p, lv.p, (float)lv.s, R, B.coef.p + lv.lofs * R, B.phi.p);
+        });
         ++P->launches;
     }
     if (P->corr_nnz > 0) {
