@@ -1583,9 +1583,10 @@ void batch_setup(hfmm_plan* P, int R, cudaStream_t st) {
     HFMM_CUDA(cudaFuncSetAttribute(k_p2p_b<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sp2p));
     if (L >= 2) {
         const int Pl = P->lev[L].P;
+        // P2M keeps the any-order basis: with the unrolled one its registers halve the blocks per SM
+        HFMM_CUDA(cudaFuncSetAttribute(k_p2m_b<-1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p2m_b_smem(Pl)));
         with_leaf_order(P->lev[L].p, [&](auto pp) {
             constexpr int PP = decltype(pp)::value;
-            HFMM_CUDA(cudaFuncSetAttribute(k_p2m_b<PP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p2m_b_smem(Pl)));
             HFMM_CUDA(cudaFuncSetAttribute(k_l2p_b<PP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)l2p_b_smem(Pl)));
         });
     }
@@ -1609,10 +1610,8 @@ void run_matvec_batched(hfmm_plan* P, const float2* density, float2* potential, 
     if (L >= 2) {
         HFMM_CUDA(cudaMemsetAsync(B.coef.p, 0, sizeof(float2) * P->coef_total * R, st));
         const LevelInfo& lv = P->lev[L];
-        with_leaf_order(lv.p, [&](auto pp) {
-            k_p2m_b<decltype(pp)::value><<<(unsigned)P->nleaf, 256, p2m_b_smem(lv.P), st>>>(
-                P->leaf_start.p, P->pts.p, B.sig.p, lv.p, (float)lv.s, R, B.coef.p + lv.mofs * R);
-        });
+        k_p2m_b<-1><<<(unsigned)P->nleaf, 256, p2m_b_smem(lv.P), st>>>(P->leaf_start.p, P->pts.p, B.sig.p, lv.p,
+                                                                      (float)lv.s, R, B.coef.p + lv.mofs * R);
         ++P->launches;
         for (int l = L - 1; l >= 2; --l) {
             const auto& g = B.m2m_tc[l];
