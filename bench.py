@@ -117,6 +117,22 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def _max_over_ranks(v, world, device="cuda"):
+    """The largest of v over the ranks of the default process group (v itself on one rank)."""
+    if world <= 1:
+        return float(v)
+    import torch
+
+    t = torch.tensor([float(v)], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _job_rate(units_per_rank, world, max_ms):
+    """Whole-job throughput: the units all ranks processed / the slowest rank's time."""
+    return world * units_per_rank / (max_ms / 1e3)
+
+
 def _dist():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -192,6 +208,8 @@ def run_refine(args):
     import paper_1803_09948_gb300 as pkg
     import synthetic
 
+    if _dist()[1] != 0:  # a single-GPU arm: under torchrun rank 0 runs it, the others exit
+        return
     torch.cuda.set_device(0)
     __graft_entry__.build()
     name = args.workload if args.workload != "sphere_655360" else "ellipsoid_1310720"
@@ -270,6 +288,8 @@ def run_serving(args):
     import synthetic
     from paper_1803_09948_gb300 import serving
 
+    if _dist()[1] != 0:  # a single-GPU arm: under torchrun rank 0 runs it, the others exit
+        return
     torch.cuda.set_device(0)
     __graft_entry__.build()
     specs = synthetic.serving_requests(args.serve, seed=0, rate=20.0, n_max=args.serve_nmax,
@@ -350,12 +370,8 @@ def run_batched(args):
     launches = plan.launch_count() - launches0
     clk = clocks.stop()
     step_ms = [ev[q].elapsed_time(ev[q + 1]) for q in range(args.steps)]
-    total_ms = ev[0].elapsed_time(ev[args.steps])
-    if world > 1:
-        t = torch.tensor([total_ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * args.steps * R / (total_ms / 1e3)
+    total_ms = _max_over_ranks(ev[0].elapsed_time(ev[args.steps]), world)
+    value = _job_rate(args.steps * R, world, total_ms)
     # the same right-hand sides one at a time (context: the plain single right-hand-side form)
     b1, o1 = b[:N].clone(), torch.empty(N, dtype=torch.complex64, device="cuda")
     for _ in range(3):
@@ -383,7 +399,7 @@ def run_batched(args):
         h_out.copy_(out, non_blocking=True)
     e1.record(stream)
     barrier()
-    e2e_ms = e0.elapsed_time(e1)
+    e2e_ms = _max_over_ranks(e0.elapsed_time(e1), world)
     got = h_out.numpy().astype(np.complex128).reshape(R, N)
     S = h_in.numpy().astype(np.complex128).reshape(R, N)
     # R solves in lockstep (GMRES per right-hand side on shared batched matvecs), own timed region
@@ -439,7 +455,7 @@ def run_batched(args):
             "solve": solve,
             "single_rhs_ms": single_ms,
             "speedup_per_rhs_vs_single": single_ms / (total_ms / args.steps / R),
-            "e2e": {"value": args.steps * R / (e2e_ms / 1e3), "unit": "matvec/s", "h2d_bytes_per_step": 8 * N * R,
+            "e2e": {"value": _job_rate(args.steps * R, world, e2e_ms), "unit": "matvec/s", "h2d_bytes_per_step": 8 * N * R,
                     "d2h_bytes_per_step": 8 * N * R},
             "roofline": None,
             "cpu_baseline": cpu,
@@ -537,13 +553,9 @@ def main():
     barrier()
     launches = plan.launch_count() - launches0
     step_ms = [ev[s].elapsed_time(ev[s + 1]) for s in range(args.steps)]
-    total_ms = ev[0].elapsed_time(ev[args.steps])
-    if world > 1:
-        t = torch.tensor([total_ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = _max_over_ranks(ev[0].elapsed_time(ev[args.steps]), world)
     clk = clocks.stop()
-    value = world * args.steps / (total_ms / 1e3)
+    value = _job_rate(args.steps, world, total_ms)
 
     # ------------------------------------------------------------ per-stage breakdown (same stream)
     stages = None
@@ -569,7 +581,7 @@ def main():
         h_out.copy_(pot, non_blocking=True)
     e1.record(stream)
     barrier()
-    e2e_ms = e0.elapsed_time(e1)
+    e2e_ms = _max_over_ranks(e0.elapsed_time(e1), world)
     got = h_out.numpy().astype(np.complex128)
 
     # ------------------------------------------------------------ GMRES solves (own region)
@@ -664,7 +676,7 @@ def main():
             "stages_ms": stages,
             "plan_s": plan_s,
             "solve": solve,
-            "e2e": {"value": args.steps / (e2e_ms / 1e3), "unit": "matvec/s", "h2d_bytes_per_step": 8 * N,
+            "e2e": {"value": _job_rate(args.steps, world, e2e_ms), "unit": "matvec/s", "h2d_bytes_per_step": 8 * N,
                     "d2h_bytes_per_step": 8 * N},
             "roofline": rl,
             "cpu_baseline": cpu,
