@@ -77,6 +77,12 @@ typedef struct {
     double mem_budget_bytes; /* refuse a plan whose device footprint exceeds this (0: no limit) */
     int m2l_tensor;     /* 1: M2L of levels with (p+1)^2 <= 64 on the tensor cores (BF16 split in
                            three products, FP32 accumulation); 0: FP32 SIMT everywhere (1) */
+    int adaptive;       /* 1: adaptive octree: a box is split only while it holds more than
+                           leaf_max points, so leaves sit at several depths (depth > 0 caps them);
+                           leaves interact directly when their ancestors at the coarser leaf's
+                           level touch, every other pair through M2L between same-level boxes
+                           (the interaction lists of Sec. 2.3 read for unequal leaves).  Batched
+                           right-hand sides then run one at a time.  0: uniform depth (0) */
 } hfmm_config;
 
 /* Fills *cfg with the defaults shown in parentheses above (p_min = 7). */

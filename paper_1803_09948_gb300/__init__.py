@@ -48,6 +48,7 @@ class hfmm_config(ctypes.Structure):
         ("tol", ctypes.c_double),
         ("mem_budget_bytes", ctypes.c_double),
         ("m2l_tensor", ctypes.c_int),
+        ("adaptive", ctypes.c_int),
     ]
 
 

@@ -177,6 +177,7 @@ __device__ __forceinline__ void p2p_span(float tx, float ty, float tz, int k0, i
     }
 }
 
+constexpr int kStagedNbr = 64;  // most source leaves the staged kernel takes (27 in a uniform tree)
 template <bool POLY>
 __global__ void __launch_bounds__(128) k_p2p_staged(const int32_t* __restrict__ leaf_start,
                                                     const int4* __restrict__ leaf_ijk,
@@ -187,7 +188,7 @@ __global__ void __launch_bounds__(128) k_p2p_staged(const int32_t* __restrict__ 
                                                     float2* __restrict__ phi) {
     extern __shared__ float4 sp[];  // [cap]: shifted position, Re sigma
     float* sim = reinterpret_cast<float*>(sp + cap);  // [cap]: Im sigma
-    __shared__ int s_off[29], s_leaf[28];
+    __shared__ int s_off[kStagedNbr + 1], s_leaf[kStagedNbr], s_nl;
     const int b = blockIdx.x, tid = threadIdx.x;
     const int4 tij = __ldg(leaf_ijk + b);
     const int nb0 = __ldg(nbr_ptr + b), nn = __ldg(nbr_ptr + b + 1) - nb0;
@@ -203,10 +204,10 @@ __global__ void __launch_bounds__(128) k_p2p_staged(const int32_t* __restrict__ 
             o += __ldg(leaf_start + s_leaf[q] + 1) - __ldg(leaf_start + s_leaf[q]);
         }
         s_off[k] = o;
-        s_off[28] = k;
+        s_nl = k;
     }
     __syncthreads();
-    const int nl = s_off[28], total = s_off[nl];
+    const int nl = s_nl, total = s_off[nl];
     for (int q = 0; q < nl; ++q) {
         const int sl = s_leaf[q];
         const int j0 = __ldg(leaf_start + sl), n = s_off[q + 1] - s_off[q];
@@ -370,10 +371,14 @@ void upload_legendre_tables() {
 //   phase 3: thread c accumulates coefficient c = n^2 + n + m over the chunk.
 __global__ void __launch_bounds__(128) k_p2m(const int32_t* __restrict__ leaf_start,
                                              const float4* __restrict__ pts, const float2* __restrict__ sig,
-                                             int p, float s, float2* __restrict__ M) {
+                                             int p, float s, float2* __restrict__ M,
+                                             const int32_t* __restrict__ leaf_lev, int lev,
+                                             const int32_t* __restrict__ leaf_box) {
     constexpr int kChunk = 32;
     extern __shared__ float sm[];
     const int leaf = blockIdx.x;
+    if (leaf_lev && leaf_lev[leaf] != lev) return;  // uniform over the block: before any barrier
+    const int64_t box = leaf_box ? leaf_box[leaf] : leaf;
     const int P = (p + 1) * (p + 1);
     const int H = (p + 1) * (p + 2) / 2;
     float* rad = sm;                          // [kChunk][p+1]
@@ -469,7 +474,7 @@ __global__ void __launch_bounds__(128) k_p2m(const int32_t* __restrict__ leaf_st
         }
 #pragma unroll
         for (int q = 0; q < 2; ++q)
-            if (cc[q] < P) M[(int64_t)leaf * P + cc[q]] = make_float2(accr[q], acci[q]);
+            if (cc[q] < P) M[box * P + cc[q]] = make_float2(accr[q], acci[q]);
     }
 }
 
@@ -481,11 +486,15 @@ size_t p2m_smem_bytes(int p) {
 // ============================================================== L2P
 __global__ void __launch_bounds__(128) k_l2p(int64_t N, const int32_t* __restrict__ pt_leaf,
                                              const float4* __restrict__ pts, int p, float s,
-                                             const float2* __restrict__ Lc, float2* __restrict__ phi) {
+                                             const float2* __restrict__ Lc, float2* __restrict__ phi,
+                                             const int32_t* __restrict__ leaf_lev, int lev,
+                                             const int32_t* __restrict__ leaf_box) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
+    const int32_t b = pt_leaf[i];
+    if (leaf_lev && leaf_lev[b] != lev) return;  // adaptive tree: this launch's level only
     const int P = (p + 1) * (p + 1);
-    const float2* L = Lc + (int64_t)pt_leaf[i] * P;
+    const float2* L = Lc + (int64_t)(leaf_box ? leaf_box[b] : b) * P;
     const float4 y = pts[i];
     const Dir d = make_dir(y.x, y.y, y.z);
     float jr[HFMM_PMAX + 1];
@@ -552,7 +561,8 @@ __device__ __forceinline__ void jn_fixed(float x, float s, float (&jr)[PP + 1]) 
 template <int PP>
 __global__ void __launch_bounds__(128) k_p2m_w(int64_t nleaf, const int32_t* __restrict__ leaf_start,
                                                const float4* __restrict__ pts, const float2* __restrict__ sig,
-                                               float s, float2* __restrict__ M) {
+                                               float s, float2* __restrict__ M, const int32_t* __restrict__ leaf_lev,
+                                               int lev, const int32_t* __restrict__ leaf_box) {
     constexpr int P = (PP + 1) * (PP + 1), H = (PP + 1) * (PP + 2) / 2, NE = 2 * (PP + 1);
     constexpr int NC = (P + 31) / 32;
     __shared__ float Bs[4][H][33];
@@ -560,6 +570,8 @@ __global__ void __launch_bounds__(128) k_p2m_w(int64_t nleaf, const int32_t* __r
     const int wb = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t leaf = (int64_t)blockIdx.x * 4 + wb;
     if (leaf >= nleaf) return;  // warps are independent: no block-wide barrier below
+    if (leaf_lev && leaf_lev[leaf] != lev) return;  // adaptive tree: this launch's level only
+    const int64_t box = leaf_box ? leaf_box[leaf] : leaf;
     const int32_t b0 = leaf_start[leaf], b1 = leaf_start[leaf + 1];
     int hh[NC], ee[NC];
     float accr[NC], acci[NC];
@@ -618,18 +630,21 @@ __global__ void __launch_bounds__(128) k_p2m_w(int64_t nleaf, const int32_t* __r
     }
 #pragma unroll
     for (int q = 0; q < NC; ++q)
-        if (lane + 32 * q < P) M[leaf * P + lane + 32 * q] = make_float2(accr[q], acci[q]);
+        if (lane + 32 * q < P) M[box * P + lane + 32 * q] = make_float2(accr[q], acci[q]);
 }
 
 // L2P, one thread per point: phi += sum_nm L_nm jt_n(k r) Y_nm
 template <int PP>
 __global__ void __launch_bounds__(128) k_l2p_t(int64_t N, const int32_t* __restrict__ pt_leaf,
                                                const float4* __restrict__ pts, float s, const float2* __restrict__ Lc,
-                                               float2* __restrict__ phi) {
+                                               float2* __restrict__ phi, const int32_t* __restrict__ leaf_lev, int lev,
+                                               const int32_t* __restrict__ leaf_box) {
     constexpr int P = (PP + 1) * (PP + 1);
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
-    const float2* L = Lc + (int64_t)pt_leaf[i] * P;
+    const int32_t b = pt_leaf[i];
+    if (leaf_lev && leaf_lev[b] != lev) return;  // adaptive tree: this launch's level only
+    const float2* L = Lc + (int64_t)(leaf_box ? leaf_box[b] : b) * P;
     const float4 y = pts[i];
     const Dir d = make_dir(y.x, y.y, y.z);
     float jr[PP + 1];
@@ -671,27 +686,37 @@ __global__ void __launch_bounds__(128) k_l2p_t(int64_t N, const int32_t* __restr
     phi[i] = make_float2(o.x + accr, o.y + acci);
 }
 
-template <int PP>
-static void launch_p2m_l2p_fixed(bool p2m, const hfmm_plan* P, const LevelInfo& lv, cudaStream_t st) {
-    if (p2m)
-        k_p2m_w<PP><<<(unsigned)((P->nleaf + 3) / 4), 128, 0, st>>>(P->nleaf, P->leaf_start.p, P->pts.p, P->sig.p,
-                                                                    (float)lv.s, P->coef.p + lv.mofs);
-    else
-        k_l2p_t<PP><<<(unsigned)((P->N + 127) / 128), 128, 0, st>>>(P->N, P->pt_leaf.p, P->pts.p, (float)lv.s,
-                                                                    P->coef.p + lv.lofs, P->phi.p);
+// leaf filter of level l: every leaf of a uniform tree is at level L (no filter)
+struct LeafFilter {
+    const int32_t* lev;
+    int l;
+    const int32_t* box;
+};
+static LeafFilter leaf_filter(const hfmm_plan* P, int l) {
+    return P->adaptive ? LeafFilter{P->leaf_lev.p, l, P->leaf_box.p} : LeafFilter{nullptr, l, nullptr};
 }
 
-// P2M (p2m = true) or L2P at the leaf level at its fixed order; false if p > kFixedPMax
-static bool p2m_l2p_fixed(bool p2m, const hfmm_plan* P, const LevelInfo& lv, cudaStream_t st) {
+template <int PP>
+static void launch_p2m_l2p_fixed(bool p2m, const hfmm_plan* P, const LevelInfo& lv, LeafFilter f, cudaStream_t st) {
+    if (p2m)
+        k_p2m_w<PP><<<(unsigned)((P->nleaf + 3) / 4), 128, 0, st>>>(P->nleaf, P->leaf_start.p, P->pts.p, P->sig.p,
+                                                                    (float)lv.s, P->coef.p + lv.mofs, f.lev, f.l, f.box);
+    else
+        k_l2p_t<PP><<<(unsigned)((P->N + 127) / 128), 128, 0, st>>>(P->N, P->pt_leaf.p, P->pts.p, (float)lv.s,
+                                                                    P->coef.p + lv.lofs, P->phi.p, f.lev, f.l, f.box);
+}
+
+// P2M (p2m = true) or L2P of the leaves of one level at its fixed order; false if p > kFixedPMax
+static bool p2m_l2p_fixed(bool p2m, const hfmm_plan* P, const LevelInfo& lv, LeafFilter f, cudaStream_t st) {
     switch (lv.p) {
-        case 1: launch_p2m_l2p_fixed<1>(p2m, P, lv, st); return true;
-        case 2: launch_p2m_l2p_fixed<2>(p2m, P, lv, st); return true;
-        case 3: launch_p2m_l2p_fixed<3>(p2m, P, lv, st); return true;
-        case 4: launch_p2m_l2p_fixed<4>(p2m, P, lv, st); return true;
-        case 5: launch_p2m_l2p_fixed<5>(p2m, P, lv, st); return true;
-        case 6: launch_p2m_l2p_fixed<6>(p2m, P, lv, st); return true;
-        case 7: launch_p2m_l2p_fixed<7>(p2m, P, lv, st); return true;
-        case 8: launch_p2m_l2p_fixed<8>(p2m, P, lv, st); return true;
+        case 1: launch_p2m_l2p_fixed<1>(p2m, P, lv, f, st); return true;
+        case 2: launch_p2m_l2p_fixed<2>(p2m, P, lv, f, st); return true;
+        case 3: launch_p2m_l2p_fixed<3>(p2m, P, lv, f, st); return true;
+        case 4: launch_p2m_l2p_fixed<4>(p2m, P, lv, f, st); return true;
+        case 5: launch_p2m_l2p_fixed<5>(p2m, P, lv, f, st); return true;
+        case 6: launch_p2m_l2p_fixed<6>(p2m, P, lv, f, st); return true;
+        case 7: launch_p2m_l2p_fixed<7>(p2m, P, lv, f, st); return true;
+        case 8: launch_p2m_l2p_fixed<8>(p2m, P, lv, f, st); return true;
         default: return false;
     }
 }
@@ -956,7 +981,7 @@ void run_matvec_sorted(hfmm_plan* P, int parts, cudaStream_t st) {
     mark_stage(P, 1, st);
     if (parts & 1) {
         const size_t staged = (size_t)P->p2p_cap * (sizeof(float4) + sizeof(float));
-        if (P->p2p_cap > 0 && staged <= 96 * 1024) {
+        if (P->p2p_cap > 0 && staged <= 96 * 1024 && P->p2p_maxnbr <= kStagedNbr) {
             if (staged > 48 * 1024) {
                 HFMM_CUDA(cudaFuncSetAttribute(k_p2p_staged<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                (int)staged));
@@ -990,15 +1015,18 @@ void run_matvec_sorted(hfmm_plan* P, int parts, cudaStream_t st) {
     if (far) {
         // multipoles above the leaves and all locals accumulate: clear them
         HFMM_CUDA(cudaMemsetAsync(P->coef.p, 0, sizeof(float2) * P->coef_total, st));
-        const LevelInfo& lv = P->lev[L];
-        if (!p2m_l2p_fixed(true, P, lv, st)) {
-            const size_t smem = p2m_smem_bytes(lv.p);
-            if (smem > 48 * 1024)
-                HFMM_CUDA(cudaFuncSetAttribute(k_p2m, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            k_p2m<<<(unsigned)P->nleaf, 128, smem, st>>>(P->leaf_start.p, P->pts.p, P->sig.p, lv.p, (float)lv.s,
-                                                           P->coef.p + lv.mofs);
+        for (int l : P->leaf_levels) {  // the leaves of each level (all at L in a uniform tree)
+            const LevelInfo& lv = P->lev[l];
+            const LeafFilter f = leaf_filter(P, l);
+            if (!p2m_l2p_fixed(true, P, lv, f, st)) {
+                const size_t smem = p2m_smem_bytes(lv.p);
+                if (smem > 48 * 1024)
+                    HFMM_CUDA(cudaFuncSetAttribute(k_p2m, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+                k_p2m<<<(unsigned)P->nleaf, 128, smem, st>>>(P->leaf_start.p, P->pts.p, P->sig.p, lv.p, (float)lv.s,
+                                                               P->coef.p + lv.mofs, f.lev, f.l, f.box);
+            }
+            ++P->launches;
         }
-        ++P->launches;
     }
     mark_stage(P, 3, st);
     if (far)
@@ -1041,11 +1069,14 @@ void run_matvec_sorted(hfmm_plan* P, int parts, cudaStream_t st) {
         }
     mark_stage(P, 7, st);
     if (far) {
-        const LevelInfo& lv = P->lev[L];
-        if (!p2m_l2p_fixed(false, P, lv, st))
-            k_l2p<<<(unsigned)((N + 127) / 128), 128, 0, st>>>(N, P->pt_leaf.p, P->pts.p, lv.p, (float)lv.s,
-                                                               P->coef.p + lv.lofs, P->phi.p);
-        ++P->launches;
+        for (int l : P->leaf_levels) {
+            const LevelInfo& lv = P->lev[l];
+            const LeafFilter f = leaf_filter(P, l);
+            if (!p2m_l2p_fixed(false, P, lv, f, st))
+                k_l2p<<<(unsigned)((N + 127) / 128), 128, 0, st>>>(N, P->pt_leaf.p, P->pts.p, lv.p, (float)lv.s,
+                                                                   P->coef.p + lv.lofs, P->phi.p, f.lev, f.l, f.box);
+            ++P->launches;
+        }
     }
     mark_stage(P, 8, st);
     if ((parts & 4) && P->corr_nnz > 0) {
@@ -1454,7 +1485,7 @@ __global__ void __launch_bounds__(256) k_corr_b(int64_t N, int R, const int64_t*
 }
 
 bool batch_supported(const hfmm_plan* P, int R) {
-    if (R < 2 || R > kBMax) return false;
+    if (R < 2 || R > kBMax || P->adaptive) return false;
     if (P->L >= 2 && P->lev[P->L].P > kBMaxP) return false;
     return P->p2p_cap > 0 && p2p_b_smem(P->p2p_cap) <= 200 * 1024;
 }

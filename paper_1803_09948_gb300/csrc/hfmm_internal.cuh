@@ -131,7 +131,7 @@ struct hfmm_plan {
     int64_t corr_nnz = 0, m2l_count = 0;
     size_t dev_bytes = 0;
     bool poly_p2p = true;   // near field fits the polynomial kernel range
-    float p2p_shift = 0.f;  // k * side of a leaf
+    float p2p_shift = 0.f;  // k * half the side of a level-L box (the unit of leaf_ijk)
     int p2p_cap = 0;        // most source points in one leaf's neighbourhood (staged near field)
 
     // sorted point data
@@ -145,7 +145,12 @@ struct hfmm_plan {
     std::vector<int32_t> host_t;         // triangle of each point
     // leaves
     DBuf<int32_t> leaf_start;  // nleaf + 1
-    DBuf<int4> leaf_ijk;       // integer coordinates at level L
+    DBuf<int4> leaf_ijk;       // centre in units of half a level-L side: (2 ijk + 1) 2^(L - level)
+    bool adaptive = false;     // leaves at several levels (else every leaf is at level L)
+    DBuf<int32_t> leaf_lev;    // adaptive: level of each leaf
+    DBuf<int32_t> leaf_box;    // adaptive: index of each leaf among its level's boxes
+    std::vector<int> leaf_levels;  // levels that hold leaves (ascending)
+    int p2p_maxnbr = 27;       // most source leaves in one leaf's near list
     DBuf<int32_t> nbr_ptr, nbr;
     DBuf<int4> tiles;          // (leaf, first point, count, 0)
     // far field
@@ -269,20 +274,21 @@ int64_t build_correction(hfmm_plan* P, const CorrInputs& in, cudaStream_t st);
 // [lo, lo + 2^20 / scale)^3, sorted stably: keys_sorted[i], perm[i] = user index.
 void tree_sort_points(const double* x, int64_t N, const double lo[3], double scale, uint64_t* keys_sorted,
                       int32_t* perm, cudaStream_t st);
-struct LeafData {      // per sorted point i (leaf_ijk per leaf)
-    float4* pts;       // k (x - leaf centre)
+struct LeafData {      // per sorted point i
+    float4* pts;       // k (x - centre of the point's leaf)
     float* wscale;     // k w / (4 pi)
     int32_t* pt_leaf;  // leaf index
-    int4* pt_ijk;      // integer leaf coordinates at the leaf level
+    int4* pt_ijk;      // integer coordinates of the point's cell at the deepest level L
     double* x64s;      // sorted FP64 points (N x 3)
     double* w64s;      // sorted FP64 weights
     int32_t* tri_s;    // triangle of the point
     int32_t* iperm;    // user -> sorted (written at iperm[perm[i]])
-    int4* leaf_ijk;    // integer coordinates of each leaf
 };
-void tree_leaf_data(const double* x, const double* w, const int32_t* tri, const int32_t* perm, const uint64_t* leaf_key,
-                    const int32_t* leaf_start, int64_t nleaf, int64_t N, const double lo[3], double side, double k,
-                    const LeafData& out, cudaStream_t st);
+// keys: the sorted point keys; leaf_c2: each leaf's centre in units of half the side of a
+// level-L box ((2 ijk + 1) 2^(L - l) for a leaf at level l), so centre = lo + c2 * half_side
+void tree_leaf_data(const double* x, const double* w, const int32_t* tri, const int32_t* perm, const uint64_t* keys,
+                    int L, const int4* leaf_c2, const int32_t* leaf_start, int64_t nleaf, int64_t N,
+                    const double lo[3], double half_side, double k, const LeafData& out, cudaStream_t st);
 // 27-box neighbour lists of the leaves (self included, order dx, dy, dz); also returns
 // the host copy of the list offsets and each leaf's neighbourhood point count.
 void tree_leaf_neighbours(const uint64_t* leaf_key, const int32_t* leaf_start, int64_t nleaf, int L,

@@ -25,6 +25,33 @@ static thread_local std::string g_last_error;
 
 void hfmm_set_last_error(const std::string& msg) { g_last_error = msg; }
 
+static inline uint64_t spread3_h(uint64_t v) {
+    v &= 0x1fffff;
+    v = (v | v << 32) & 0x1f00000000ffffull;
+    v = (v | v << 16) & 0x1f0000ff0000ffull;
+    v = (v | v << 8) & 0x100f00f00f00f00full;
+    v = (v | v << 4) & 0x10c30c30c30c30c3ull;
+    v = (v | v << 2) & 0x1249249249249249ull;
+    return v;
+}
+static inline uint64_t morton_h(uint64_t x, uint64_t y, uint64_t z) {
+    return (spread3_h(x) << 2) | (spread3_h(y) << 1) | spread3_h(z);
+}
+static inline uint64_t compact3_h(uint64_t v) {
+    v &= 0x1249249249249249ull;
+    v = (v ^ (v >> 2)) & 0x10c30c30c30c30c3ull;
+    v = (v ^ (v >> 4)) & 0x100f00f00f00f00full;
+    v = (v ^ (v >> 8)) & 0x1f0000ff0000ffull;
+    v = (v ^ (v >> 16)) & 0x1f00000000ffffull;
+    v = (v ^ (v >> 32)) & 0x1fffff;
+    return v;
+}
+static inline void demorton_h(uint64_t k, int64_t* c) {
+    c[0] = (int64_t)compact3_h(k >> 2);
+    c[1] = (int64_t)compact3_h(k >> 1);
+    c[2] = (int64_t)compact3_h(k);
+}
+
 static int64_t find_sorted(const std::vector<uint64_t>& keys, uint64_t key) {
     auto it = std::lower_bound(keys.begin(), keys.end(), key);
     if (it == keys.end() || *it != key) return -1;
@@ -58,8 +85,25 @@ static int level_order(const hfmm_config& c, double k, double side) {
 namespace {
 struct HostLevel {
     std::vector<uint64_t> key;
-    std::vector<int32_t> start;  // nbox + 1
+    std::vector<int32_t> start;  // uniform: nbox + 1 (boxes cover the points); adaptive: nbox
+    std::vector<int32_t> end;    // adaptive: end of each box's point range
+    std::vector<int32_t> leaf;   // adaptive: leaf index of each box, -1 for a split box
 };
+
+// every occupied cell of level l of the sorted keys (20 bits per axis)
+static HostLevel occupied_cells(const std::vector<uint64_t>& skeys, int l) {
+    HostLevel h;
+    const int sh = 3 * (20 - l);
+    for (size_t i = 0; i < skeys.size(); ++i) {
+        const uint64_t key = skeys[i] >> sh;
+        if (i == 0 || key != (skeys[i - 1] >> sh)) {
+            h.key.push_back(key);
+            h.start.push_back((int32_t)i);
+        }
+    }
+    h.start.push_back((int32_t)skeys.size());
+    return h;
+}
 
 // (source, destination) column pairs grouped by operator: bucket g is
 // pairs[start[g] .. start[g + 1])
@@ -170,32 +214,78 @@ static void build_plan(hfmm_plan* P, const double* V, int64_t nv, const int32_t*
     std::vector<uint64_t> skeys(N);
     HFMM_CUDA(cudaMemcpyAsync(skeys.data(), d_keys.p, sizeof(uint64_t) * N, cudaMemcpyDeviceToHost, st));
     HFMM_CUDA(cudaStreamSynchronize(st));
-    d_keys.release();
-    int L = cfg.depth;
-    if (L <= 0) {
-        for (L = 0; L < LMAX; ++L) {
-            int sh = 3 * (LMAX - L);
-            int64_t run = 0, best = 0;
-            for (int64_t i = 0; i < N; ++i) {
-                run = (i > 0 && (skeys[i] >> sh) == (skeys[i - 1] >> sh)) ? run + 1 : 1;
-                best = std::max(best, run);
+    // The tree's boxes per level (sorted keys) and its leaves in Morton order.  Uniform: every
+    // occupied cell down to the smallest depth whose fullest cell holds <= leaf_max points;
+    // adaptive: a box is split only while it holds more than leaf_max points.
+    std::vector<HostLevel> lv;
+    std::vector<uint64_t> leaf_key;
+    std::vector<int32_t> leaf_lev, leaf_box, leaf_start;
+    int L = 0;
+    if (!cfg.adaptive) {
+        L = cfg.depth;
+        if (L <= 0) {
+            for (L = 0; L < LMAX; ++L) {
+                int sh = 3 * (LMAX - L);
+                int64_t run = 0, best = 0;
+                for (int64_t i = 0; i < N; ++i) {
+                    run = (i > 0 && (skeys[i] >> sh) == (skeys[i - 1] >> sh)) ? run + 1 : 1;
+                    best = std::max(best, run);
+                }
+                if (best <= cfg.leaf_max) break;
             }
-            if (best <= cfg.leaf_max) break;
         }
+        L = std::min(L, LMAX);
+        lv.resize(L + 1);
+        for (int l = 0; l <= L; ++l) lv[l] = occupied_cells(skeys, l);
+        leaf_key = lv[L].key;
+        leaf_start = lv[L].start;
+        leaf_lev.assign(leaf_key.size(), L);
+        leaf_box.resize(leaf_key.size());
+        std::iota(leaf_box.begin(), leaf_box.end(), 0);
+    } else {
+        const int maxdepth = cfg.depth > 0 ? std::min(cfg.depth, LMAX) : LMAX;
+        lv.resize(maxdepth + 1);
+        // depth first in Morton order, so each level's boxes come out with ascending keys
+        struct Node {
+            int l;
+            int32_t b, e;
+        };
+        std::vector<Node> stack{{0, 0, (int32_t)N}};
+        std::vector<Node> ch;
+        while (!stack.empty()) {
+            const Node nd = stack.back();
+            stack.pop_back();
+            const int sh = 3 * (LMAX - nd.l);
+            HostLevel& h = lv[nd.l];
+            h.key.push_back(skeys[nd.b] >> sh);
+            h.start.push_back(nd.b);
+            h.end.push_back(nd.e);
+            if (nd.e - nd.b <= cfg.leaf_max || nd.l == maxdepth) {
+                h.leaf.push_back((int32_t)leaf_key.size());
+                leaf_key.push_back(skeys[nd.b] >> sh);
+                leaf_lev.push_back(nd.l);
+                leaf_box.push_back((int32_t)h.key.size() - 1);
+                leaf_start.push_back(nd.b);
+                L = std::max(L, nd.l);
+            } else {
+                h.leaf.push_back(-1);
+                const int shc = 3 * (LMAX - nd.l - 1);
+                ch.clear();
+                for (int32_t i = nd.b; i < nd.e;) {
+                    int32_t j = i;
+                    while (j < nd.e && (skeys[j] >> shc) == (skeys[i] >> shc)) ++j;
+                    ch.push_back({nd.l + 1, i, j});
+                    i = j;
+                }
+                for (auto it = ch.rbegin(); it != ch.rend(); ++it) stack.push_back(*it);
+            }
+        }
+        leaf_start.push_back((int32_t)N);
+        lv.resize(L + 1);
     }
-    L = std::min(L, LMAX);
     P->L = L;
-    std::vector<HostLevel> lv(L + 1);
+    P->adaptive = cfg.adaptive != 0;
     for (int l = 0; l <= L; ++l) {
-        int sh = 3 * (LMAX - l);
-        for (int64_t i = 0; i < N; ++i) {
-            uint64_t key = skeys[i] >> sh;
-            if (i == 0 || key != (skeys[i - 1] >> sh)) {
-                lv[l].key.push_back(key);
-                lv[l].start.push_back((int32_t)i);
-            }
-        }
-        lv[l].start.push_back((int32_t)N);
         P->lev[l].nbox = (int64_t)lv[l].key.size();
         P->lev[l].side = D / std::ldexp(1.0, l);
         if (l >= 2) {
@@ -206,10 +296,23 @@ static void build_plan(hfmm_plan* P, const double* V, int64_t nv, const int32_t*
         P->lev[l].s = std::min(1.0, k * 0.5 * std::sqrt(3.0) * P->lev[l].side);
     }
     // ---------------------------------------------------------- sorted point data
-    const HostLevel& leaves = lv[L];
-    int64_t nleaf = (int64_t)leaves.key.size();
+    const int64_t nleaf = (int64_t)leaf_key.size();
     P->nleaf = nleaf;
     const double sideL = P->lev[L].side;
+    int lmin = L;  // coarsest leaf level
+    for (int32_t l : leaf_lev) lmin = std::min(lmin, (int)l);
+    P->leaf_levels.clear();
+    for (int l = std::max(lmin, 2); l <= L; ++l)
+        if (std::find(leaf_lev.begin(), leaf_lev.end(), l) != leaf_lev.end()) P->leaf_levels.push_back(l);
+    // leaf centres in units of half a level-L side
+    std::vector<int4> leaf_c2(nleaf);
+    for (int64_t b = 0; b < nleaf; ++b) {
+        int64_t c[3];
+        demorton_h(leaf_key[b], c);
+        const int sh = L - leaf_lev[b];
+        leaf_c2[b] = make_int4((int)((2 * c[0] + 1) << sh), (int)((2 * c[1] + 1) << sh), (int)((2 * c[2] + 1) << sh),
+                               leaf_lev[b]);
+    }
     upload_legendre_tables();
     DBuf<double> d_w, d_x64s, d_w64s, d_V;
     DBuf<int32_t> d_t, d_tri, d_F, d_sstart;
@@ -217,39 +320,90 @@ static void build_plan(hfmm_plan* P, const double* V, int64_t nv, const int32_t*
     DBuf<int4> d_pt_ijk;
     d_w.upload(W, nullptr, st);
     d_t.upload(T, nullptr, st);
-    d_leafkey.upload(leaves.key, nullptr, st);
-    P->leaf_start.upload(leaves.start, cnt, st);
+    P->leaf_start.upload(leaf_start, cnt, st);
+    P->leaf_ijk.upload(leaf_c2, cnt, st);
     P->pts.alloc(N, cnt);
     P->iperm.alloc(N, cnt);
     P->wscale.alloc(N, cnt);
     P->pt_leaf.alloc(N, cnt);
-    P->leaf_ijk.alloc(nleaf, cnt);
     d_x64s.alloc(3 * N, nullptr);
     d_w64s.alloc(N, nullptr);
     d_tri.alloc(N, nullptr);
     d_pt_ijk.alloc(N, nullptr);
-    LeafData ld{P->pts.p, P->wscale.p, P->pt_leaf.p, d_pt_ijk.p, d_x64s.p, d_w64s.p, d_tri.p, P->iperm.p, P->leaf_ijk.p};
-    tree_leaf_data(P->x64.p, d_w.p, d_t.p, P->perm.p, d_leafkey.p, P->leaf_start.p, nleaf, N, P->lo, sideL, k, ld, st);
-    // neighbour lists (27 boxes, self included) and target tiles
+    LeafData ld{P->pts.p, P->wscale.p, P->pt_leaf.p, d_pt_ijk.p, d_x64s.p, d_w64s.p, d_tri.p, P->iperm.p};
+    tree_leaf_data(P->x64.p, d_w.p, d_t.p, P->perm.p, d_keys.p, L, P->leaf_ijk.p, P->leaf_start.p, nleaf, N, P->lo,
+                   0.5 * sideL, k, ld, st);
+    // near lists (self included) and target tiles
     std::vector<int32_t> nbr_ptr;
     std::vector<int64_t> hood;
-    tree_leaf_neighbours(d_leafkey.p, P->leaf_start.p, nleaf, L, P->nbr_ptr, P->nbr, nbr_ptr, hood, cnt, st);
+    if (!P->adaptive) {  // 27 same-level boxes, on the device
+        d_leafkey.upload(leaf_key, nullptr, st);
+        tree_leaf_neighbours(d_leafkey.p, P->leaf_start.p, nleaf, L, P->nbr_ptr, P->nbr, nbr_ptr, hood, cnt, st);
+        P->p2p_maxnbr = 27;
+    } else {
+        // Leaves t, s interact directly when their ancestors at level min(level t, level s)
+        // touch (or coincide); every other pair meets through M2L between two same-level
+        // boxes with touching parents.  For leaf t: (a) the leaves among the 27 neighbours of
+        // each ancestor of t (t included), (b) every leaf under a split neighbour of t.
+        std::vector<int32_t> nbr;
+        nbr_ptr.assign(nleaf + 1, 0);
+        hood.assign(nleaf, 0);
+        int maxn = 0;
+        for (int64_t t = 0; t < nleaf; ++t) {
+            const int lt = leaf_lev[t];
+            const size_t n0 = nbr.size();
+            for (int m = 0; m <= lt; ++m) {
+                int64_t c[3];
+                demorton_h(leaf_key[t] >> (3 * (lt - m)), c);
+                const int64_t nl = (int64_t)1 << m;
+                for (int dx = -1; dx <= 1; ++dx)
+                    for (int dy = -1; dy <= 1; ++dy)
+                        for (int dz = -1; dz <= 1; ++dz) {
+                            const int64_t x = c[0] + dx, y = c[1] + dy, z = c[2] + dz;
+                            if (x < 0 || y < 0 || z < 0 || x >= nl || y >= nl || z >= nl) continue;
+                            const int64_t q = find_sorted(lv[m].key, morton_h(x, y, z));
+                            if (q < 0) continue;
+                            if (lv[m].leaf[q] >= 0) {
+                                nbr.push_back(lv[m].leaf[q]);
+                            } else if (m == lt) {  // split neighbour of t: its leaves are consecutive
+                                const int64_t l0 = std::lower_bound(leaf_start.begin(), leaf_start.end() - 1,
+                                                                    lv[m].start[q]) - leaf_start.begin();
+                                const int64_t l1 = std::lower_bound(leaf_start.begin(), leaf_start.end() - 1,
+                                                                    lv[m].end[q]) - leaf_start.begin();
+                                for (int64_t s2 = l0; s2 < l1; ++s2) nbr.push_back((int32_t)s2);
+                            }
+                        }
+            }
+            for (size_t q = n0; q < nbr.size(); ++q) hood[t] += leaf_start[nbr[q] + 1] - leaf_start[nbr[q]];
+            nbr_ptr[t + 1] = (int32_t)nbr.size();
+            maxn = std::max(maxn, (int)(nbr.size() - n0));
+        }
+        P->nbr_ptr.upload(nbr_ptr, cnt, st);
+        P->nbr.upload(nbr, cnt, st);
+        P->p2p_maxnbr = maxn;
+        P->leaf_lev.upload(leaf_lev, cnt, st);
+        P->leaf_box.upload(leaf_box, cnt, st);
+    }
     std::vector<int4> tiles;
     for (int64_t b = 0; b < nleaf; ++b)
-        for (int32_t i0 = leaves.start[b]; i0 < leaves.start[b + 1]; i0 += kP2PTile)
-            tiles.push_back(make_int4((int)b, i0, std::min(kP2PTile, leaves.start[b + 1] - i0), 0));
+        for (int32_t i0 = leaf_start[b]; i0 < leaf_start[b + 1]; i0 += kP2PTile)
+            tiles.push_back(make_int4((int)b, i0, std::min(kP2PTile, leaf_start[b + 1] - i0), 0));
     P->ntiles = (int64_t)tiles.size();
     double pairs = 0.0;
     int64_t cap = 0;
     for (int64_t b = 0; b < nleaf; ++b) {
-        pairs += (double)(leaves.start[b + 1] - leaves.start[b]) * (double)hood[b];
+        pairs += (double)(leaf_start[b + 1] - leaf_start[b]) * (double)hood[b];
         cap = std::max(cap, hood[b]);
     }
     P->cost[0] = pairs - (double)N;
     P->p2p_cap = (int)std::min<int64_t>(cap, 1 << 30);
     P->cost[4] = (double)N;
-    P->p2p_shift = (float)(k * sideL);
-    P->poly_p2p = 12.0 * (k * sideL) * (k * sideL) * 1.001 <= (double)HFMM_POLY_UMAX;
+    P->p2p_shift = (float)(0.5 * k * sideL);
+    // direct pairs are at most 2 sqrt(3) coarsest-leaf sides apart
+    const double side_c = P->lev[lmin].side;
+    P->poly_p2p = 12.0 * (k * side_c) * (k * side_c) * 1.001 <= (double)HFMM_POLY_UMAX;
+    HFMM_CUDA(cudaStreamSynchronize(st));
+    d_keys.release();
 
     P->tiles.upload(tiles, cnt, st);
     P->sig.alloc(N, cnt);
@@ -543,7 +697,7 @@ static void build_plan(hfmm_plan* P, const double* V, int64_t nv, const int32_t*
     // ---------------------------------------------------------- self / near correction (Sec. 2.2)
     int ls = L;
     while (ls > 0 && P->lev[ls].side < P->r_near) --ls;
-    const HostLevel& S = lv[ls];
+    const HostLevel S = P->adaptive ? occupied_cells(skeys, ls) : lv[ls];
     std::vector<double> Vh(V, V + 3 * nv);
     std::vector<int32_t> Fh(F, F + 3 * nt);
     d_V.upload(Vh, nullptr, st);
@@ -606,6 +760,7 @@ void hfmm_default_config(hfmm_config* c) {
     c->tol = 1e-4;
     c->mem_budget_bytes = 0.0;
     c->m2l_tensor = 1;
+    c->adaptive = 0;
 }
 
 const char* hfmm_last_error(void) { return g_last_error.c_str(); }
@@ -632,7 +787,7 @@ int hfmm_plan_create(const hfmm_config* cfg, const double* vertices, int64_t n_v
     if (cfg->leaf_max < 1 || cfg->depth < 0 || cfg->depth > 20 || cfg->p_fixed < 0 || cfg->p_fixed > HFMM_PMAX ||
         cfg->p_min < 0 || cfg->p_min > HFMM_PMAX || !(cfg->near_factor >= 0.0) || cfg->quad_order < 2 ||
         cfg->quad_order > 64 || cfg->restart < 1 || cfg->max_iter < 1 || !(cfg->tol > 0.0) ||
-        (cfg->m2l_tensor != 0 && cfg->m2l_tensor != 1))
+        (cfg->m2l_tensor != 0 && cfg->m2l_tensor != 1) || (cfg->adaptive != 0 && cfg->adaptive != 1))
         return HFMM_E_INVALID;
     if (3 * n_tri > (int64_t)INT32_MAX / 2) return HFMM_E_INVALID;
     HFMM_GUARD_BEGIN

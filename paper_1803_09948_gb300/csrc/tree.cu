@@ -1,8 +1,8 @@
 // Octree construction on the device (Sec. 2.3 octree; Sec. 3.1-3.2 Morton order, a
 // cell = first index + count): Morton keys of the points and their stable sort,
 // per-point leaf data (positions relative to the leaf centre, pre-scaled weights,
-// integer coordinates), the 27-box neighbour lists of the leaves, and the M2L
-// interaction lists of one level bucketed by translation offset.
+// integer coordinates), the 27-box neighbour lists of the leaves of a uniform tree, and
+// the M2L interaction lists of one level bucketed by translation offset.
 //
 // Keys interleave 20 bits per axis (x in the highest bit of each triple).  Every
 // list comes out in the order a sequential loop would produce it (neighbours by
@@ -73,9 +73,9 @@ __global__ void k_morton_keys(const double* __restrict__ x, int64_t N, double lo
 
 // one thread per sorted point: its leaf's data and the sorted copies of its inputs
 __global__ void k_leaf_data(const double* __restrict__ x, const double* __restrict__ w, const int32_t* __restrict__ tri,
-                            const int32_t* __restrict__ perm, const uint64_t* __restrict__ leaf_key,
-                            const int32_t* __restrict__ leaf_start, int64_t nleaf, int64_t N, double lo0, double lo1,
-                            double lo2, double side, double k, LeafData o) {
+                            const int32_t* __restrict__ perm, const uint64_t* __restrict__ keys, int L,
+                            const int4* __restrict__ leaf_c2, const int32_t* __restrict__ leaf_start, int64_t nleaf,
+                            int64_t N, double lo0, double lo1, double lo2, double half_side, double k, LeafData o) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     // leaf of point i: the last b with leaf_start[b] <= i
@@ -86,21 +86,19 @@ __global__ void k_leaf_data(const double* __restrict__ x, const double* __restri
         else hi = mid - 1;
     }
     const int64_t b = lo;
-    const int4 c = t_demorton(leaf_key[b]);
-    const double ctr[3] = {lo0 + ((double)c.x + 0.5) * side, lo1 + ((double)c.y + 0.5) * side,
-                           lo2 + ((double)c.z + 0.5) * side};
+    const int4 c = leaf_c2[b];
+    const double ctr[3] = {lo0 + (double)c.x * half_side, lo1 + (double)c.y * half_side, lo2 + (double)c.z * half_side};
     const int32_t u = perm[i];
     const double xu[3] = {x[3 * (int64_t)u], x[3 * (int64_t)u + 1], x[3 * (int64_t)u + 2]};
     o.pts[i] = make_float4((float)(k * (xu[0] - ctr[0])), (float)(k * (xu[1] - ctr[1])), (float)(k * (xu[2] - ctr[2])),
                            0.f);
     o.wscale[i] = (float)(k * w[u] / (4.0 * 3.14159265358979323846));
     o.pt_leaf[i] = (int32_t)b;
-    o.pt_ijk[i] = c;
+    o.pt_ijk[i] = t_demorton(keys[i] >> (3 * (kLmax - L)));
     for (int d = 0; d < 3; ++d) o.x64s[3 * i + d] = xu[d];
     o.w64s[i] = w[u];
     o.tri_s[i] = tri[u];
     o.iperm[u] = (int32_t)i;
-    if (i == leaf_start[b]) o.leaf_ijk[b] = c;
 }
 
 // neighbour lists: pass 0 counts, pass 1 writes (order dx, dy, dz) and each leaf's
@@ -225,12 +223,12 @@ void tree_sort_points(const double* x, int64_t N, const double lo[3], double sca
     HFMM_CUDA(cudaStreamSynchronize(st));  // the scratch buffers are freed on return
 }
 
-void tree_leaf_data(const double* x, const double* w, const int32_t* tri, const int32_t* perm, const uint64_t* leaf_key,
-                    const int32_t* leaf_start, int64_t nleaf, int64_t N, const double lo[3], double side, double k,
-                    const LeafData& o, cudaStream_t st) {
+void tree_leaf_data(const double* x, const double* w, const int32_t* tri, const int32_t* perm, const uint64_t* keys,
+                    int L, const int4* leaf_c2, const int32_t* leaf_start, int64_t nleaf, int64_t N,
+                    const double lo[3], double half_side, double k, const LeafData& o, cudaStream_t st) {
     if (N <= 0) return;
-    k_leaf_data<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(x, w, tri, perm, leaf_key, leaf_start, nleaf, N, lo[0],
-                                                             lo[1], lo[2], side, k, o);
+    k_leaf_data<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(x, w, tri, perm, keys, L, leaf_c2, leaf_start, nleaf, N,
+                                                             lo[0], lo[1], lo[2], half_side, k, o);
     HFMM_CUDA(cudaGetLastError());
 }
 

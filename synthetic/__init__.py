@@ -8,6 +8,7 @@ from .meshes import (  # noqa: F401
     icosphere,
     bisect_longest_edges,
     sphere_mesh,
+    refined_cap_sphere,
     ellipsoid_mesh,
     star_mesh,
     geodesic_sphere,

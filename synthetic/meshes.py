@@ -110,6 +110,19 @@ def bisect_longest_edges(v, f):
     return np.concatenate([v, mid], axis=0), nf.astype(np.int32)
 
 
+def refined_cap_sphere(level: int, extra: int, z0: float = 0.5):
+    """Icosphere of the given level whose triangles with centroid z > z0 are split across
+    their longest edge `extra` more times (T-junctions at the cap's rim): the point density
+    in the cap is 2^extra times the rest, the non-uniform case for an adaptive octree."""
+    v, f = icosphere(level)
+    for _ in range(extra):
+        c = (v[f[:, 0]] + v[f[:, 1]] + v[f[:, 2]]) / 3.0
+        cap = c[:, 2] > z0
+        v2, f2 = bisect_longest_edges(v, f[cap])
+        v, f = v2, np.concatenate([f[~cap], f2]).astype(np.int32)
+    return v, f
+
+
 def sphere_mesh(level: int, bisect: bool = False, radius: float = 1.0):
     v, f = icosphere(level)
     if bisect:

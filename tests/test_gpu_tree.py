@@ -13,6 +13,14 @@ restatement of their definitions (Sec. 2.3 octree and interaction lists; Sec.
   * M2M / L2L: one translation per (child, parent) pair.
 
 Exact integer equality of every count.
+
+Adaptive trees (config adaptive = 1): a box is split only while it holds more than
+leaf_max points (or until the depth cap); leaves t, s interact directly when their
+ancestors at level min(level t, level s) touch or coincide; M2L runs between same-level
+boxes that do not touch and whose parents do.  The restatement below walks the tree with
+dictionaries of integer cells (no Morton keys), and checks on its own lists that every
+ordered point pair is covered exactly once: sum over near leaf pairs of n_t n_s plus the sum
+over M2L pairs of |A| |B| equals N^2.
 """
 import numpy as np
 import pytest
@@ -98,6 +106,20 @@ def _expected(X, leaf_max, orders_of, depth=0):
     out["m2l"] = m2l
     out["m2l_cmacs"] = m2l_cmacs
     out["m2m_l2l_cmacs"] = trans
+    # every ordered point pair exactly once: near leaf pairs plus M2L box pairs
+    cover = 0
+    for l in range(2, L + 1):
+        c, n = lv[l]
+        ek = _enc(c)
+        order = np.argsort(ek)
+        ks = ek[order]
+        for d in offs:
+            s_ = c + d
+            par_ok = np.all(np.abs((s_ >> 1) - (c >> 1)) <= 1, axis=1)
+            j = _lookup(c, ks, order, s_, 2 ** l)
+            ok = par_ok & (j >= 0)
+            cover += int(np.sum(n[ok] * n[j[ok]]))
+    assert pairs + cover == X.shape[0] ** 2
     return out
 
 
@@ -147,5 +169,89 @@ def test_cube_face_points_are_clamped_into_the_last_cell():
         exp = _expected(X, 8, P)
         assert (info["depth"], info["n_leaves"], info["m2l_translations"]) == (exp["depth"], exp["n_leaves"], exp["m2l"])
         assert costs["p2p_pairs"] == exp["near_pairs"] and costs["m2l_cmacs"] == exp["m2l_cmacs"]
+    finally:
+        plan.close()
+
+
+def _adaptive_expected(X, leaf_max, orders_of, maxdepth=20):
+    mn, mx = X.min(0), X.max(0)
+    ext = float(np.max(mx - mn))
+    D = 1.0
+    if ext > 0:
+        while D < ext:
+            D *= 2.0
+        while D * 0.5 >= ext:
+            D *= 0.5
+    lo = 0.5 * (mn + mx) - 0.5 * D
+    q = np.clip(np.floor((X - lo) * (2.0 ** 20 / D)), 0, 2 ** 20 - 1).astype(np.int64)
+    boxes = {}  # (level, cell) -> (point count, is leaf)
+    stack = [(0, (0, 0, 0), np.arange(X.shape[0]))]
+    while stack:
+        l, c, idx = stack.pop()
+        leaf = len(idx) <= leaf_max or l == maxdepth
+        boxes[(l, c)] = (len(idx), leaf)
+        if not leaf:
+            ch = q[idx] >> (20 - (l + 1))
+            keys, inv = np.unique(ch, axis=0, return_inverse=True)
+            for j, kc in enumerate(keys):
+                stack.append((l + 1, tuple(int(v) for v in kc), idx[inv.ravel() == j]))
+    leaves = [(l, c) for (l, c), (n, lf) in boxes.items() if lf]
+    L = max(l for l, _ in leaves)
+    nbr = [(dx, dy, dz) for dx in (-1, 0, 1) for dy in (-1, 0, 1) for dz in (-1, 0, 1)]
+    near = 0
+    for (lt, ct) in leaves:
+        nt = boxes[(lt, ct)][0]
+        hood = 0
+        for m in range(lt + 1):
+            a = tuple(v >> (lt - m) for v in ct)
+            for d in nbr:
+                b = (m, (a[0] + d[0], a[1] + d[1], a[2] + d[2]))
+                if b in boxes:
+                    n, lf = boxes[b]
+                    if lf or m == lt:  # a leaf at its own level, or a split neighbour of t: all its points
+                        hood += n
+        near += nt * hood
+    m2l, cmacs, cover = 0, 0, 0
+    offs = [(dx, dy, dz) for dx in range(-3, 4) for dy in range(-3, 4) for dz in range(-3, 4)
+            if max(abs(dx), abs(dy), abs(dz)) >= 2]
+    for (l, c), (n, _) in boxes.items():
+        if l < 2:
+            continue
+        for d in offs:
+            s_ = (c[0] + d[0], c[1] + d[1], c[2] + d[2])
+            if all(abs((s_[i] >> 1) - (c[i] >> 1)) <= 1 for i in range(3)) and (l, s_) in boxes:
+                m2l += 1
+                cmacs += orders_of(l) ** 2
+                cover += n * boxes[(l, s_)][0]
+    trans = sum(2 * orders_of(l) * orders_of(l - 1) for (l, _) in boxes if l >= 3)
+    N = X.shape[0]
+    assert near + cover == N * N  # every ordered pair exactly once (including i = j, direct)
+    return {"depth": L, "n_leaves": len(leaves), "near_pairs": near - N, "m2l": m2l, "m2l_cmacs": cmacs,
+            "m2m_l2l_cmacs": trans}
+
+
+ADAPTIVE_CASES = [
+    ("cap_sphere_5952_leaf32", lambda: synthetic.refined_cap_sphere(3, 4), 2.0, dict(leaf_max=32, p_fixed=6)),
+    ("ellipsoid_5120_leaf16", lambda: synthetic.ellipsoid_mesh(4), 5.0, dict(leaf_max=16)),
+    ("sphere_5120_leaf40", lambda: synthetic.sphere_mesh(4), 3.0, dict(leaf_max=40)),
+    ("cap_sphere_depth_cap", lambda: synthetic.refined_cap_sphere(2, 5), 1.0, dict(leaf_max=8, depth=4)),
+]
+
+
+@pytest.mark.parametrize("name,mesh,k,kw", ADAPTIVE_CASES, ids=[c[0] for c in ADAPTIVE_CASES])
+def test_adaptive_tree_counts_match_definition(name, mesh, k, kw):
+    V, F = mesh()
+    plan = pkg.Plan(V, F, k, adaptive=1, **kw)
+    try:
+        info, costs = plan.info(), plan.costs()
+        X, _, _ = plan.points()
+        P = lambda l: (info["orders"][l] + 1) ** 2  # noqa: E731
+        exp = _adaptive_expected(X, plan.cfg.leaf_max, P, maxdepth=kw.get("depth", 0) or 20)
+        assert info["depth"] == exp["depth"]
+        assert info["n_leaves"] == exp["n_leaves"]
+        assert info["m2l_translations"] == exp["m2l"]
+        assert costs["p2p_pairs"] == exp["near_pairs"]
+        assert costs["m2l_cmacs"] == exp["m2l_cmacs"]
+        assert costs["m2m_l2l_cmacs"] == exp["m2m_l2l_cmacs"]
     finally:
         plan.close()
