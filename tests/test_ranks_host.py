@@ -44,7 +44,8 @@ def test_max_over_two_gloo_ranks_under_torchrun(tmp_path):
         dist.barrier()
         mx = bench._max_over_ranks(ms, world, device="cpu")
         rate = bench._job_rate(50, world, mx)
-        print(json.dumps({{"rank": rank, "world": world, "local": local, "max": mx, "rate": rate}}), flush=True)
+        with open(os.path.join({str(tmp_path)!r}, f"rank{{rank}}.json"), "w") as f:  # one file per rank
+            json.dump({{"rank": rank, "world": world, "local": local, "max": mx, "rate": rate}}, f)
         dist.destroy_process_group()
     """))
     env = dict(os.environ, PYTHONUNBUFFERED="1")
@@ -52,7 +53,7 @@ def test_max_over_two_gloo_ranks_under_torchrun(tmp_path):
            "--master-addr", "127.0.0.1", "--master-port", str(_free_port()), str(script)]
     r = subprocess.run(cmd, capture_output=True, text=True, timeout=240, env=env, cwd=str(tmp_path))
     assert r.returncode == 0, r.stderr[-2000:]
-    lines = [json.loads(l) for l in r.stdout.splitlines() if l.startswith("{")]
+    lines = [json.loads((tmp_path / f"rank{q}.json").read_text()) for q in range(2)]
     assert sorted(d["rank"] for d in lines) == [0, 1]
     for d in lines:
         assert d["world"] == 2 and d["local"] == d["rank"]
