@@ -218,6 +218,10 @@ def run_refine(args):
         restart = args.restart
     V, F = synthetic.workload_mesh(mesh)
     t0 = time.perf_counter()
+    if args.adaptive:
+        over = dict(over, adaptive=1)
+    if args.leaf_max > 0:
+        over = dict(over, leaf_max=args.leaf_max)
     inner = pkg.Plan(V, F, k, restart=restart, tol=1e-4, **over)
     torch.cuda.synchronize()
     t_in = time.perf_counter() - t0
@@ -339,6 +343,10 @@ def run_batched(args):
     cfg = dict(over)
     if args.simt:
         cfg["m2l_tensor"] = 0
+    if args.adaptive:
+        cfg["adaptive"] = 1
+    if args.leaf_max > 0:
+        cfg["leaf_max"] = args.leaf_max
     V, F = synthetic.workload_mesh(mesh)
     N, R = 3 * F.shape[0], args.nrhs
     stream = torch.cuda.current_stream()
@@ -479,6 +487,9 @@ def main():
     ap.add_argument("--solves", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--simt", action="store_true", help="M2L on FP32 SIMT cores only (the plain form)")
+    ap.add_argument("--leaf-max", type=int, default=0, help="> 0: points per leaf at most (default: the plan's 64)")
+    ap.add_argument("--adaptive", action="store_true",
+                    help="adaptive octree (boxes split only above leaf_max points; leaves at several depths)")
     ap.add_argument("--refine", action="store_true",
                     help="mixed-precision refinement to 1e-6 beside plain GMRES to 1e-4 (default workload: the ellipsoid)")
     ap.add_argument("--refine-pmin", type=int, default=12, help="minimum order of the outer (residual) plan")
@@ -520,6 +531,10 @@ def main():
     cfg["restart"] = restart
     if args.simt:
         cfg["m2l_tensor"] = 0
+    if args.adaptive:
+        cfg["adaptive"] = 1
+    if args.leaf_max > 0:
+        cfg["leaf_max"] = args.leaf_max
     V, F = synthetic.workload_mesh(mesh)
     N = 3 * F.shape[0]
     stream = torch.cuda.current_stream()
@@ -668,6 +683,7 @@ def main():
                        "near_factor": plan.cfg.near_factor, "corr_nnz": info["corr_nnz"],
                        "m2l": "FP32 SIMT" if args.simt else "tcgen05 BF16x3 (levels with (p+1)^2 <= 64), FP32 SIMT above",
                        "m2l_translations": info["m2l_translations"], "device_bytes": info["device_bytes"],
+                       "tree": "adaptive" if args.adaptive else "uniform", "leaves": info["n_leaves"],
                        "parallelism": "replicas" if world > 1 else "single GPU",
                        "l2": f"inputs larger than L2 (plan holds {info['device_bytes'] / 1e9:.2f} GB)"},
             "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99)),

@@ -721,6 +721,155 @@ static bool p2m_l2p_fixed(bool p2m, const hfmm_plan* P, const LevelInfo& lv, Lea
     }
 }
 
+// ============================================================== adaptive W lists (M2P, P2L)
+// Singular functions of an expansion about a box centre, scaled like the translation
+// operators: ht_n = h_n(x) s^(n+1), h_n = j_n + i y_n (n = 0..p).  y_n by its upward
+// recurrence (stable), scaled: yt_{n+1} = (2n+1) s yt_n / x - s^2 yt_{n-1}.
+__device__ void f_hn_scaled(int p, float x, float s, float* hr, float* hi) {
+    float jr[HFMM_PMAX + 1];
+    f_jn_scaled(p, x, s, jr);  // j_n / s^n
+    float sn, cs;
+    sincosf(x, &sn, &cs);
+    const float s2 = s * s, inv = 1.0f / x;
+    hi[0] = -cs * inv * s;
+    if (p >= 1) hi[1] = (-cs * inv * inv - sn * inv) * s2;
+    for (int n = 1; n < p; ++n) hi[n + 1] = (float)(2 * n + 1) * inv * s * hi[n] - s2 * hi[n - 1];
+    float sp = s;
+    for (int n = 0; n <= p; ++n) {
+        hr[n] = jr[n] * sp;  // j_n s^(n+1)
+        sp *= s2;
+    }
+}
+
+// M2P: phi_i += (4 pi i / s_c) sum_nm M_nm(c) ht_n(k r) Y_nm(r^) over the W boxes c of the
+// leaf of sorted point i, r = x_i - centre of c; M is the P2M kernels' multipole
+// (sum_j sig_j jt_n conj Y_nm), so this is sum_j sig_j e^{ikR} / (kR) over c's points.
+__global__ void __launch_bounds__(128) k_m2p(int64_t N, const int32_t* __restrict__ pt_leaf,
+                                             const float4* __restrict__ pts, const int4* __restrict__ leaf_c2,
+                                             const int32_t* __restrict__ w_ptr, const int4* __restrict__ w_c2,
+                                             const int32_t* __restrict__ w_idx, const AdLevel* __restrict__ lev,
+                                             float half_k, const float2* __restrict__ coef,
+                                             float2* __restrict__ phi) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const int32_t b = pt_leaf[i];
+    const int32_t q0 = w_ptr[b], q1 = w_ptr[b + 1];
+    if (q0 == q1) return;
+    const float4 y = pts[i];
+    const int4 lc = leaf_c2[b];
+    float hr[HFMM_PMAX + 1], hi[HFMM_PMAX + 1];
+    float accr = 0.f, acci = 0.f;
+    for (int32_t q = q0; q < q1; ++q) {
+        const int4 c = w_c2[q];
+        const AdLevel lv = lev[c.w];
+        const int p = lv.p, P = (p + 1) * (p + 1);
+        const float2* M = coef + lv.mofs + (int64_t)w_idx[q] * P;
+        const Dir d = make_dir(y.x + (float)(lc.x - c.x) * half_k, y.y + (float)(lc.y - c.y) * half_k,
+                               y.z + (float)(lc.z - c.z) * half_k);
+        f_hn_scaled(p, d.r, lv.s, hr, hi);
+        float sr = 0.f, si = 0.f;  // sum_nm M_nm ht_n Y_nm
+        float stp = 1.f, er = 1.f, ei = 0.f;
+        for (int m = 0; m <= p; ++m) {
+            if (m > 0) {
+                stp *= d.st;
+                const float t = er * d.ex - ei * d.ey;
+                ei = er * d.ey + ei * d.ex;
+                er = t;
+            }
+            const float qmm = c_leg_qmm[m] * stp;
+            float qa = qmm, qb = 0.f;
+            for (int n = m; n <= p; ++n) {
+                float qn = qmm;
+                if (n > m) {
+                    const int h = n * (n + 1) / 2 + m;
+                    qn = (n == m + 1) ? c_leg_a[h] * d.ct * qmm : c_leg_a[h] * (d.ct * qa - c_leg_b[h] * qb);
+                    qb = qa;
+                    qa = qn;
+                }
+                const float br = hr[n] * qn, bi = hi[n] * qn;
+                const float2 mp = __ldg(M + n * n + n + m);  // M_{n,m} e^{+i m phi}
+                const float a = mp.x * er - mp.y * ei, bb = mp.x * ei + mp.y * er;
+                sr += br * a - bi * bb;
+                si += br * bb + bi * a;
+                if (m > 0) {  // M_{n,-m} e^{-i m phi}
+                    const float2 mm = __ldg(M + n * n + n - m);
+                    const float a2 = mm.x * er + mm.y * ei, b2 = mm.y * er - mm.x * ei;
+                    sr += br * a2 - bi * b2;
+                    si += br * b2 + bi * a2;
+                }
+            }
+        }
+        const float f = 12.566370614359172f / lv.s;  // 4 pi / s, times i below
+        accr -= f * si;
+        acci += f * sr;
+    }
+    const float2 o = phi[i];
+    phi[i] = make_float2(o.x + accr, o.y + acci);
+}
+
+// P2L: L_nm(c) += (4 pi i / s_c) sum_j sig_j ht_n(k r_j) conj Y_nm(r_j^) for the points j of
+// the leaf that owns W entry e (block e), r_j = y_j - centre of c; the sums collect in
+// shared memory and reach the locals with one reduction per coefficient.
+__global__ void __launch_bounds__(128) k_p2l(const int32_t* __restrict__ w_leaf, const int4* __restrict__ w_c2,
+                                             const int32_t* __restrict__ w_idx, const AdLevel* __restrict__ lev,
+                                             const int32_t* __restrict__ leaf_start,
+                                             const int4* __restrict__ leaf_c2, const float4* __restrict__ pts,
+                                             const float2* __restrict__ sig, float half_k,
+                                             float2* __restrict__ coef) {
+    extern __shared__ float acc_p2l[];  // [2 P]: Re, Im
+    const int e = blockIdx.x;
+    const int32_t t = w_leaf[e];
+    const int4 c = w_c2[e];
+    const AdLevel lv = lev[c.w];
+    const int p = lv.p, P = (p + 1) * (p + 1);
+    for (int q = threadIdx.x; q < 2 * P; q += blockDim.x) acc_p2l[q] = 0.f;
+    __syncthreads();
+    const int4 lc = leaf_c2[t];
+    float hr[HFMM_PMAX + 1], hi[HFMM_PMAX + 1];
+    for (int32_t j = leaf_start[t] + threadIdx.x; j < leaf_start[t + 1]; j += blockDim.x) {
+        const float4 y = pts[j];
+        const float2 g = sig[j];
+        const Dir d = make_dir(y.x + (float)(lc.x - c.x) * half_k, y.y + (float)(lc.y - c.y) * half_k,
+                               y.z + (float)(lc.z - c.z) * half_k);
+        f_hn_scaled(p, d.r, lv.s, hr, hi);
+        float stp = 1.f, er = 1.f, ei = 0.f;
+        for (int m = 0; m <= p; ++m) {
+            if (m > 0) {
+                stp *= d.st;
+                const float tt = er * d.ex - ei * d.ey;
+                ei = er * d.ey + ei * d.ex;
+                er = tt;
+            }
+            const float qmm = c_leg_qmm[m] * stp;
+            float qa = qmm, qb = 0.f;
+            for (int n = m; n <= p; ++n) {
+                float qn = qmm;
+                if (n > m) {
+                    const int h = n * (n + 1) / 2 + m;
+                    qn = (n == m + 1) ? c_leg_a[h] * d.ct * qmm : c_leg_a[h] * (d.ct * qa - c_leg_b[h] * qb);
+                    qb = qa;
+                    qa = qn;
+                }
+                const float br = hr[n] * qn, bi = hi[n] * qn;
+                const float u = g.x * br - g.y * bi, v = g.x * bi + g.y * br;  // sig ht_n Q
+                const int ip = n * n + n + m;
+                atomicAdd(&acc_p2l[2 * ip], u * er + v * ei);  // times e^{-i m phi}
+                atomicAdd(&acc_p2l[2 * ip + 1], v * er - u * ei);
+                if (m > 0) {  // index (n, -m): times e^{+i m phi}
+                    const int im = n * n + n - m;
+                    atomicAdd(&acc_p2l[2 * im], u * er - v * ei);
+                    atomicAdd(&acc_p2l[2 * im + 1], v * er + u * ei);
+                }
+            }
+        }
+    }
+    __syncthreads();
+    const float f = 12.566370614359172f / lv.s;
+    float2* L = coef + lv.lofs + (int64_t)w_idx[e] * P;
+    for (int q = threadIdx.x; q < P; q += blockDim.x)  // times 4 pi i / s
+        red_add(L + q, make_float2(-f * acc_p2l[2 * q + 1], f * acc_p2l[2 * q]));
+}
+
 // ============================================================== batched translations
 // Out[:, dst] += T * In[:, src] for the column pairs of one work item.
 // 128 threads; a block computes one output tile of 4 * (128 / CG) rows x 4 * CG
@@ -1027,6 +1176,12 @@ void run_matvec_sorted(hfmm_plan* P, int parts, cudaStream_t st) {
             }
             ++P->launches;
         }
+        if (P->adaptive && P->n_w > 0) {  // W lists: the leaf's points into the W boxes' locals
+            k_p2l<<<(unsigned)P->n_w, 128, sizeof(float) * 2 * P->w_maxP, st>>>(
+                P->w_leaf.p, P->w_c2.p, P->w_idx.p, P->ad_lev.p, P->leaf_start.p, P->leaf_ijk.p, P->pts.p, P->sig.p,
+                P->p2p_shift, P->coef.p);
+            ++P->launches;
+        }
     }
     mark_stage(P, 3, st);
     if (far)
@@ -1041,6 +1196,12 @@ void run_matvec_sorted(hfmm_plan* P, int parts, cudaStream_t st) {
                                  HFMM_TRANS_NB, st);
             }
         }
+    if (far && P->adaptive && P->n_w > 0) {  // W lists: the W boxes' multipoles at the leaf's points
+        k_m2p<<<(unsigned)((N + 127) / 128), 128, 0, st>>>(N, P->pt_leaf.p, P->pts.p, P->leaf_ijk.p, P->w_ptr.p,
+                                                           P->w_c2.p, P->w_idx.p, P->ad_lev.p, P->p2p_shift,
+                                                           P->coef.p, P->phi.p);
+        ++P->launches;
+    }
     mark_stage(P, 4, st);
     if (far)
         for (const SimtRange& r : P->m2l_simt)  // high orders: K in 2-3 parts for more blocks in flight

@@ -82,6 +82,13 @@ struct SimtRange {
     int pout_max, width;
 };
 
+// per-level constants the adaptive W-list kernels read on the device
+struct AdLevel {
+    int64_t mofs, lofs;  // this level's multipoles and locals in coef
+    int p;               // order
+    float s;             // scale min(1, k a)
+};
+
 struct LevelInfo {
     int p = 0, P = 0;       // order and (p+1)^2
     double s = 1.0;         // scale min(1, k a)
@@ -150,6 +157,14 @@ struct hfmm_plan {
     DBuf<int32_t> leaf_lev;    // adaptive: level of each leaf
     DBuf<int32_t> leaf_box;    // adaptive: index of each leaf among its level's boxes
     std::vector<int> leaf_levels;  // levels that hold leaves (ascending)
+    // adaptive W lists: for leaf t, entries w_ptr[t] .. w_ptr[t+1] name boxes (centre in half
+    // level-L sides and level in w_c2, index among their level's boxes in w_idx) whose
+    // multipoles are evaluated at t's points, and which take t's points into their locals
+    DBuf<int32_t> w_ptr, w_idx, w_leaf;
+    DBuf<int4> w_c2;
+    DBuf<AdLevel> ad_lev;
+    int64_t n_w = 0;
+    int w_maxP = 0;            // largest (p+1)^2 among the W boxes' levels
     int p2p_maxnbr = 27;       // most source leaves in one leaf's near list
     DBuf<int32_t> nbr_ptr, nbr;
     DBuf<int4> tiles;          // (leaf, first point, count, 0)

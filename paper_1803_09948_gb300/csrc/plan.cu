@@ -218,6 +218,8 @@ static void build_plan(hfmm_plan* P, const double* V, int64_t nv, const int32_t*
     // occupied cell down to the smallest depth whose fullest cell holds <= leaf_max points;
     // adaptive: a box is split only while it holds more than leaf_max points.
     std::vector<HostLevel> lv;
+    std::vector<int32_t> w_ptr, w_idx, w_leaf;  // adaptive W lists (per leaf: box index, owner leaf)
+    std::vector<int4> w_c2;                      // W boxes: centre in half level-L sides, level
     std::vector<uint64_t> leaf_key;
     std::vector<int32_t> leaf_lev, leaf_box, leaf_start;
     int L = 0;
@@ -341,20 +343,44 @@ static void build_plan(hfmm_plan* P, const double* V, int64_t nv, const int32_t*
         tree_leaf_neighbours(d_leafkey.p, P->leaf_start.p, nleaf, L, P->nbr_ptr, P->nbr, nbr_ptr, hood, cnt, st);
         P->p2p_maxnbr = 27;
     } else {
-        // Leaves t, s interact directly when their ancestors at level min(level t, level s)
-        // touch (or coincide); every other pair meets through M2L between two same-level
-        // boxes with touching parents.  For leaf t: (a) the leaves among the 27 neighbours of
-        // each ancestor of t (t included), (b) every leaf under a split neighbour of t.
+        // Adaptive lists of leaf t (the interaction lists of Sec. 2.3 read for leaves at
+        // several depths):
+        //   U: every leaf that touches t, at any level: direct;
+        //   W: the boxes under a split same-level neighbour of t that do not touch t while
+        //      their parents do: their multipoles are evaluated at t's points (M2P) and t's
+        //      points enter their local expansions (P2L, the dual list);
+        // every other pair meets through M2L between same-level boxes that do not touch and
+        // whose parents do.  W boxes need orders <= kWMaxP (the FP32 singular radial
+        // recurrence stays in range); a tree that would need more is refused.
+        constexpr int kWMaxP = 30;
+        bool w_order_ok = true;
+        auto touches = [&](int l1, uint64_t k1, int l2, uint64_t k2) {
+            int64_t a[3], b[3];
+            demorton_h(k1, a);
+            demorton_h(k2, b);
+            const int s1 = L - l1, s2 = L - l2;
+            for (int d = 0; d < 3; ++d)
+                if ((a[d] << s1) > ((b[d] + 1) << s2) || (b[d] << s2) > ((a[d] + 1) << s1)) return false;
+            return true;
+        };
+        auto children = [&](int l, int64_t q, int64_t& c0, int64_t& c1) {
+            const auto& kk = lv[l + 1].key;
+            c0 = std::lower_bound(kk.begin(), kk.end(), lv[l].key[q] << 3) - kk.begin();
+            c1 = std::lower_bound(kk.begin(), kk.end(), (lv[l].key[q] + 1) << 3) - kk.begin();
+        };
         std::vector<int32_t> nbr;
         nbr_ptr.assign(nleaf + 1, 0);
         hood.assign(nleaf, 0);
+        w_ptr.assign(nleaf + 1, 0);
         int maxn = 0;
+        std::vector<std::pair<int, int64_t>> stack;
         for (int64_t t = 0; t < nleaf; ++t) {
             const int lt = leaf_lev[t];
+            const uint64_t kt = leaf_key[t];
             const size_t n0 = nbr.size();
             for (int m = 0; m <= lt; ++m) {
                 int64_t c[3];
-                demorton_h(leaf_key[t] >> (3 * (lt - m)), c);
+                demorton_h(kt >> (3 * (lt - m)), c);
                 const int64_t nl = (int64_t)1 << m;
                 for (int dx = -1; dx <= 1; ++dx)
                     for (int dy = -1; dy <= 1; ++dy)
@@ -364,20 +390,43 @@ static void build_plan(hfmm_plan* P, const double* V, int64_t nv, const int32_t*
                             const int64_t q = find_sorted(lv[m].key, morton_h(x, y, z));
                             if (q < 0) continue;
                             if (lv[m].leaf[q] >= 0) {
-                                nbr.push_back(lv[m].leaf[q]);
-                            } else if (m == lt) {  // split neighbour of t: its leaves are consecutive
-                                const int64_t l0 = std::lower_bound(leaf_start.begin(), leaf_start.end() - 1,
-                                                                    lv[m].start[q]) - leaf_start.begin();
-                                const int64_t l1 = std::lower_bound(leaf_start.begin(), leaf_start.end() - 1,
-                                                                    lv[m].end[q]) - leaf_start.begin();
-                                for (int64_t s2 = l0; s2 < l1; ++s2) nbr.push_back((int32_t)s2);
+                                if (m == lt || touches(m, lv[m].key[q], lt, kt)) nbr.push_back(lv[m].leaf[q]);
+                            } else if (m == lt) {
+                                stack.assign(1, {m, q});
+                                while (!stack.empty()) {
+                                    const auto [l, bq] = stack.back();
+                                    stack.pop_back();
+                                    int64_t c0, c1;
+                                    children(l, bq, c0, c1);
+                                    for (int64_t cq = c0; cq < c1; ++cq) {
+                                        const bool tch = touches(l + 1, lv[l + 1].key[cq], lt, kt);
+                                        if (!tch) {  // boxes of level >= 2 here: level-1 boxes all touch
+                                            w_order_ok = w_order_ok && P->lev[l + 1].p <= kWMaxP;
+                                            int64_t cc[3];
+                                            demorton_h(lv[l + 1].key[cq], cc);
+                                            const int sh = L - (l + 1);
+                                            w_c2.push_back(make_int4((int)((2 * cc[0] + 1) << sh), (int)((2 * cc[1] + 1) << sh),
+                                                                     (int)((2 * cc[2] + 1) << sh), l + 1));
+                                            w_idx.push_back((int32_t)cq);
+                                            w_leaf.push_back((int32_t)t);
+                                        } else if (lv[l + 1].leaf[cq] >= 0) {
+                                            nbr.push_back(lv[l + 1].leaf[cq]);
+                                        } else {
+                                            stack.push_back({l + 1, cq});
+                                        }
+                                    }
+                                }
                             }
                         }
             }
             for (size_t q = n0; q < nbr.size(); ++q) hood[t] += leaf_start[nbr[q] + 1] - leaf_start[nbr[q]];
             nbr_ptr[t + 1] = (int32_t)nbr.size();
+            w_ptr[t + 1] = (int32_t)w_idx.size();
             maxn = std::max(maxn, (int)(nbr.size() - n0));
         }
+        if (!w_order_ok)
+            throw HfmmError{HFMM_E_INVALID, "adaptive tree: leaves of different depths meet where the expansion "
+                                            "order exceeds 30; use the uniform tree (adaptive = 0)"};
         P->nbr_ptr.upload(nbr_ptr, cnt, st);
         P->nbr.upload(nbr, cnt, st);
         P->p2p_maxnbr = maxn;
@@ -432,6 +481,17 @@ static void build_plan(hfmm_plan* P, const double* V, int64_t nv, const int32_t*
         }
         P->coef_total = off;
         P->cost[5] = (double)off;
+        if (P->adaptive) {
+            std::vector<AdLevel> al(L + 1);
+            for (int l = 2; l <= L; ++l) al[l] = AdLevel{P->lev[l].mofs, P->lev[l].lofs, P->lev[l].p, (float)P->lev[l].s};
+            P->ad_lev.upload(al, cnt, st);
+            P->w_ptr.upload(w_ptr, cnt, st);
+            P->w_idx.upload(w_idx, cnt, st);
+            P->w_leaf.upload(w_leaf, cnt, st);
+            P->w_c2.upload(w_c2, cnt, st);
+            P->n_w = (int64_t)w_idx.size();
+            for (const int4& c : w_c2) P->w_maxP = std::max(P->w_maxP, P->lev[c.w].P);
+        }
         int64_t ooff = 0;
         for (int l = 2; l <= L; ++l) {
             int Pl = P->lev[l].P;

@@ -1,11 +1,12 @@
 """Adaptive octree (config adaptive = 1) through the C ABI on a sphere whose cap carries 16
-times the point density of the rest (leaves at two to three depths):
+times the point density of the rest (leaves at two to three depths; the far field uses the
+M2L, M2P and P2L lists):
 
   matvec vs the oracle's FP64 direct sum on sampled rows      1e-4  (p = 8 and 10: the fixed-
                                                                      order and any-order P2M/L2P)
   adaptive vs uniform plan, same orders                         1e-4
-  near field alone vs the oracle's point sum over the same     1e-5  (FP32 P2P; the near lists
-  near lists (restated here from their definition)                    decide which pairs are direct)
+  near field alone vs the oracle's point sum over the leaves   1e-5  (FP32 P2P; the direct pairs
+  touching each target's leaf (restated from the definition)          are exactly these)
   GMRES on the adaptive plan: converges to 1e-4, within 1e-3 of the uniform plan's solution
   three right-hand sides (run one at a time) equal three single matvecs     5e-6  (reduction order)
 """
@@ -72,10 +73,9 @@ def test_adaptive_matvec_against_oracle_rows(cap, p):
         plan.close()
 
 
-def _near_lists(X, leaf_max):
-    """Leaves and the direct pairs of the adaptive tree, from its definition: a box splits
-    while it holds more than leaf_max points; leaves t, s are direct when their ancestors at
-    level min(level t, level s) touch."""
+def _leaves(X, leaf_max):
+    """Leaves of the adaptive tree from its definition (a box splits while it holds more than
+    leaf_max points): each point's leaf, and each leaf's closed box in level-20 units."""
     mn, mx = X.min(0), X.max(0)
     ext = float(np.max(mx - mn))
     D = 1.0
@@ -86,42 +86,39 @@ def _near_lists(X, leaf_max):
     lo = 0.5 * (mn + mx) - 0.5 * D
     q = np.clip(np.floor((X - lo) * (2.0 ** 20 / D)), 0, 2 ** 20 - 1).astype(np.int64)
     leaf_of = np.empty(X.shape[0], dtype=np.int64)
-    leaves = []
+    blo, bhi = [], []
     stack = [(0, np.arange(X.shape[0]))]
     while stack:
         l, idx = stack.pop()
         if len(idx) <= leaf_max:
-            leaf_of[idx] = len(leaves)
-            leaves.append((l, tuple(int(v) for v in q[idx[0]] >> (20 - l))))
+            leaf_of[idx] = len(blo)
+            c = q[idx[0]] >> (20 - l)
+            blo.append(c << (20 - l))
+            bhi.append((c + 1) << (20 - l))
             continue
         ch = q[idx] >> (20 - (l + 1))
         keys, inv = np.unique(ch, axis=0, return_inverse=True)
         for j in range(len(keys)):
             stack.append((l + 1, idx[inv.ravel() == j]))
-    lev = np.array([l for l, _ in leaves])
-    cell = np.array([c for _, c in leaves])
-    return leaf_of, lev, cell
+    return leaf_of, np.array(blo), np.array(bhi)
 
 
 def test_adaptive_near_field_against_point_sum(cap):
-    """parts = 1 (near field only): every target's sum over the sources in its direct leaves,
-    against the oracle's point sum over exactly those sources (checked on sampled targets)."""
+    """parts = 1 (near field only): every target's sum over the points of the leaves that
+    touch its leaf, against the oracle's point sum over exactly those sources (sampled)."""
     V, F, k = cap
     plan = pkg.Plan(V, F, k, adaptive=1, leaf_max=32, p_fixed=8)
     try:
         X, W, _ = plan.points()
         s = synthetic.random_density(plan.n, seed=7)
         got = _mv(plan, s, parts=1)
-        leaf_of, lev, cell = _near_lists(X, 32)
-        assert plan.info()["n_leaves"] == len(lev)
+        leaf_of, blo, bhi = _leaves(X, 32)
+        assert plan.info()["n_leaves"] == len(blo)
         rng = np.random.default_rng(11)
         for i in rng.choice(plan.n, 40, replace=False):
             t = leaf_of[i]
-            m = np.minimum(lev[t], lev)
-            a_t = cell[t][None, :] >> (lev[t] - m)[:, None]
-            a_s = cell >> (lev - m)[:, None]
-            direct = np.all(np.abs(a_t - a_s) <= 1, axis=1)
-            src = np.flatnonzero(direct[leaf_of])
+            touch = np.all((blo[t] <= bhi) & (blo <= bhi[t]), axis=1)
+            src = np.flatnonzero(touch[leaf_of])
             sel = np.concatenate([[i], src[src != i]])
             ref = oracle.point_sum(X[sel], W[sel], k, s[sel])[0]  # target i against its direct sources
             assert abs(got[i] - ref) <= 1e-5 * max(abs(ref), 1e-3 * np.abs(got).max())

@@ -15,12 +15,13 @@ restatement of their definitions (Sec. 2.3 octree and interaction lists; Sec.
 Exact integer equality of every count.
 
 Adaptive trees (config adaptive = 1): a box is split only while it holds more than
-leaf_max points (or until the depth cap); leaves t, s interact directly when their
-ancestors at level min(level t, level s) touch or coincide; M2L runs between same-level
-boxes that do not touch and whose parents do.  The restatement below walks the tree with
-dictionaries of integer cells (no Morton keys), and checks on its own lists that every
-ordered point pair is covered exactly once: sum over near leaf pairs of n_t n_s plus the sum
-over M2L pairs of |A| |B| equals N^2.
+leaf_max points (or until the depth cap); leaves that touch interact directly (U); a box
+that does not touch leaf t while its parent does, under a same-level neighbour of t, meets
+t through M2P and P2L (W and its dual X); M2L runs between same-level boxes that do not
+touch and whose parents do (V).  The restatement below builds the tree with dictionaries of
+integer cells (no Morton keys) and finds the lists by brute force over all boxes, and checks
+on its own lists that every ordered point pair is covered exactly once:
+sum_U n_t n_s + sum_V |A| |B| + 2 sum_W n_t |c| = N^2.
 """
 import numpy as np
 import pytest
@@ -174,6 +175,10 @@ def test_cube_face_points_are_clamped_into_the_last_cell():
 
 
 def _adaptive_expected(X, leaf_max, orders_of, maxdepth=20):
+    """The adaptive tree by brute force over its boxes: U(t) = the leaves touching leaf t;
+    W(t) = the boxes that do not touch t, whose parents do, and that lie under a same-level
+    neighbour of t (M2P to t and P2L from t); V = same-level boxes that do not touch while
+    their parents do (M2L).  Touching is tested on the closed boxes in level-20 units."""
     mn, mx = X.min(0), X.max(0)
     ext = float(np.max(mx - mn))
     D = 1.0
@@ -195,22 +200,31 @@ def _adaptive_expected(X, leaf_max, orders_of, maxdepth=20):
             keys, inv = np.unique(ch, axis=0, return_inverse=True)
             for j, kc in enumerate(keys):
                 stack.append((l + 1, tuple(int(v) for v in kc), idx[inv.ravel() == j]))
-    leaves = [(l, c) for (l, c), (n, lf) in boxes.items() if lf]
-    L = max(l for l, _ in leaves)
-    nbr = [(dx, dy, dz) for dx in (-1, 0, 1) for dy in (-1, 0, 1) for dz in (-1, 0, 1)]
-    near = 0
-    for (lt, ct) in leaves:
-        nt = boxes[(lt, ct)][0]
-        hood = 0
-        for m in range(lt + 1):
-            a = tuple(v >> (lt - m) for v in ct)
-            for d in nbr:
-                b = (m, (a[0] + d[0], a[1] + d[1], a[2] + d[2]))
-                if b in boxes:
-                    n, lf = boxes[b]
-                    if lf or m == lt:  # a leaf at its own level, or a split neighbour of t: all its points
-                        hood += n
-        near += nt * hood
+    items = list(boxes.items())
+    lev = np.array([l for (l, _), _ in items])
+    cell = np.array([c for (_, c), _ in items], dtype=np.int64)
+    npt = np.array([n for _, (n, _) in items], dtype=np.int64)
+    isleaf = np.array([lf for _, (_, lf) in items])
+    span = np.left_shift(1, 20 - lev)
+    blo = cell * span[:, None]
+    bhi = (cell + 1) * span[:, None]
+    plo = (cell >> 1) * (2 * span)[:, None]
+    phi_ = ((cell >> 1) + 1) * (2 * span)[:, None]
+
+    def touch(lo1, hi1, lo2, hi2):
+        return np.all((lo1 <= hi2) & (lo2 <= hi1), axis=-1)
+
+    L = int(lev[isleaf].max())
+    near = wcov = 0
+    for t in np.flatnonzero(isleaf):
+        lt = lev[t]
+        tu = touch(blo[t], bhi[t], blo, bhi)
+        near += npt[t] * int(np.sum(npt[tu & isleaf]))
+        deeper = lev > lt
+        anc = cell >> np.maximum(lev - lt, 0)[:, None]
+        under_nbr = deeper & np.all(np.abs(anc - cell[t]) <= 1, axis=1)
+        w = under_nbr & ~tu & touch(blo[t], bhi[t], plo, phi_)
+        wcov += 2 * npt[t] * int(np.sum(npt[w]))
     m2l, cmacs, cover = 0, 0, 0
     offs = [(dx, dy, dz) for dx in range(-3, 4) for dy in range(-3, 4) for dz in range(-3, 4)
             if max(abs(dx), abs(dy), abs(dz)) >= 2]
@@ -225,8 +239,8 @@ def _adaptive_expected(X, leaf_max, orders_of, maxdepth=20):
                 cover += n * boxes[(l, s_)][0]
     trans = sum(2 * orders_of(l) * orders_of(l - 1) for (l, _) in boxes if l >= 3)
     N = X.shape[0]
-    assert near + cover == N * N  # every ordered pair exactly once (including i = j, direct)
-    return {"depth": L, "n_leaves": len(leaves), "near_pairs": near - N, "m2l": m2l, "m2l_cmacs": cmacs,
+    assert near + cover + wcov == N * N  # every ordered pair exactly once (i = j counted as direct)
+    return {"depth": L, "n_leaves": int(isleaf.sum()), "near_pairs": near - N, "m2l": m2l, "m2l_cmacs": cmacs,
             "m2m_l2l_cmacs": trans}
 
 
