@@ -34,6 +34,7 @@ WORKLOADS = {
     "sphere_40960": ("sphere_40960", 10.0, {}, 50),
     # GMRES(50) stagnates near 5e-4 on this body at k = 30; GMRES(200) converges
     "ellipsoid_1310720": ("ellipsoid_1310720", 30.0, {}, 200),
+    "cap_sphere_387864": ("cap_sphere_387864", 10.0, {}, 50),
 }
 
 

@@ -808,67 +808,87 @@ __global__ void __launch_bounds__(128) k_m2p(int64_t N, const int32_t* __restric
 }
 
 // P2L: L_nm(c) += (4 pi i / s_c) sum_j sig_j ht_n(k r_j) conj Y_nm(r_j^) for the points j of
-// the leaf that owns W entry e (block e), r_j = y_j - centre of c; the sums collect in
-// shared memory and reach the locals with one reduction per coefficient.
+// the leaf that owns W entry e (block e), r_j = y_j - centre of c.  The leaf's points are
+// taken in chunks: thread j writes its point's row sig_j ht_n Q_n^|m| e^{-/+ i m phi} (P
+// values, row stride P + 1) into shared memory, then thread q sums coefficient q over the
+// chunk; one reduction per coefficient reaches the locals.
+constexpr int kP2LMaxPerThread = 8;  // coefficients per thread: P <= 8 * 128 (orders <= 30)
 __global__ void __launch_bounds__(128) k_p2l(const int32_t* __restrict__ w_leaf, const int4* __restrict__ w_c2,
                                              const int32_t* __restrict__ w_idx, const AdLevel* __restrict__ lev,
                                              const int32_t* __restrict__ leaf_start,
                                              const int4* __restrict__ leaf_c2, const float4* __restrict__ pts,
-                                             const float2* __restrict__ sig, float half_k,
+                                             const float2* __restrict__ sig, float half_k, int chunk,
                                              float2* __restrict__ coef) {
-    extern __shared__ float acc_p2l[];  // [2 P]: Re, Im
+    extern __shared__ float2 rows_p2l[];  // [chunk][P + 1]
     const int e = blockIdx.x;
     const int32_t t = w_leaf[e];
     const int4 c = w_c2[e];
     const AdLevel lv = lev[c.w];
-    const int p = lv.p, P = (p + 1) * (p + 1);
-    for (int q = threadIdx.x; q < 2 * P; q += blockDim.x) acc_p2l[q] = 0.f;
-    __syncthreads();
+    const int p = lv.p, P = (p + 1) * (p + 1), stride = P + 1;
     const int4 lc = leaf_c2[t];
+    const int32_t j0 = leaf_start[t], j1 = leaf_start[t + 1];
+    float2 acc[kP2LMaxPerThread];
+#pragma unroll
+    for (int u = 0; u < kP2LMaxPerThread; ++u) acc[u] = make_float2(0.f, 0.f);
     float hr[HFMM_PMAX + 1], hi[HFMM_PMAX + 1];
-    for (int32_t j = leaf_start[t] + threadIdx.x; j < leaf_start[t + 1]; j += blockDim.x) {
-        const float4 y = pts[j];
-        const float2 g = sig[j];
-        const Dir d = make_dir(y.x + (float)(lc.x - c.x) * half_k, y.y + (float)(lc.y - c.y) * half_k,
-                               y.z + (float)(lc.z - c.z) * half_k);
-        f_hn_scaled(p, d.r, lv.s, hr, hi);
-        float stp = 1.f, er = 1.f, ei = 0.f;
-        for (int m = 0; m <= p; ++m) {
-            if (m > 0) {
-                stp *= d.st;
-                const float tt = er * d.ex - ei * d.ey;
-                ei = er * d.ey + ei * d.ex;
-                er = tt;
-            }
-            const float qmm = c_leg_qmm[m] * stp;
-            float qa = qmm, qb = 0.f;
-            for (int n = m; n <= p; ++n) {
-                float qn = qmm;
-                if (n > m) {
-                    const int h = n * (n + 1) / 2 + m;
-                    qn = (n == m + 1) ? c_leg_a[h] * d.ct * qmm : c_leg_a[h] * (d.ct * qa - c_leg_b[h] * qb);
-                    qb = qa;
-                    qa = qn;
+    for (int32_t jb = j0; jb < j1; jb += chunk) {
+        const int cnt = min(chunk, j1 - jb);
+        __syncthreads();  // the previous chunk's rows are summed
+        for (int jj = threadIdx.x; jj < cnt; jj += blockDim.x) {
+            const float4 y = pts[jb + jj];
+            const float2 g = sig[jb + jj];
+            float2* row = rows_p2l + jj * stride;
+            const Dir d = make_dir(y.x + (float)(lc.x - c.x) * half_k, y.y + (float)(lc.y - c.y) * half_k,
+                                   y.z + (float)(lc.z - c.z) * half_k);
+            f_hn_scaled(p, d.r, lv.s, hr, hi);
+            float stp = 1.f, er = 1.f, ei = 0.f;
+            for (int m = 0; m <= p; ++m) {
+                if (m > 0) {
+                    stp *= d.st;
+                    const float tt = er * d.ex - ei * d.ey;
+                    ei = er * d.ey + ei * d.ex;
+                    er = tt;
                 }
-                const float br = hr[n] * qn, bi = hi[n] * qn;
-                const float u = g.x * br - g.y * bi, v = g.x * bi + g.y * br;  // sig ht_n Q
-                const int ip = n * n + n + m;
-                atomicAdd(&acc_p2l[2 * ip], u * er + v * ei);  // times e^{-i m phi}
-                atomicAdd(&acc_p2l[2 * ip + 1], v * er - u * ei);
-                if (m > 0) {  // index (n, -m): times e^{+i m phi}
-                    const int im = n * n + n - m;
-                    atomicAdd(&acc_p2l[2 * im], u * er - v * ei);
-                    atomicAdd(&acc_p2l[2 * im + 1], v * er + u * ei);
+                const float qmm = c_leg_qmm[m] * stp;
+                float qa = qmm, qb = 0.f;
+                for (int n = m; n <= p; ++n) {
+                    float qn = qmm;
+                    if (n > m) {
+                        const int h = n * (n + 1) / 2 + m;
+                        qn = (n == m + 1) ? c_leg_a[h] * d.ct * qmm : c_leg_a[h] * (d.ct * qa - c_leg_b[h] * qb);
+                        qb = qa;
+                        qa = qn;
+                    }
+                    const float br = hr[n] * qn, bi = hi[n] * qn;
+                    const float u = g.x * br - g.y * bi, v = g.x * bi + g.y * br;  // sig ht_n Q
+                    row[n * n + n + m] = make_float2(u * er + v * ei, v * er - u * ei);  // e^{-i m phi}
+                    if (m > 0) row[n * n + n - m] = make_float2(u * er - v * ei, v * er + u * ei);  // e^{+i m phi}
                 }
             }
         }
+        __syncthreads();
+#pragma unroll
+        for (int u = 0; u < kP2LMaxPerThread; ++u) {
+            const int q = threadIdx.x + u * blockDim.x;
+            if (q < P)
+                for (int jj = 0; jj < cnt; ++jj) {
+                    const float2 r = rows_p2l[jj * stride + q];
+                    acc[u].x += r.x;
+                    acc[u].y += r.y;
+                }
+        }
     }
-    __syncthreads();
     const float f = 12.566370614359172f / lv.s;
     float2* L = coef + lv.lofs + (int64_t)w_idx[e] * P;
-    for (int q = threadIdx.x; q < P; q += blockDim.x)  // times 4 pi i / s
-        red_add(L + q, make_float2(-f * acc_p2l[2 * q + 1], f * acc_p2l[2 * q]));
+#pragma unroll
+    for (int u = 0; u < kP2LMaxPerThread; ++u) {  // times 4 pi i / s
+        const int q = threadIdx.x + u * blockDim.x;
+        if (q < P) red_add(L + q, make_float2(-f * acc[u].y, f * acc[u].x));
+    }
 }
+
+// rows of the chunk that fit 24 KiB of shared memory
+static int p2l_chunk(int P) { return std::max(1, std::min(32, 24576 / (8 * (P + 1)))); }
 
 // ============================================================== batched translations
 // Out[:, dst] += T * In[:, src] for the column pairs of one work item.
@@ -1177,9 +1197,10 @@ void run_matvec_sorted(hfmm_plan* P, int parts, cudaStream_t st) {
             ++P->launches;
         }
         if (P->adaptive && P->n_w > 0) {  // W lists: the leaf's points into the W boxes' locals
-            k_p2l<<<(unsigned)P->n_w, 128, sizeof(float) * 2 * P->w_maxP, st>>>(
+            const int chunk = p2l_chunk(P->w_maxP);
+            k_p2l<<<(unsigned)P->n_w, 128, sizeof(float2) * chunk * (P->w_maxP + 1), st>>>(
                 P->w_leaf.p, P->w_c2.p, P->w_idx.p, P->ad_lev.p, P->leaf_start.p, P->leaf_ijk.p, P->pts.p, P->sig.p,
-                P->p2p_shift, P->coef.p);
+                P->p2p_shift, chunk, P->coef.p);
             ++P->launches;
         }
     }

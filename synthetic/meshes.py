@@ -239,6 +239,10 @@ WORKLOADS = {
     "sphere_655360": ("unit sphere, icosphere level 7 + longest-edge bisection", lambda: sphere_mesh(7, True)),
     # 20 * 4**8 = 1,310,720 triangles -> N = 3,932,160 points
     "ellipsoid_1310720": ("ellipsoid (2,1,1), icosphere level 8", lambda: ellipsoid_mesh(8)),
+    # icosphere level 6 with the cap z > 0.5 bisected 4 more times (16x the point density):
+    # 387,864 triangles -> N = 1,163,592 points, the non-uniform case for the adaptive tree
+    "cap_sphere_387864": ("unit sphere, icosphere level 6, cap z > 0.5 refined 4 more times",
+                         lambda: refined_cap_sphere(6, 4)),
 }
 
 
