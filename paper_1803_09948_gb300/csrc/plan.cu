@@ -350,8 +350,10 @@ static void build_plan(hfmm_plan* P, const double* V, int64_t nv, const int32_t*
         //      their parents do: their multipoles are evaluated at t's points (M2P) and t's
         //      points enter their local expansions (P2L, the dual list);
         // every other pair meets through M2L between same-level boxes that do not touch and
-        // whose parents do.  W boxes need orders <= kWMaxP (the FP32 singular radial
-        // recurrence stays in range); a tree that would need more is refused.
+        // whose parents do.  A W box holding no more points than its expansion has terms is
+        // cheaper summed directly, both ways: its leaves join U(t) and t joins theirs.  W boxes
+        // need orders <= kWMaxP (the FP32 singular radial recurrence stays in range); a tree
+        // that would need more is refused.
         constexpr int kWMaxP = 30;
         bool w_order_ok = true;
         auto touches = [&](int l1, uint64_t k1, int l2, uint64_t k2) {
@@ -374,6 +376,7 @@ static void build_plan(hfmm_plan* P, const double* V, int64_t nv, const int32_t*
         w_ptr.assign(nleaf + 1, 0);
         int maxn = 0;
         std::vector<std::pair<int, int64_t>> stack;
+        std::vector<std::pair<int32_t, int32_t>> rev;  // (target leaf, source leaf) added from the source's side
         for (int64_t t = 0; t < nleaf; ++t) {
             const int lt = leaf_lev[t];
             const uint64_t kt = leaf_key[t];
@@ -400,7 +403,17 @@ static void build_plan(hfmm_plan* P, const double* V, int64_t nv, const int32_t*
                                     children(l, bq, c0, c1);
                                     for (int64_t cq = c0; cq < c1; ++cq) {
                                         const bool tch = touches(l + 1, lv[l + 1].key[cq], lt, kt);
-                                        if (!tch) {  // boxes of level >= 2 here: level-1 boxes all touch
+                                        const int64_t npts = lv[l + 1].end[cq] - lv[l + 1].start[cq];
+                                        if (!tch && npts <= P->lev[l + 1].P) {  // small W box: direct
+                                            const int64_t l0 = std::lower_bound(leaf_start.begin(), leaf_start.end() - 1,
+                                                                                lv[l + 1].start[cq]) - leaf_start.begin();
+                                            const int64_t l1 = std::lower_bound(leaf_start.begin(), leaf_start.end() - 1,
+                                                                                lv[l + 1].end[cq]) - leaf_start.begin();
+                                            for (int64_t s2 = l0; s2 < l1; ++s2) {
+                                                nbr.push_back((int32_t)s2);
+                                                rev.push_back({(int32_t)s2, (int32_t)t});
+                                            }
+                                        } else if (!tch) {  // boxes of level >= 2 here: level-1 boxes all touch
                                             w_order_ok = w_order_ok && P->lev[l + 1].p <= kWMaxP;
                                             int64_t cc[3];
                                             demorton_h(lv[l + 1].key[cq], cc);
@@ -419,10 +432,28 @@ static void build_plan(hfmm_plan* P, const double* V, int64_t nv, const int32_t*
                             }
                         }
             }
-            for (size_t q = n0; q < nbr.size(); ++q) hood[t] += leaf_start[nbr[q] + 1] - leaf_start[nbr[q]];
             nbr_ptr[t + 1] = (int32_t)nbr.size();
             w_ptr[t + 1] = (int32_t)w_idx.size();
-            maxn = std::max(maxn, (int)(nbr.size() - n0));
+        }
+        {  // merge the pairs added from the source's side into the targets' lists
+            std::stable_sort(rev.begin(), rev.end(),
+                             [](const std::pair<int32_t, int32_t>& a, const std::pair<int32_t, int32_t>& b) {
+                                 return a.first < b.first;
+                             });
+            std::vector<int32_t> merged, mptr(nleaf + 1, 0);
+            merged.reserve(nbr.size() + rev.size());
+            size_t r = 0;
+            for (int64_t t = 0; t < nleaf; ++t) {
+                merged.insert(merged.end(), nbr.begin() + nbr_ptr[t], nbr.begin() + nbr_ptr[t + 1]);
+                for (; r < rev.size() && rev[r].first == t; ++r) merged.push_back(rev[r].second);
+                mptr[t + 1] = (int32_t)merged.size();
+            }
+            nbr.swap(merged);
+            nbr_ptr.swap(mptr);
+            for (int64_t t = 0; t < nleaf; ++t) {
+                for (int32_t q = nbr_ptr[t]; q < nbr_ptr[t + 1]; ++q) hood[t] += leaf_start[nbr[q] + 1] - leaf_start[nbr[q]];
+                maxn = std::max(maxn, nbr_ptr[t + 1] - nbr_ptr[t]);
+            }
         }
         if (!w_order_ok)
             throw HfmmError{HFMM_E_INVALID, "adaptive tree: leaves of different depths meet where the expansion "

@@ -21,7 +21,8 @@ t through M2P and P2L (W and its dual X); M2L runs between same-level boxes that
 touch and whose parents do (V).  The restatement below builds the tree with dictionaries of
 integer cells (no Morton keys) and finds the lists by brute force over all boxes, and checks
 on its own lists that every ordered point pair is covered exactly once:
-sum_U n_t n_s + sum_V |A| |B| + 2 sum_W n_t |c| = N^2.
+sum_U n_t n_s + sum_V |A| |B| + 2 sum_W n_t |c| = N^2 (W boxes with no more points than
+expansion terms are summed directly, both ways, and count in U).
 """
 import numpy as np
 import pytest
@@ -177,8 +178,9 @@ def test_cube_face_points_are_clamped_into_the_last_cell():
 def _adaptive_expected(X, leaf_max, orders_of, maxdepth=20):
     """The adaptive tree by brute force over its boxes: U(t) = the leaves touching leaf t;
     W(t) = the boxes that do not touch t, whose parents do, and that lie under a same-level
-    neighbour of t (M2P to t and P2L from t); V = same-level boxes that do not touch while
-    their parents do (M2L).  Touching is tested on the closed boxes in level-20 units."""
+    neighbour of t (M2P to t and P2L from t), except that a W box holding no more points than
+    its expansion has terms is summed directly both ways; V = same-level boxes that do not
+    touch while their parents do (M2L).  Touching: closed boxes in level-20 units."""
     mn, mx = X.min(0), X.max(0)
     ext = float(np.max(mx - mn))
     D = 1.0
@@ -215,6 +217,7 @@ def _adaptive_expected(X, leaf_max, orders_of, maxdepth=20):
         return np.all((lo1 <= hi2) & (lo2 <= hi1), axis=-1)
 
     L = int(lev[isleaf].max())
+    Pl = np.array([orders_of(int(l)) if l >= 2 else 0 for l in lev])
     near = wcov = 0
     for t in np.flatnonzero(isleaf):
         lt = lev[t]
@@ -224,7 +227,9 @@ def _adaptive_expected(X, leaf_max, orders_of, maxdepth=20):
         anc = cell >> np.maximum(lev - lt, 0)[:, None]
         under_nbr = deeper & np.all(np.abs(anc - cell[t]) <= 1, axis=1)
         w = under_nbr & ~tu & touch(blo[t], bhi[t], plo, phi_)
-        wcov += 2 * npt[t] * int(np.sum(npt[w]))
+        small = w & (npt <= Pl)  # fewer points than expansion terms: direct, both ways
+        near += 2 * npt[t] * int(np.sum(npt[small]))
+        wcov += 2 * npt[t] * int(np.sum(npt[w & ~small]))
     m2l, cmacs, cover = 0, 0, 0
     offs = [(dx, dy, dz) for dx in range(-3, 4) for dy in range(-3, 4) for dz in range(-3, 4)
             if max(abs(dx), abs(dy), abs(dz)) >= 2]
