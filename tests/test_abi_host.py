@@ -39,6 +39,7 @@ def test_default_config_and_status_strings():
     c = pkg.hfmm_default_config()
     assert c.leaf_max == 64 and c.restart == 30 and abs(c.tol - 1e-4) < 1e-18
     assert c.near_factor == 1.0 and c.p_min == 7
+    assert c.m2l_tensor == 1 and c.adaptive == 0  # tensor-core M2L, uniform tree
     for s in [0, 1, -1, -2, -3, -4, -5, -6]:
         assert pkg.hfmm_status_string(s) != "unknown status"
     assert pkg.hfmm_status_string(12345) == "unknown status"
@@ -61,6 +62,8 @@ def test_invalid_arguments_are_rejected_on_the_host():
     assert _create(V, F, p_fixed=99)[0] == pkg.HFMM_E_INVALID
     assert _create(V, F, tol=0.0)[0] == pkg.HFMM_E_INVALID
     assert _create(V, F, quad_order=1)[0] == pkg.HFMM_E_INVALID
+    assert _create(V, F, adaptive=2)[0] == pkg.HFMM_E_INVALID
+    assert _create(V, F, m2l_tensor=-1)[0] == pkg.HFMM_E_INVALID
     assert _create(V[:0], F)[0] == pkg.HFMM_E_INVALID          # no vertices
     assert _create(V, F[:0])[0] == pkg.HFMM_E_INVALID          # N = 0
     st, out = _create(V, F, k=0.0)
