@@ -2,9 +2,10 @@
 //
 // One matvec (Sec. 2.3 and the Nystrom operator of Sec. 2.2):
 //   density prep   sh_i = k w_i s_perm(i) / (4 pi)  (Morton order)
-//   near field     phi_i  = sum_{j in neighbour leaves, j != i} sh_j (C(u)/sqrt(u) + i S(u)),
+//   near field     phi_i  = sum_{j in direct leaves, j != i} sh_j (C(u)/sqrt(u) + i S(u)),
 //                  u = (k R_ij)^2   [= w_j s_j exp(ikR)/(4 pi R), Eq. 6; Listing 1's P2P]
-//   far field      P2M -> M2M -> M2L -> L2L -> L2P   (Eq. 11-14)
+//   far field      P2M -> M2M -> M2L -> L2L -> L2P   (Eq. 11-14); an adaptive tree adds
+//                  P2L after P2M and M2P after M2M for its W lists
 //   correction     phi_i += sum_j C~_ij sh_j  (exact self/near integrals minus point terms)
 //   output         potential[perm(i)] = phi_i
 #include <algorithm>

@@ -1,11 +1,13 @@
 // Plan construction (host orchestration) and the C ABI entry points.
 //
-// A plan holds, on the device: Morton-sorted points and weights, the uniform
-// octree (leaves, neighbour lists, interaction lists grouped by translation
-// offset), all translation operators, and the sparse self/near correction.
-// The sort, the per-point leaf data, the neighbour and interaction lists, the
-// operators and the correction are built by device kernels; the host keeps the
-// per-level box tables and turns the lists into work items.
+// A plan holds, on the device: Morton-sorted points and weights, the octree
+// (leaves, neighbour lists, interaction lists grouped by translation offset), all
+// translation operators, and the sparse self/near correction.  The octree is uniform
+// (every leaf at the smallest depth that holds leaf_max points) or, with the adaptive
+// option, split box by box with U / V / W / X lists for leaves of unequal depth.
+// The sort, the per-point leaf data, the neighbour and interaction lists of a uniform
+// tree, the operators and the correction are built by device kernels; the host keeps
+// the per-level box tables, builds the adaptive lists, and turns lists into work items.
 // Sec. 2.2 (discretisation, singular treatment), Sec. 2.3 (octree, sweeps),
 // Sec. 3.1-3.2 (Morton order, cell = index + count).
 #include <algorithm>
