@@ -46,7 +46,11 @@ def lib():
         L.or_correction_csr.restype = ctypes.c_int64
         L.or_direct_rows.argtypes = [_dp, _i32p, ctypes.c_int64, ctypes.c_double, ctypes.c_double,
                                      _i64p, ctypes.c_int64, _dp, _dp, ctypes.c_int]
+        L.or_direct_rows.restype = ctypes.c_int
         L.or_dense_Z.argtypes = [_dp, _i32p, ctypes.c_int64, ctypes.c_double, ctypes.c_double, _dp]
+        L.or_dense_Z.restype = ctypes.c_int
+        L.or_near_sets.argtypes = [_dp, _i32p, ctypes.c_int64, ctypes.c_double, _i64p, _i32p]
+        L.or_near_sets.restype = ctypes.c_int64
         L.or_point_sum.argtypes = [_dp, _dp, ctypes.c_int64, ctypes.c_double, _dp, _dp]
         L.or_fmm.argtypes = [_dp, _dp, ctypes.c_int64, ctypes.c_double, ctypes.c_int, ctypes.c_int,
                              ctypes.c_int, ctypes.c_int, _dp, _dp, ctypes.c_int, _ip]
@@ -97,6 +101,26 @@ def near_radius(V, F, near_factor):
     return near_factor * mean_edge(V, F)
 
 
+class NearSetOverflow(RuntimeError):
+    """A near set S(i) has more candidates than the oracle's fixed table holds."""
+
+
+def near_sets(V, F, r_near):
+    """S(i) for every point i: (ptr [N+1], idx) with idx[ptr[i]:ptr[i+1]] the sorted
+    ids of the own triangle and of every triangle with a point within r_near of x_i."""
+    V, F = _mesh(V, F)
+    nt = F.shape[0]
+    ptr = np.zeros(3 * nt + 1, dtype=np.int64)
+    tot = lib().or_near_sets(_d(V), F.ctypes.data_as(_i32p), nt, float(r_near),
+                             ptr.ctypes.data_as(_i64p), None)
+    if tot < 0:
+        raise NearSetOverflow("a near set exceeds the oracle's capacity; lower r_near")
+    idx = np.empty(max(tot, 1), dtype=np.int32)
+    lib().or_near_sets(_d(V), F.ctypes.data_as(_i32p), nt, float(r_near), ptr.ctypes.data_as(_i64p),
+                       idx.ctypes.data_as(_i32p))
+    return ptr, idx[:tot]
+
+
 def tri_potential_1overR(x, v):
     x, v = _f64(x), _f64(v).reshape(9)
     I0 = np.zeros(1)
@@ -123,10 +147,13 @@ def correction_csr(V, F, k, r_near):
     rowptr = np.zeros(N + 1, dtype=np.int64)
     nnz = lib().or_correction_csr(_d(V), F.ctypes.data_as(_i32p), nt, float(k), float(r_near),
                                   rowptr.ctypes.data_as(_i64p), None, None)
+    if nnz < 0:
+        raise NearSetOverflow("a near set exceeds the oracle's capacity; lower r_near")
     col = np.empty(max(nnz, 1), dtype=np.int64)
     val = np.empty(2 * max(nnz, 1))
-    lib().or_correction_csr(_d(V), F.ctypes.data_as(_i32p), nt, float(k), float(r_near),
-                            rowptr.ctypes.data_as(_i64p), col.ctypes.data_as(_i64p), _d(val))
+    if lib().or_correction_csr(_d(V), F.ctypes.data_as(_i32p), nt, float(k), float(r_near),
+                               rowptr.ctypes.data_as(_i64p), col.ctypes.data_as(_i64p), _d(val)) < 0:
+        raise NearSetOverflow("a near set exceeds the oracle's capacity; lower r_near")
     v = val[0:2 * nnz:2] + 1j * val[1:2 * nnz:2]
     return sp.csr_matrix((v, col[:nnz], rowptr), shape=(N, N))
 
@@ -137,8 +164,9 @@ def direct_rows(V, F, k, r_near, rows, sigma, mode=3):
     rows = np.ascontiguousarray(rows, dtype=np.int64)
     s = _c128(sigma).view(np.float64)
     out = np.zeros(2 * rows.size)
-    lib().or_direct_rows(_d(V), F.ctypes.data_as(_i32p), F.shape[0], float(k), float(r_near),
-                         rows.ctypes.data_as(_i64p), rows.size, _d(s), _d(out), int(mode))
+    if lib().or_direct_rows(_d(V), F.ctypes.data_as(_i32p), F.shape[0], float(k), float(r_near),
+                            rows.ctypes.data_as(_i64p), rows.size, _d(s), _d(out), int(mode)) < 0:
+        raise NearSetOverflow("a near set exceeds the oracle's capacity; lower r_near")
     return out[0::2] + 1j * out[1::2]
 
 
@@ -151,8 +179,9 @@ def dense_Z(V, F, k, r_near):
     V, F = _mesh(V, F)
     N = 3 * F.shape[0]
     Z = np.zeros((N, N), dtype=np.complex128)
-    lib().or_dense_Z(_d(V), F.ctypes.data_as(_i32p), F.shape[0], float(k), float(r_near),
-                     _d(Z.view(np.float64)))
+    if lib().or_dense_Z(_d(V), F.ctypes.data_as(_i32p), F.shape[0], float(k), float(r_near),
+                        _d(Z.view(np.float64))) < 0:
+        raise NearSetOverflow("a near set exceeds the oracle's capacity; lower r_near")
     return Z
 
 

@@ -443,7 +443,12 @@ static int cmp_i32(const void* a, const void* b) {
     return (x > y) - (x < y);
 }
 
-/* collects the sorted, unique near triangles of point i into out (cap entries) */
+/*
+ * Collects the sorted, unique triangles of S(i) (own triangle, plus every
+ * triangle with a point within r_near of x_i) into out.  Returns their number,
+ * or -1 when the candidate list would exceed cap entries: the set is then
+ * refused, never truncated.
+ */
 static int near_tris_of(const grid_t* g, const double* X, const int32_t* T, int64_t i,
                         double r_near, int32_t* out, int cap) {
     int cnt = 0;
@@ -463,7 +468,10 @@ static int near_tris_of(const grid_t* g, const double* X, const int32_t* T, int6
                     int64_t j = g->order[s];
                     double d[3];
                     v_sub(X + 3 * i, X + 3 * j, d);
-                    if (v_dot(d, d) <= r2 && cnt < cap) out[cnt++] = T[j];
+                    if (v_dot(d, d) <= r2) {
+                        if (cnt >= cap) return -1;
+                        out[cnt++] = T[j];
+                    }
                 }
             }
     qsort(out, (size_t)cnt, sizeof(int32_t), cmp_i32);
@@ -480,6 +488,8 @@ static int near_tris_of(const grid_t* g, const double* X, const int32_t* T, int6
  * (rows and columns are point indices 3n+a; Z_point_ij = w_j G(x_i,x_j), 0 on
  * the diagonal).  Call once with col == NULL to get row counts in rowptr[1..N]
  * (rowptr[0] = 0 and the prefix sum are filled in), then again with storage.
+ * Returns the number of nonzeros, or -1 if some near set exceeds NEAR_CAP
+ * candidate entries (the matrix is then incomplete and must not be used).
  */
 int64_t or_correction_csr(const double* V, const int32_t* F, int64_t nt, double k, double r_near,
                           int64_t* rowptr, int64_t* col, double* val_ri) {
@@ -490,12 +500,18 @@ int64_t or_correction_csr(const double* V, const int32_t* F, int64_t nt, double 
     or_points(V, F, nt, X, W, T);
     grid_t g;
     grid_build(&g, X, N, r_near);
+    int overflow = 0;
     if (col == NULL) {
         rowptr[0] = 0;
 #pragma omp parallel for schedule(dynamic, 64)
         for (int64_t i = 0; i < N; ++i) {
             int32_t buf[NEAR_CAP];
             int c = near_tris_of(&g, X, T, i, r_near, buf, NEAR_CAP);
+            if (c < 0) {
+#pragma omp atomic write
+                overflow = 1;
+                c = 0;
+            }
             rowptr[i + 1] = 3 * (int64_t)c;
         }
         for (int64_t i = 0; i < N; ++i) rowptr[i + 1] += rowptr[i];
@@ -504,6 +520,11 @@ int64_t or_correction_csr(const double* V, const int32_t* F, int64_t nt, double 
         for (int64_t i = 0; i < N; ++i) {
             int32_t buf[NEAR_CAP];
             int c = near_tris_of(&g, X, T, i, r_near, buf, NEAR_CAP);
+            if (c < 0) {
+#pragma omp atomic write
+                overflow = 1;
+                continue;
+            }
             int64_t o = rowptr[i];
             for (int q = 0; q < c; ++q) {
                 int64_t n = buf[q];
@@ -532,7 +553,7 @@ int64_t or_correction_csr(const double* V, const int32_t* F, int64_t nt, double 
     free(X);
     free(W);
     free(T);
-    return rowptr[N];
+    return overflow ? -1 : rowptr[N];
 }
 
 /*
@@ -540,9 +561,10 @@ int64_t or_correction_csr(const double* V, const int32_t* F, int64_t nt, double 
  * rows: nrows point indices; sigma: N complex (interleaved); out: nrows complex.
  * mode bit 0: include the point part; bit 1: include the near/self integrals.
  */
-void or_direct_rows(const double* V, const int32_t* F, int64_t nt, double k, double r_near,
-                    const int64_t* rows, int64_t nrows, const double* sigma_ri, double* out_ri,
-                    int mode) {
+int or_direct_rows(const double* V, const int32_t* F, int64_t nt, double k, double r_near,
+                   const int64_t* rows, int64_t nrows, const double* sigma_ri, double* out_ri,
+                   int mode) {
+    int overflow = 0;
     int64_t N = 3 * nt;
     double* X = (double*)malloc(sizeof(double) * 3 * (size_t)N);
     double* W = (double*)malloc(sizeof(double) * (size_t)N);
@@ -558,6 +580,12 @@ void or_direct_rows(const double* V, const int32_t* F, int64_t nt, double k, dou
             int64_t i = rows[r];
             int32_t buf[NEAR_CAP];
             int c = near_tris_of(&g, X, T, i, r_near, buf, NEAR_CAP);
+            if (c < 0) {
+#pragma omp atomic write
+                overflow = 1;
+                out_ri[2 * r] = out_ri[2 * r + 1] = NAN;
+                continue;
+            }
             for (int q = 0; q < c; ++q) mark[buf[q]] = 1;
             cplx acc = 0.0;
             if (mode & 1) {
@@ -594,11 +622,14 @@ void or_direct_rows(const double* V, const int32_t* F, int64_t nt, double k, dou
     free(X);
     free(W);
     free(T);
+    return overflow ? -1 : 0;
 }
 
-/* Dense Z (row-major, N x N complex interleaved) by the same definition. */
-void or_dense_Z(const double* V, const int32_t* F, int64_t nt, double k, double r_near,
-                double* Z_ri) {
+/* Dense Z (row-major, N x N complex interleaved) by the same definition.
+   Returns 0, or -1 if some near set exceeds NEAR_CAP candidate entries. */
+int or_dense_Z(const double* V, const int32_t* F, int64_t nt, double k, double r_near,
+               double* Z_ri) {
+    int overflow = 0;
     int64_t N = 3 * nt;
     double* X = (double*)malloc(sizeof(double) * 3 * (size_t)N);
     double* W = (double*)malloc(sizeof(double) * (size_t)N);
@@ -610,6 +641,11 @@ void or_dense_Z(const double* V, const int32_t* F, int64_t nt, double k, double 
     for (int64_t i = 0; i < N; ++i) {
         int32_t buf[NEAR_CAP];
         int c = near_tris_of(&g, X, T, i, r_near, buf, NEAR_CAP);
+        if (c < 0) {
+#pragma omp atomic write
+            overflow = 1;
+            c = 0;
+        }
         double* row = Z_ri + 2 * N * i;
         for (int64_t j = 0; j < N; ++j) {
             if (j == i) { row[2 * j] = row[2 * j + 1] = 0.0; continue; }
@@ -636,6 +672,47 @@ void or_dense_Z(const double* V, const int32_t* F, int64_t nt, double k, double 
     free(X);
     free(W);
     free(T);
+    return overflow ? -1 : 0;
+}
+
+/*
+ * The near sets S(i) themselves, in CSR form: ptr[0..N] and idx[ptr[i]..ptr[i+1])
+ * = the sorted triangle ids of S(i) (Sec. 2.2: the own patch and the patches
+ * within the near distance, which Listing 1 integrates apart).  Call with
+ * idx == NULL for the counts (ptr gets the prefix sum), then with storage.
+ * Returns the total number of entries, or -1 if some set exceeds NEAR_CAP
+ * candidate entries.
+ */
+int64_t or_near_sets(const double* V, const int32_t* F, int64_t nt, double r_near, int64_t* ptr,
+                     int32_t* idx) {
+    int64_t N = 3 * nt;
+    double* X = (double*)malloc(sizeof(double) * 3 * (size_t)(N > 0 ? N : 1));
+    double* W = (double*)malloc(sizeof(double) * (size_t)(N > 0 ? N : 1));
+    int32_t* T = (int32_t*)malloc(sizeof(int32_t) * (size_t)(N > 0 ? N : 1));
+    or_points(V, F, nt, X, W, T);
+    grid_t g;
+    grid_build(&g, X, N, r_near);
+    int overflow = 0;
+    if (idx == NULL) ptr[0] = 0;
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t i = 0; i < N; ++i) {
+        int32_t buf[NEAR_CAP];
+        int c = near_tris_of(&g, X, T, i, r_near, buf, NEAR_CAP);
+        if (c < 0) {
+#pragma omp atomic write
+            overflow = 1;
+            c = 0;
+        }
+        if (idx == NULL) ptr[i + 1] = c;
+        else memcpy(idx + ptr[i], buf, sizeof(int32_t) * (size_t)c);
+    }
+    if (idx == NULL)
+        for (int64_t i = 0; i < N; ++i) ptr[i + 1] += ptr[i];
+    grid_free(&g);
+    free(X);
+    free(W);
+    free(T);
+    return overflow ? -1 : ptr[N];
 }
 
 /* Raw kernel sum  out_i = sum_{j != i, R_ij > 0} w_j G(x_i, x_j) s_j  (no corrections). */

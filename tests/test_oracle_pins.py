@@ -217,6 +217,124 @@ def test_points_weights_cover_surface():
     assert np.allclose(X[3 * n + 1], (2 / 3) * p[n, 1] + (p[n, 0] + p[n, 2]) / 6)
 
 
+def _mean_edge_numpy(V, F):
+    V, F = np.asarray(V, float), np.asarray(F)
+    L = [np.linalg.norm(V[F[:, (a + 1) % 3]] - V[F[:, a]], axis=1) for a in range(3)]
+    return np.concatenate(L).mean()
+
+
+@pytest.mark.parametrize("mesh", ["sphere", "star", "ellipsoid", "bisected"])
+def test_mean_edge_against_numpy(mesh):
+    """h-bar (the unit of the near radius, Sec. 6.4's near-patch distance) is the
+    mean over all triangles of their three edge lengths."""
+    V, F = {"sphere": lambda: synthetic.sphere_mesh(2),
+            "star": lambda: synthetic.star_mesh(2, seed=3),
+            "ellipsoid": lambda: synthetic.ellipsoid_mesh(2),
+            "bisected": lambda: synthetic.sphere_mesh(2, bisect=True)}[mesh]()
+    # sequential vs pairwise summation of ~2k terms: rounding well below 1e-12
+    assert abs(oracle.mean_edge(V, F) - _mean_edge_numpy(V, F)) < 1e-12 * _mean_edge_numpy(V, F)
+    # hand value: one right triangle with legs 3, 4 (edges 3, 4, 5)
+    V1 = np.array([[0.0, 0, 0], [3.0, 0, 0], [0.0, 4, 0]])
+    assert oracle.mean_edge(V1, np.array([[0, 1, 2]])) == 4.0
+
+
+def _near_sets_bruteforce(X, T, r):
+    """S(i) = {own triangle} U {triangle of every point j with |x_i - x_j| <= r}, squared
+    distances summed in the same order (x, y, z) as any FP64 implementation would."""
+    out = []
+    r2 = r * r
+    for i in range(X.shape[0]):
+        d = X[i][None, :] - X
+        d2 = d[:, 0] * d[:, 0] + d[:, 1] * d[:, 1] + d[:, 2] * d[:, 2]
+        out.append(np.union1d([T[i]], T[d2 <= r2]))
+    return out
+
+
+@pytest.mark.parametrize("mesh,factor", [("sphere", 1.0), ("sphere", 2.5), ("star", 1.0), ("star", 1.7),
+                                         ("bisected", 1.0)])
+def test_near_sets_against_bruteforce(mesh, factor):
+    """Sec. 2.2 / Listing 1: the own patch and every patch with a point within the near
+    distance are integrated exactly; the oracle's hash-grid search must return exactly
+    the brute-force set for every point."""
+    V, F = {"sphere": lambda: synthetic.sphere_mesh(2),
+            "star": lambda: synthetic.star_mesh(2, seed=5),
+            "bisected": lambda: synthetic.sphere_mesh(1, bisect=True)}[mesh]()
+    X, _, T = oracle.points(V, F)
+    r = factor * _mean_edge_numpy(V, F)
+    ptr, idx = oracle.near_sets(V, F, r)
+    ref = _near_sets_bruteforce(X, T, r)
+    sizes = np.diff(ptr)
+    assert np.array_equal(sizes, [len(s) for s in ref])
+    for i in range(X.shape[0]):
+        assert np.array_equal(idx[ptr[i]:ptr[i + 1]], ref[i]), i
+    # the sets are not trivially the own triangle: neighbours are found
+    assert sizes.mean() > 4
+
+
+def test_near_set_boundary_is_inclusive():
+    """A triangle whose nearest point lies exactly at r_near belongs to S(i); one ulp
+    less and it does not."""
+    V, F = synthetic.star_mesh(2, seed=7)
+    X, _, T = oracle.points(V, F)
+    rng = np.random.default_rng(11)
+    checked = 0
+    for i in rng.permutation(X.shape[0])[:400]:
+        d = X[i][None, :] - X
+        d2 = d[:, 0] * d[:, 0] + d[:, 1] * d[:, 1] + d[:, 2] * d[:, 2]
+        other = T != T[i]
+        # the triangle of the nearest foreign point, and its nearest point's distance
+        j = np.flatnonzero(other)[np.argmin(d2[other])]
+        d2min = d2[T == T[j]].min()
+        r = float(np.sqrt(d2min))
+        if r * r != d2min:
+            continue
+        # nothing else sits between (r - 1 ulp) and r
+        if np.count_nonzero(d2 == d2min) != 1:
+            continue
+        ptr, idx = oracle.near_sets(V, F, r)
+        assert T[j] in idx[ptr[i]:ptr[i + 1]]
+        ptr, idx = oracle.near_sets(V, F, np.nextafter(r, 0.0))
+        assert T[j] not in idx[ptr[i]:ptr[i + 1]]
+        checked += 1
+        if checked == 3:
+            break
+    assert checked == 3
+
+
+def test_near_set_overflow_is_refused():
+    """A near radius that puts more candidates in one set than the oracle's table holds
+    raises instead of silently truncating S(i)."""
+    V, F = synthetic.sphere_mesh(4)  # 15,360 points, all within 2.1 of each other
+    with pytest.raises(oracle.NearSetOverflow):
+        oracle.near_sets(V, F, 2.1)
+    with pytest.raises(oracle.NearSetOverflow):
+        oracle.direct_rows(V, F, 1.0, 2.1, [0, 1], np.ones(3 * F.shape[0], complex))
+    with pytest.raises(oracle.NearSetOverflow):
+        oracle.correction_csr(V, F, 1.0, 2.1)
+
+
+def test_operator_row_from_pinned_parts():
+    """One row of Z assembled from the brute-force near set, the (separately pinned) exact
+    triangle integrals and the point rule elsewhere (Eq. 10 with Sec. 2.2's treatment)
+    equals the oracle's dense Z and its row-by-row form."""
+    V, F = synthetic.star_mesh(1, seed=2)
+    X, W, T = oracle.points(V, F)
+    k, r = 3.0, 1.5 * _mean_edge_numpy(V, F)
+    Z = oracle.dense_Z(V, F, k, r)
+    S = _near_sets_bruteforce(X, T, r)
+    rng = np.random.default_rng(4)
+    for i in rng.choice(X.shape[0], 6, replace=False):
+        R = np.linalg.norm(X[i] - X, axis=1)
+        row = np.where(R > 0, W * np.exp(1j * k * R) / (4 * np.pi * np.where(R > 0, R, 1.0)), 0.0)
+        for n in S[i]:
+            row[3 * n:3 * n + 3] = oracle.tri_integrals(X[i], V[F[n]], k)
+        assert np.allclose(Z[i], row, rtol=0, atol=1e-13 * np.abs(row).max())
+        e = np.zeros(X.shape[0], complex)
+        e[rng.integers(X.shape[0])] = 1.0
+        s = synthetic.random_density(X.shape[0], int(i))
+        assert abs(oracle.direct_rows(V, F, k, r, [i], s)[0] - row @ s) < 1e-12 * np.abs(row @ s)
+
+
 def test_green_kernel_symmetry():
     V, F = synthetic.sphere_mesh(2)
     X, _, _ = oracle.points(V, F)
