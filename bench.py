@@ -38,24 +38,26 @@ WORKLOADS = {
 }
 
 
-def _m2l_traffic(translations):
-    """DRAM bytes of one tensor-core M2L launch, from the committed ncu summary of that kernel
-    (bytes per translation on a smaller case, scaled by this launch's translations); None when
-    the kernel source has changed since the capture."""
+DRAM_PROFILE = os.path.join(ROOT, "profiles", "dram_sphere_655360.md")
+
+
+def _source_sha(fname):
     import hashlib
 
-    src = os.path.join(ROOT, "paper_1803_09948_gb300", "csrc", "m2l_tc.cu")
-    prof = os.path.join(ROOT, "profiles", "k_m2l_tc_sphere_163840.md")
+    with open(os.path.join(ROOT, "paper_1803_09948_gb300", "csrc", fname), "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def _ncu_dram(kernel):
+    """DRAM bytes (read + write) of one launch of `kernel` on the 1.97 M-point sphere, from the
+    committed ncu summary; None when the kernel's source file changed since the capture."""
     try:
-        with open(prof) as f:
+        with open(DRAM_PROFILE) as f:
             kv = dict(line.strip().split(" = ", 1) for line in f if " = " in line and line.startswith("    "))
-        with open(src, "rb") as f:
-            sha = hashlib.sha256(f.read()).hexdigest()[:16]
-        if sha != kv["kernel_source_sha256_16"]:
+        files, shas = kv[f"{kernel}.file"].split(","), kv[f"{kernel}.sha256_16"].split(",")
+        if any(_source_sha(f_.strip()) != s_.strip() for f_, s_ in zip(files, shas)):
             return None, "kernel changed since the ncu capture"
-        per = float(kv["dram_bytes_per_translation"])
-        return per * translations, (f"ncu dram__bytes_read+write on sphere_163840 ({per:.1f} B per translation), "
-                                    f"scaled to {int(translations)} translations")
+        return float(kv[f"{kernel}.dram_bytes_per_launch"]), "ncu dram__bytes_read.sum + dram__bytes_write.sum"
     except (OSError, KeyError, ValueError):
         return None, "no ncu capture"
 
@@ -486,6 +488,8 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--p-min", type=int, default=None)
     ap.add_argument("--solves", type=int, default=2)
+    ap.add_argument("--plain-steps", type=int, default=20,
+                    help="matvecs of the plain single-RHS FP32 form (SIMT M2L) timed beside the headline; 0: skip")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--simt", action="store_true", help="M2L on FP32 SIMT cores only (the plain form)")
     ap.add_argument("--leaf-max", type=int, default=0, help="> 0: points per leaf at most (default: the plan's 64)")
@@ -582,19 +586,17 @@ def main():
     stages = {q: v / reps for q, v in stages.items()}
 
     # ------------------------------------------------------------ end to end through the ABI (host buffers)
+    # hfmm_matvec_host: density copied in from page-locked host memory, potential copied back,
+    # inside the call, every step
     h_in = torch.from_numpy(sigma.astype(np.complex64)).pin_memory()
     h_out = torch.empty_like(h_in).pin_memory()
     for _ in range(2):
-        dens.copy_(h_in, non_blocking=True)
-        plan.matvec(dens, pot)
-        h_out.copy_(pot, non_blocking=True)
+        plan.matvec_host(h_in, h_out)
     barrier()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(args.steps):
-        dens.copy_(h_in, non_blocking=True)
-        plan.matvec(dens, pot)
-        h_out.copy_(pot, non_blocking=True)
+        plan.matvec_host(h_in, h_out)
     e1.record(stream)
     barrier()
     e2e_ms = _max_over_ranks(e0.elapsed_time(e1), world)
@@ -623,6 +625,39 @@ def main():
                  "iterations": its[-1], "true_relres": rrs[-1], "restart": restart, "tol": 1e-4,
                  "status": "converged" if stt == 0 else "not converged", "rhs": "plane wave along +z"}
 
+    # ------------------------------------------------------------ the plain single-RHS FP32 form
+    # (M2L on FP32 SIMT at every level), same workload, same CUDA-event timing on the same stream
+    plain = None
+    if not args.simt and args.plain_steps > 0:
+        pplan = pkg.Plan(V, F, k, **dict(cfg, m2l_tensor=0))
+        ppot = torch.empty_like(dens)
+        for _ in range(args.warmup):
+            pplan.matvec(dens, ppot)
+        barrier()
+        e0.record(stream)
+        for _ in range(args.plain_steps):
+            pplan.matvec(dens, ppot)
+        e1.record(stream)
+        barrier()
+        plain_ms = _max_over_ranks(e0.elapsed_time(e1), world) / args.plain_steps
+        pstages = pplan.matvec_timed(dens, ppot)
+        pgot = ppot.cpu().numpy().astype(np.complex128)
+        plain = {"value": _job_rate(1, world, plain_ms), "unit": "matvec/s", "ms_per_matvec": plain_ms,
+                 "steps": args.plain_steps, "m2l": "FP32 SIMT at every level", "stages_ms": pstages,
+                 "speedup_of_headline": plain_ms / (total_ms / args.steps)}
+        if args.solves > 0:
+            b = torch.empty_like(dens)
+            pplan.rhs_planewave([0.0, 0.0, 1.0], b)
+            x2 = torch.empty_like(dens)
+            pplan.solve(b, x2)  # warm-up (Krylov basis)
+            barrier()
+            t1 = time.perf_counter()
+            stt2, it2, rr2 = pplan.solve(b, x2)
+            torch.cuda.synchronize()
+            plain["solve"] = {"ms_per_solve": 1e3 * (time.perf_counter() - t1), "iterations": it2[0],
+                              "true_relres": rr2[0], "status": "converged" if stt2 == 0 else "not converged"}
+        pplan.close()
+
     # ------------------------------------------------------------ roofline of the dominant stage
     hbm, peak_src, smax = _peaks()
     try:
@@ -634,33 +669,53 @@ def main():
     fp32_peak = props.multi_processor_count * 128 * 2 * smax * 1e6 / 1e12  # TFLOP/s
     dom = max(stages, key=stages.get)
     tc_cmacs = costs["m2l_tc_cmacs"]
+    # stage -> (bound, algorithmic amount per launch, unit, peak, convention, kernel name for ncu)
     work = {
-        "p2p": ("alu", costs["p2p_pairs"] * 24 / 1e12, "TFLOP/s", fp32_peak, "24 flop per source-target pair"),
+        "p2p": ("alu", costs["p2p_pairs"] * 24 / 1e12, "TFLOP/s", fp32_peak, "24 flop per source-target pair",
+                "k_p2p_staged"),
         "m2l_simt": ("alu", (costs["m2l_cmacs"] - tc_cmacs) * 8 / 1e12, "TFLOP/s", fp32_peak,
-                     "8 flop per complex multiply-add, P_l^2 per translation (SIMT levels)"),
-        "m2l": ("tensor", tc_cmacs * 8 * 3 / 1e12, "TFLOP/s", bf16_peak,
-                "real-form contraction, 8 flop per complex multiply-add (P^2 per translation) x 3 BF16 "
-                "products (hi*hi, hi*lo, lo*hi); "
-                f"{int(costs['m2l_tc_translations'])} translations per launch"),
-        "m2m": ("alu", costs["m2m_l2l_cmacs"] * 4 / 1e12, "TFLOP/s", fp32_peak, "M2M half of the M2M+L2L work"),
-        "l2l": ("alu", costs["m2m_l2l_cmacs"] * 4 / 1e12, "TFLOP/s", fp32_peak, "L2L half of the M2M+L2L work"),
+                     "8 flop per complex multiply-add, P_l^2 per translation (SIMT levels)", None),
+        "m2l": ("tensor", tc_cmacs * 8 / 1e12, "TFLOP/s", bf16_peak,
+                "the method's flops: 8 per complex multiply-add, P^2 per translation "
+                f"({int(costs['m2l_tc_translations'])} translations per launch)", "k_m2l_tc"),
         "corr": ("hbm", (costs["corr_nnz"] * 12 + costs["n_points"] * 16) / 1e9, "GB/s", hbm,
-                 "12 B per nonzero + 16 B per row"),
+                 "12 B per nonzero + 16 B per row", "k_corr"),
     }
-    rl = None
-    traffic, traffic_note = None, None
-    if dom == "m2l":
-        traffic, traffic_note = _m2l_traffic(costs["m2l_tc_translations"])
-    if dom in work:
-        bound, amount, unit, peak, note = work[dom]
-        achieved = amount / (stages[dom] / 1e3)
-        rl = {"kernel": dom, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
-              "frac": achieved / peak, "traffic": traffic, "traffic_source": traffic_note,
-              "peak_source": (f"FP32: {props.multi_processor_count} SMs x 128 lanes x 2 flop x {smax:.0f} MHz"
-                              if bound == "alu" else
-                              (f"dense BF16 cuBLAS burst, {peak_src}" if bound == "tensor"
-                               else f"HBM {peak_src} copy bandwidth")),
-              "work_per_launch": note}
+    peak_source = {"alu": f"FP32: {props.multi_processor_count} SMs x 128 lanes x 2 flop x {smax:.0f} MHz",
+                   "tensor": f"dense BF16 cuBLAS burst, {peak_src}", "hbm": f"HBM {peak_src} copy bandwidth"}
+
+    def _roof(stage):
+        bound, amount, unit, peak, note, kname = work[stage]
+        achieved = amount / (stages[stage] / 1e3)
+        traffic, tnote = _ncu_dram(kname) if kname else (None, "no ncu capture")
+        return {"kernel": kname or stage, "stage": stage, "bound": bound, "achieved": achieved, "peak": peak,
+                "unit": unit, "frac": achieved / peak, "traffic": traffic, "traffic_source": tnote,
+                "peak_source": peak_source[bound], "work_per_launch": note}
+
+    rl = _roof(dom) if dom in work else None
+    if rl is not None and dom == "m2l":
+        # what the tensor pipe executes: each multiply-add as three BF16 products (hi*hi, hi*lo, lo*hi)
+        rl["issued_bf16x3"] = {"achieved": 3 * rl["achieved"], "frac": 3 * rl["achieved"] / bf16_peak,
+                               "note": "three BF16 products per multiply-add of the split; the method's work is "
+                                       "a third of it (frac above)"}
+    p2p_block = _roof("p2p")
+    # tree passes: bytes by the stated model (8 B per complex coefficient, 16 B per point
+    # position, 8 B per density / potential value), against the measured HBM copy bandwidth
+    nL, c_leaf = costs["n_points"], costs["leaf_coefficients"]
+    c_all, c2, cL = costs["multipole_coefficients"], costs["level2_coefficients"], costs["levelL_coefficients"]
+    tree_model = {
+        "p2m": ("k_p2m_w", nL * (16 + 8) + 8 * c_leaf, "read points and densities, write leaf multipoles"),
+        "m2m": ("m2m", 8 * (2 * c_all - c2 - cL), "read children's multipoles, write parents'"),
+        "l2l": ("l2l", 8 * (2 * c_all - c2 - cL), "read parents' locals, add into children's"),
+        "l2p": ("k_l2p_t", nL * (16 + 8 + 8) + 8 * c_leaf, "read points, leaf locals and potentials, write potentials"),
+    }
+    tree = {}
+    for stg, (kname, nbytes, note) in tree_model.items():
+        gbs = nbytes / 1e9 / (stages[stg] / 1e3)
+        traffic, tnote = _ncu_dram(kname)
+        tree[stg] = {"ms": stages[stg], "algorithmic_bytes": nbytes, "achieved_gbs": gbs, "frac_of_hbm": gbs / hbm,
+                     "model": note, "traffic": traffic, "traffic_source": tnote,
+                     "dram_gbs": traffic / 1e9 / (stages[stg] / 1e3) if traffic else None}
 
     # ------------------------------------------------------------ accuracy and CPU baseline (rank 0)
     cpu = None
@@ -669,6 +724,8 @@ def main():
         rows, ref, dt = cpu_baseline(V, F, k, plan.cfg.near_factor, sigma)
         acc = {"sampled_rows": int(len(rows)),
                "rel_err_vs_oracle": float(np.linalg.norm(got[rows] - ref) / np.linalg.norm(ref))}
+        if plain is not None:
+            plain["rel_err_vs_oracle"] = float(np.linalg.norm(pgot[rows] - ref) / np.linalg.norm(ref))
         cpu = {"value": len(rows) / N / dt, "unit": "matvec/s", "cores": os.cpu_count(), "kind": "oracle",
                "sample": f"{len(rows)} sampled rows of the FP64 direct sum (point part + exact self/near "
                          f"integrals), {dt:.1f} s, scaled to whole matvecs"}
@@ -677,7 +734,10 @@ def main():
         out = {
             "metric": METRIC, "value": value, "unit": "matvec/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "fp32 (P2P, M2L, tree passes); fp64 GMRES",
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": ("fp32 (P2P, tree passes, M2L on every level)" if args.simt else
+                      "fp32 (P2P, tree passes, SIMT M2L at (p+1)^2 > 64); bf16x3 split with fp32 accumulation "
+                      "(tensor-core M2L at (p+1)^2 <= 64)") + "; fp64-class double-float GMRES",
             "data": "synthetic",
             "config": {"workload": f"{args.workload}: {synthetic.WORKLOADS[mesh][0]}", "N": N, "k": k,
                        "leaf_max": plan.cfg.leaf_max, "depth": info["depth"], "orders": info["orders"],
@@ -696,6 +756,9 @@ def main():
             "e2e": {"value": _job_rate(args.steps, world, e2e_ms), "unit": "matvec/s", "h2d_bytes_per_step": 8 * N,
                     "d2h_bytes_per_step": 8 * N},
             "roofline": rl,
+            "p2p": p2p_block,
+            "tree_passes": tree,
+            "plain_fp32": plain,
             "cpu_baseline": cpu,
             "accuracy": acc,
             "clocks": clk,

@@ -127,6 +127,17 @@ int hfmm_plan_info(const hfmm_plan* plan, int* depth, int* orders, int64_t* n_le
 int hfmm_matvec(hfmm_plan* plan, const void* density, void* potential, int nrhs, void* stream);
 
 /*
+ * hfmm_matvec with HOST buffers: density and potential are host complex64
+ * vectors, N x nrhs, user point order (page-locked memory gives the fastest
+ * copies; pageable memory works).  Each chunk of up to 64 right-hand sides is
+ * copied to plan-owned device staging (allocated on the first call, 2 x 8 x N x
+ * min(nrhs, 64) bytes, kept and counted in the plan's device bytes), multiplied,
+ * and copied back, all on `stream`; the call returns after the last copy has
+ * landed.  The caller owns both buffers.
+ */
+int hfmm_matvec_host(hfmm_plan* plan, const void* density, void* potential, int nrhs, void* stream);
+
+/*
  * Like hfmm_matvec but evaluates only part of the operator (for tests and
  * breakdowns): parts bit 0 = near field (P2P between neighbouring leaves),
  * bit 1 = far field (P2M..L2P), bit 2 = near/self correction.  parts = 7 is
@@ -209,13 +220,17 @@ int hfmm_matvec_timed(hfmm_plan* plan, const void* density, void* potential, flo
                       void* stream);
 
 /*
- * Algorithmic work of one matvec (HOST, 8 doubles): 0 near-field source-target
- * pairs (j != i), 1 M2L complex multiply-adds (sum over translations of
- * P_l^2), 2 M2M + L2L complex multiply-adds, 3 correction nonzeros,
- * 4 points N, 5 expansion coefficients (all levels, multipoles + locals),
- * 6 the part of 1 done on the tensor cores, 7 the number of M2L translations
- * done on the tensor cores.
+ * Algorithmic work of one matvec (HOST, HFMM_NUM_COSTS doubles): 0 near-field
+ * source-target pairs (j != i), 1 M2L complex multiply-adds (sum over
+ * translations of P_l^2), 2 M2M + L2L complex multiply-adds, 3 correction
+ * nonzeros, 4 points N, 5 expansion coefficients (all levels, multipoles +
+ * locals, padded), 6 the part of 1 done on the tensor cores, 7 the number of
+ * M2L translations done on the tensor cores, 8 complex coefficients of the
+ * leaves' expansions (sum over leaves of P_leaf-level), 9 complex multipole
+ * coefficients of level 2, 10 complex multipole coefficients of levels 2..L,
+ * 11 complex multipole coefficients of level L.
  */
+#define HFMM_NUM_COSTS 12
 int hfmm_plan_costs(const hfmm_plan* plan, double* costs);
 
 /*
@@ -246,14 +261,22 @@ int64_t hfmm_launch_count(const hfmm_plan* plan);
  *
  * Working memory is a fixed file-scope device array of HFMM_NOALLOC_MAX_POINTS
  * entries (32 bytes each, 8 MiB), held by every device that loads the library
- * until the process exits; the call itself allocates and frees nothing.
- * n > HFMM_NOALLOC_MAX_POINTS returns HFMM_E_OVERFLOW (see hfmm_last_error).
- * The first call on a device looks up the array's device address (with that
- * device current); make that first call before any stream capture.  All calls
- * on a device share the one array, so calls that overlap on the GPU (on
- * different streams, or from different threads) race and must be serialised
- * by the caller.  Each call overwrites the entries it reads; nothing needs
- * clearing between calls.
+ * until the process exits; the call itself never calls cudaMalloc or cudaFree.
+ * With CUDA's default lazy module loading the array (with the module holding
+ * it) is brought onto a device by the first call there, which therefore grows
+ * the device footprint by about 8 MiB once: a caller whose footprint must not
+ * grow later makes one call (any n) at start-up, or runs with
+ * CUDA_MODULE_LOADING=EAGER.  That first call on a device also looks up the
+ * array's device address (with that device current); make it before any
+ * stream capture.  `stream` must belong to the current device (else
+ * HFMM_E_INVALID).  n > HFMM_NOALLOC_MAX_POINTS returns HFMM_E_OVERFLOW;
+ * a null pointer, n <= 0, or k not finite and positive returns HFMM_E_INVALID
+ * (see hfmm_last_error).  All calls on a device share the one array, so calls
+ * that overlap on the GPU (on different streams, or from different threads)
+ * race and must be serialised by the caller.  Each call overwrites the entries
+ * it reads; nothing needs clearing between calls.  Positions are staged as
+ * float32 hi + lo parts of k (x - x_0), so close pairs keep float32 relative
+ * precision at any |k x|.
  */
 #define HFMM_NOALLOC_MAX_POINTS 262144
 int hfmm_point_sum_noalloc(const double* xyz, const double* w, int64_t n, double k,

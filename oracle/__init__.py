@@ -52,6 +52,8 @@ def lib():
         L.or_near_sets.argtypes = [_dp, _i32p, ctypes.c_int64, ctypes.c_double, _i64p, _i32p]
         L.or_near_sets.restype = ctypes.c_int64
         L.or_point_sum.argtypes = [_dp, _dp, ctypes.c_int64, ctypes.c_double, _dp, _dp]
+        L.or_point_sum_rows.argtypes = [_dp, _dp, ctypes.c_int64, ctypes.c_double, _i64p, ctypes.c_int64,
+                                        _dp, _dp]
         L.or_fmm.argtypes = [_dp, _dp, ctypes.c_int64, ctypes.c_double, ctypes.c_int, ctypes.c_int,
                              ctypes.c_int, ctypes.c_int, _dp, _dp, ctypes.c_int, _ip]
         L.or_fmm.restype = ctypes.c_int
@@ -191,6 +193,17 @@ def point_sum(X, W, k, sigma):
     s = _c128(sigma).view(np.float64)
     out = np.zeros(2 * W.size)
     lib().or_point_sum(_d(X), _d(W), W.size, float(k), _d(s), _d(out))
+    return out[0::2] + 1j * out[1::2]
+
+
+def point_sum_rows(X, W, k, sigma, rows):
+    """Rows `rows` of point_sum (the same definition, O(N) per row)."""
+    X, W = _f64(X), _f64(W)
+    rows = np.ascontiguousarray(rows, dtype=np.int64)
+    s = _c128(sigma).view(np.float64)
+    out = np.zeros(2 * rows.size)
+    lib().or_point_sum_rows(_d(X), _d(W), W.size, float(k), rows.ctypes.data_as(_i64p), rows.size, _d(s),
+                            _d(out))
     return out[0::2] + 1j * out[1::2]
 
 

@@ -732,3 +732,22 @@ void or_point_sum(const double* X, const double* W, int64_t N, double k, const d
         out_ri[2 * i + 1] = cimag(acc);
     }
 }
+
+/* Rows of the raw kernel sum: out_r = sum_{j != i, R_ij > 0} w_j G(x_i, x_j) s_j for i = rows[r]. */
+void or_point_sum_rows(const double* X, const double* W, int64_t N, double k, const int64_t* rows,
+                       int64_t nrows, const double* sigma_ri, double* out_ri) {
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int64_t r = 0; r < nrows; ++r) {
+        int64_t i = rows[r];
+        cplx acc = 0.0;
+        for (int64_t j = 0; j < N; ++j) {
+            double d[3];
+            v_sub(X + 3 * i, X + 3 * j, d);
+            double R = v_norm(d);
+            if (j == i || R == 0.0) continue;
+            acc += W[j] * green(k, R) * (sigma_ri[2 * j] + I * sigma_ri[2 * j + 1]);
+        }
+        out_ri[2 * r] = creal(acc);
+        out_ri[2 * r + 1] = cimag(acc);
+    }
+}

@@ -30,6 +30,7 @@ EXPORTED = [
     "hfmm_plan_info", "hfmm_matvec", "hfmm_matvec_parts", "hfmm_direct", "hfmm_rhs_planewave",
     "hfmm_solve", "hfmm_solve_refined", "hfmm_status_string", "hfmm_last_error", "hfmm_matvec_timed",
     "hfmm_launch_count", "hfmm_plan_costs", "hfmm_point_sum_noalloc", "hfmm_device_status", "hfmm_field",
+    "hfmm_matvec_host",
 ]
 HFMM_NOALLOC_MAX_POINTS = 262144
 STAGES = ["prep", "p2p", "p2m", "m2m", "m2l_simt", "m2l", "l2l", "l2p", "corr", "output"]
@@ -81,6 +82,7 @@ def lib():
                                      ctypes.POINTER(i64)]
         L.hfmm_matvec.argtypes = [vp, vp, vp, ctypes.c_int, vp]
         L.hfmm_matvec_parts.argtypes = [vp, vp, vp, ctypes.c_int, ctypes.c_int, vp]
+        L.hfmm_matvec_host.argtypes = [vp, vp, vp, ctypes.c_int, vp]
         L.hfmm_direct.argtypes = [vp, vp, vp, ctypes.c_int, vp]
         L.hfmm_rhs_planewave.argtypes = [vp, dp, ctypes.c_int, vp, vp]
         L.hfmm_solve.argtypes = [vp, vp, vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), dp, vp]
@@ -206,6 +208,19 @@ def hfmm_matvec(plan, density, potential, nrhs=1, stream=None):
     _check(lib().hfmm_matvec(plan, _ptr(density), _ptr(potential), int(nrhs), _stream(stream)), "hfmm_matvec")
 
 
+def hfmm_matvec_host(plan, density, potential, nrhs=1, stream=None):
+    """density / potential: contiguous complex64 CPU tensors (page-locked for speed) of N x nrhs."""
+    import torch
+
+    n = hfmm_num_points(plan)
+    for t, name in ((density, "density"), (potential, "potential")):
+        if not (isinstance(t, torch.Tensor) and not t.is_cuda and t.dtype == torch.complex64
+                and t.is_contiguous() and t.numel() == n * nrhs):
+            raise ValueError(f"{name}: expected a contiguous complex64 CPU tensor of {n * nrhs} elements")
+    _check(lib().hfmm_matvec_host(plan, _ptr(density), _ptr(potential), int(nrhs), _stream(stream)),
+           "hfmm_matvec_host")
+
+
 def hfmm_matvec_parts(plan, density, potential, parts, nrhs=1, stream=None):
     n = hfmm_num_points(plan)
     _vec(density, n, nrhs, "density")
@@ -226,7 +241,8 @@ def hfmm_matvec_timed(plan, density, potential, stream=None):
 
 def hfmm_plan_costs(plan):
     keys = ["p2p_pairs", "m2l_cmacs", "m2m_l2l_cmacs", "corr_nnz", "n_points", "coefficients", "m2l_tc_cmacs",
-            "m2l_tc_translations"]
+            "m2l_tc_translations", "leaf_coefficients", "level2_coefficients", "multipole_coefficients",
+            "levelL_coefficients"]
     c = (ctypes.c_double * len(keys))()
     _check(lib().hfmm_plan_costs(plan, c), "hfmm_plan_costs")
     return dict(zip(keys, [float(v) for v in c]))
@@ -339,6 +355,9 @@ class Plan:
 
     def matvec(self, density, potential, nrhs=1, stream=None):
         hfmm_matvec(self.handle, density, potential, nrhs, stream)
+
+    def matvec_host(self, density, potential, nrhs=1, stream=None):
+        hfmm_matvec_host(self.handle, density, potential, nrhs, stream)
 
     def matvec_parts(self, density, potential, parts, nrhs=1, stream=None):
         hfmm_matvec_parts(self.handle, density, potential, parts, nrhs, stream)

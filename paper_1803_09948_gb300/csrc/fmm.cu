@@ -243,6 +243,156 @@ __global__ void __launch_bounds__(128) k_p2p_staged(const int32_t* __restrict__ 
     }
 }
 
+// ------------------------------------------------------------------ packed near field
+// One block per target leaf.  The neighbourhood's sources are staged in shared memory in
+// pairs, laid out so that each operand of a pair is an aligned register pair:
+//   sq[2q]   = {x_2q, x_2q+1, y_2q, y_2q+1},  sq[2q+1] = {z_2q, z_2q+1, Re s_2q, Re s_2q+1},
+//   sim[q]   = {Im s_2q, Im s_2q+1}
+// (self leaf first, each of the two segments padded to an even length with a zero-density
+// source far away).  A thread holds one target and evaluates both sources of a pair at once
+// with packed FP32x2 arithmetic (fma.rn.f32x2 and friends), walking every S-th pair; the S
+// threads that share a target meet in shared memory.  The complex multiply-add is kept as
+// four real accumulators (Re s Re G, Im s Im G, Re s Im G, Im s Re G), so it needs no
+// negated operand.  Same kernel (cos, sinc polynomials in u = (kR)^2, hardware rsqrt) and
+// the same j != i rule as the staged kernel above.
+constexpr int kPkThreads = 128;
+constexpr float kPkPad = 64.0f;  // padding sources sit at (64, 64, 64) (scaled units): u stays finite
+
+__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+
+template <int D>
+__device__ __forceinline__ float2 horner2(const float (&c)[D + 1], float2 u) {
+    float2 a = f2(c[D]);
+#pragma unroll
+    for (int q = D - 1; q >= 0; --q) a = __ffma2_rn(a, u, f2(c[q]));
+    return a;
+}
+
+// d2 = 2q - (target's staged index): half 0 of the pair is the target itself when d2 == 0,
+// half 1 when d2 == -1 (MASK: the self segment only)
+template <bool MASK>
+__device__ __forceinline__ void pk_pair(const float4 xy, const float4 zr, float2 si, float2 ntx, float2 nty, float2 ntz,
+                                        int d2, float2& A, float2& B, float2& C, float2& D) {
+    constexpr float kC[HFMM_POLY_C_DEG + 1] = HFMM_POLY_C_INIT;
+    constexpr float kS[HFMM_POLY_S_DEG + 1] = HFMM_POLY_S_INIT;
+    const float2 dx = __fadd2_rn(make_float2(xy.x, xy.y), ntx);
+    const float2 dy = __fadd2_rn(make_float2(xy.z, xy.w), nty);
+    const float2 dz = __fadd2_rn(make_float2(zr.x, zr.y), ntz);
+    float2 u = __fmul2_rn(dz, dz);
+    u = __ffma2_rn(dy, dy, u);
+    u = __ffma2_rn(dx, dx, u);
+    float2 sr = make_float2(zr.z, zr.w);
+    if (MASK) {
+        if (d2 == 0) sr.x = si.x = 0.f;
+        if (d2 == -1) sr.y = si.y = 0.f;
+        u.x = fmaxf(u.x, 1e-30f);
+        u.y = fmaxf(u.y, 1e-30f);
+    }
+    const float2 rinv = make_float2(rsqrt_ftz(u.x), rsqrt_ftz(u.y));
+    const float2 re = __fmul2_rn(horner2<HFMM_POLY_C_DEG>(kC, u), rinv);  // cos(kR)/(kR)
+    const float2 im = horner2<HFMM_POLY_S_DEG>(kS, u);                     // sin(kR)/(kR)
+    A = __ffma2_rn(sr, re, A);
+    B = __ffma2_rn(si, im, B);
+    C = __ffma2_rn(sr, im, C);
+    D = __ffma2_rn(si, re, D);
+}
+
+__global__ void __launch_bounds__(kPkThreads) k_p2p_packed(const int32_t* __restrict__ leaf_start,
+                                                           const int4* __restrict__ leaf_ijk,
+                                                           const int32_t* __restrict__ nbr_ptr,
+                                                           const int32_t* __restrict__ nbr,
+                                                           const float4* __restrict__ pts,
+                                                           const float2* __restrict__ sig, float shift, int cap_pairs,
+                                                           float2* __restrict__ phi) {
+    extern __shared__ float4 sq[];                                   // [2 cap_pairs]
+    float2* sim = reinterpret_cast<float2*>(sq + 2 * cap_pairs);    // [cap_pairs]
+    __shared__ int s_off[kStagedNbr + 1], s_leaf[kStagedNbr], s_nl;
+    __shared__ float2 s_red[kPkThreads];
+    const int b = blockIdx.x, tid = threadIdx.x;
+    const int4 tij = __ldg(leaf_ijk + b);
+    const int nb0 = __ldg(nbr_ptr + b), nn = __ldg(nbr_ptr + b + 1) - nb0;
+    if (tid == 0) {
+        int k = 0, o = 0;
+        s_leaf[k++] = b;  // self first
+        for (int q = 0; q < nn; ++q) {
+            const int sl = __ldg(nbr + nb0 + q);
+            if (sl != b) s_leaf[k++] = sl;
+        }
+        for (int q = 0; q < k; ++q) {
+            s_off[q] = o;
+            o += __ldg(leaf_start + s_leaf[q] + 1) - __ldg(leaf_start + s_leaf[q]);
+            if (q == 0) o = (o + 1) & ~1;  // the self segment ends on a pair boundary
+        }
+        s_off[k] = (o + 1) & ~1;
+        s_nl = k;
+    }
+    __syncthreads();
+    const int nl = s_nl, npair = s_off[nl] >> 1;
+    const int nself = __ldg(leaf_start + b + 1) - __ldg(leaf_start + b);
+    const int qself = s_off[1] >> 1;  // pairs of the self segment
+    float* sf = reinterpret_cast<float*>(sq);
+    float* sfi = reinterpret_cast<float*>(sim);
+    for (int q = 0; q < nl; ++q) {
+        const int sl = s_leaf[q];
+        const int j0 = __ldg(leaf_start + sl), n = __ldg(leaf_start + sl + 1) - j0;
+        const int4 sij = __ldg(leaf_ijk + sl);
+        const float ox = (float)(sij.x - tij.x) * shift, oy = (float)(sij.y - tij.y) * shift,
+                    oz = (float)(sij.z - tij.z) * shift;
+        const int end = (q + 1 < nl) ? s_off[q + 1] : s_off[nl];
+        for (int e = tid; e < end - s_off[q]; e += kPkThreads) {
+            const int p = s_off[q] + e, pq = p >> 1, h = p & 1;
+            float x = kPkPad, y = kPkPad, z = kPkPad, sr = 0.f, si = 0.f;
+            if (e < n) {
+                const float4 pt = __ldg(pts + j0 + e);
+                const float2 g = __ldg(sig + j0 + e);
+                x = pt.x + ox;
+                y = pt.y + oy;
+                z = pt.z + oz;
+                sr = g.x;
+                si = g.y;
+            }
+            float* r = sf + 8 * pq;
+            r[h] = x;
+            r[2 + h] = y;
+            r[4 + h] = z;
+            r[6 + h] = sr;
+            sfi[2 * pq + h] = si;
+        }
+    }
+    __syncthreads();
+    const int TT = min(nself, kPkThreads);  // target slots per round
+    const int S = kPkThreads / max(TT, 1);  // threads sharing a target
+    const int slot = tid % max(TT, 1), sp = tid / max(TT, 1);
+    const int i0 = __ldg(leaf_start + b);
+    for (int t0 = 0; t0 < nself; t0 += TT) {
+        const int it = t0 + slot;
+        float ar = 0.f, ai = 0.f;
+        if (sp < S && it < nself) {
+            const float* tr = sf + 8 * (it >> 1) + (it & 1);
+            const float2 ntx = f2(-tr[0]), nty = f2(-tr[2]), ntz = f2(-tr[4]);
+            float2 A = f2(0.f), B = f2(0.f), C = f2(0.f), D = f2(0.f);
+            int q = sp;
+            for (; q < qself; q += S) pk_pair<true>(sq[2 * q], sq[2 * q + 1], sim[q], ntx, nty, ntz, 2 * q - it, A, B, C, D);
+#pragma unroll 2
+            for (; q < npair; q += S) pk_pair<false>(sq[2 * q], sq[2 * q + 1], sim[q], ntx, nty, ntz, 0, A, B, C, D);
+            ar = (A.x + A.y) - (B.x + B.y);
+            ai = (C.x + C.y) + (D.x + D.y);
+        }
+        s_red[tid] = make_float2(ar, ai);
+        __syncthreads();
+        if (sp == 0 && it < nself) {
+            float2 acc = s_red[slot];
+            for (int r = 1; r < S; ++r) {
+                const float2 v = s_red[slot + r * TT];
+                acc.x += v.x;
+                acc.y += v.y;
+            }
+            phi[i0 + it] = acc;
+        }
+        __syncthreads();
+    }
+}
+
 // ============================================================== FP32 special functions
 // out[n] = j_n(x) / s^n, n = 0..p
 // Reciprocals for the small-argument series of j_n (uploaded with the Legendre tables):
@@ -1158,7 +1308,16 @@ void run_matvec_sorted(hfmm_plan* P, int parts, cudaStream_t st) {
                 HFMM_CUDA(cudaFuncSetAttribute(k_p2p_staged<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                (int)staged));
             }
-            if (P->poly_p2p)
+            const int cap_pairs = P->p2p_cap / 2 + 2;
+            const size_t pk_smem = (size_t)cap_pairs * (2 * sizeof(float4) + sizeof(float2));
+            if (P->poly_p2p && P->p2p_variant == 1) {
+                if (pk_smem > 48 * 1024)
+                    HFMM_CUDA(cudaFuncSetAttribute(k_p2p_packed, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   (int)pk_smem));
+                k_p2p_packed<<<(unsigned)P->nleaf, kPkThreads, pk_smem, st>>>(
+                    P->leaf_start.p, P->leaf_ijk.p, P->nbr_ptr.p, P->nbr.p, P->pts.p, P->sig.p, P->p2p_shift,
+                    cap_pairs, P->phi.p);
+            } else if (P->poly_p2p)
                 k_p2p_staged<true><<<(unsigned)P->nleaf, 128, staged, st>>>(
                     P->leaf_start.p, P->leaf_ijk.p, P->nbr_ptr.p, P->nbr.p, P->pts.p, P->sig.p, P->p2p_shift,
                     P->p2p_cap, P->phi.p);

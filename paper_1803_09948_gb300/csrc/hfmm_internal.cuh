@@ -140,6 +140,7 @@ struct hfmm_plan {
     bool poly_p2p = true;   // near field fits the polynomial kernel range
     float p2p_shift = 0.f;  // k * half the side of a level-L box (the unit of leaf_ijk)
     int p2p_cap = 0;        // most source points in one leaf's neighbourhood (staged near field)
+    int p2p_variant = 0;    // near-field kernel: 0 staged (4 lanes per target), 1 packed FP32x2 pairs
 
     // sorted point data
     DBuf<float4> pts;        // k * (x - leaf centre), sorted
@@ -192,6 +193,8 @@ struct hfmm_plan {
     DBuf<float2> corr_val;
     // scratch (one matvec at a time per plan)
     DBuf<float2> sig, phi;
+    // device staging of hfmm_matvec_host (allocated on first use, kept)
+    DBuf<float2> hio_in, hio_out;
     // GMRES workspace (allocated on first solve, kept resident)
     DBuf<float4> kry;          // (restart + 1) x N, double-float complex
     DBuf<float4> gw, gx, gb;   // work vector, iterate, right-hand side (double-float complex)
@@ -210,7 +213,7 @@ struct hfmm_plan {
     DBuf<float2> r32, d32;
     DBuf<double> rred;
     int64_t launches = 0;       // kernels launched by this plan
-    double cost[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // see hfmm_plan_costs
+    double cost[HFMM_NUM_COSTS] = {};  // see hfmm_plan_costs
     cudaEvent_t* stage_ev = nullptr;  // set by hfmm_matvec_timed: events after each stage
     BatchState batch;
 };

@@ -6,6 +6,7 @@
 // device footprint after start-up).  The variant stages its working set in a
 // fixed file-scope __device__ array instead of plan-owned buffers; the caller
 // passes only inputs and outputs.  No plan is needed.
+#include <cmath>
 #include <mutex>
 #include <string>
 
@@ -16,10 +17,11 @@ namespace {
 constexpr int64_t kMaxPoints = HFMM_NOALLOC_MAX_POINTS;
 constexpr int kMaxDevices = 64;
 
+// k (x - x_0) split into float32 hi + lo parts, so a difference of two nearby
+// points keeps float32 relative precision however far they sit from x_0.
 struct StagedSource {
-    float4 pos;  // k * (x - x_0), float32
-    float2 sig;  // k w s / (4 pi)
-    float2 pad;
+    float4 hi;  // hi parts of k (x - x_0), Re (k w s / (4 pi))
+    float4 lo;  // lo parts of k (x - x_0), Im (k w s / (4 pi))
 };
 
 // Shared by every call on a device and kept until the process exits
@@ -47,54 +49,57 @@ cudaError_t scratch_address(StagedSource** out) {
     return cudaSuccess;
 }
 
-// Stage positions relative to the first point (scaled by k) and the
-// pre-weighted density.  Every entry [0, n) is overwritten, so nothing left by
-// an earlier call is read.
+// Stage positions relative to the first point (scaled by k, as hi + lo float32
+// pairs) and the pre-weighted density.  Every entry [0, n) is overwritten, so
+// nothing left by an earlier call is read.
 __global__ void k_noalloc_stage(int64_t n, const double* __restrict__ xyz, const double* __restrict__ w,
                                 const float2* __restrict__ density, double k, StagedSource* __restrict__ scratch) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const double c0 = xyz[0], c1 = xyz[1], c2 = xyz[2];
-    StagedSource s;
-    s.pos = make_float4((float)(k * (xyz[3 * i] - c0)), (float)(k * (xyz[3 * i + 1] - c1)),
-                        (float)(k * (xyz[3 * i + 2] - c2)), 0.f);
+    const double px = k * (xyz[3 * i] - xyz[0]), py = k * (xyz[3 * i + 1] - xyz[1]),
+                 pz = k * (xyz[3 * i + 2] - xyz[2]);
+    const float hx = (float)px, hy = (float)py, hz = (float)pz;
     float sc = (float)(k * w[i] / (4.0 * 3.14159265358979323846));
     float2 d = density[i];
-    s.sig = make_float2(sc * d.x, sc * d.y);
-    s.pad = make_float2(0.f, 0.f);
+    StagedSource s;
+    s.hi = make_float4(hx, hy, hz, sc * d.x);
+    s.lo = make_float4((float)(px - (double)hx), (float)(py - (double)hy), (float)(pz - (double)hz), sc * d.y);
     scratch[i] = s;
 }
 
-// All-pairs sum over the staged sources (same arithmetic as the library's
-// direct-summation kernel, without its leaf-local coordinates).
+// All-pairs sum over the staged sources.  A coordinate difference is
+// (hi_t - hi_s) + (lo_t - lo_s): for nearby points the first term is exact, so
+// the difference carries float32 relative precision even where |k (x - x_0)|
+// is large (the plain float32 difference would lose it to the offset).
 __global__ void __launch_bounds__(256) k_noalloc_sum(int64_t n, const StagedSource* __restrict__ scratch,
                                                      float2* __restrict__ out) {
-    __shared__ float4 sp[256];
-    __shared__ float2 sg[256];
+    __shared__ float4 shi[256];
+    __shared__ float4 slo[256];
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     bool active = i < n;
-    float4 t = active ? scratch[i].pos : make_float4(0, 0, 0, 0);
+    StagedSource t = active ? scratch[i] : StagedSource{make_float4(0, 0, 0, 0), make_float4(0, 0, 0, 0)};
     float ar = 0.f, ai = 0.f;
     for (int64_t j0 = 0; j0 < n; j0 += 256) {
         int64_t j = j0 + threadIdx.x;
         if (j < n) {
-            sp[threadIdx.x] = scratch[j].pos;
-            sg[threadIdx.x] = scratch[j].sig;
+            shi[threadIdx.x] = scratch[j].hi;
+            slo[threadIdx.x] = scratch[j].lo;
         }
         __syncthreads();
         int cnt = (n - j0 < 256) ? (int)(n - j0) : 256;
         for (int q = 0; q < cnt; ++q) {
             if (j0 + q == i) continue;
-            float4 s = sp[q];
-            float dx = t.x - s.x, dy = t.y - s.y, dz = t.z - s.z;
+            const float4 h = shi[q], l = slo[q];
+            float dx = (t.hi.x - h.x) + (t.lo.x - l.x);
+            float dy = (t.hi.y - h.y) + (t.lo.y - l.y);
+            float dz = (t.hi.z - h.z) + (t.lo.z - l.z);
             float u = dx * dx + dy * dy + dz * dz;
             if (u == 0.f) continue;
             float rinv = rsqrtf(u), r = u * rinv, sn, cs;
             sincosf(r, &sn, &cs);
             float re = cs * rinv, im = sn * rinv;
-            float2 g = sg[q];
-            ar += g.x * re - g.y * im;
-            ai += g.x * im + g.y * re;
+            ar += h.w * re - l.w * im;
+            ai += h.w * im + l.w * re;
         }
         __syncthreads();
     }
@@ -105,7 +110,18 @@ __global__ void __launch_bounds__(256) k_noalloc_sum(int64_t n, const StagedSour
 
 extern "C" int hfmm_point_sum_noalloc(const double* xyz, const double* w, int64_t n, double k,
                                       const void* density, void* potential, void* stream) {
-    if (!xyz || !w || !density || !potential || n <= 0 || !(k > 0.0)) return HFMM_E_INVALID;
+    if (!xyz || !w || !density || !potential) {
+        hfmm_set_last_error("hfmm_point_sum_noalloc: null pointer argument");
+        return HFMM_E_INVALID;
+    }
+    if (n <= 0) {
+        hfmm_set_last_error("hfmm_point_sum_noalloc: n must be positive");
+        return HFMM_E_INVALID;
+    }
+    if (!(k > 0.0) || !std::isfinite(k)) {
+        hfmm_set_last_error("hfmm_point_sum_noalloc: k must be finite and positive");
+        return HFMM_E_INVALID;
+    }
     if (n > kMaxPoints) {
         hfmm_set_last_error("hfmm_point_sum_noalloc: n = " + std::to_string(n) +
                             " exceeds the scratch capacity HFMM_NOALLOC_MAX_POINTS = " + std::to_string(kMaxPoints));
@@ -118,6 +134,21 @@ extern "C" int hfmm_point_sum_noalloc(const double* xyz, const double* w, int64_
         return HFMM_E_CUDA;
     }
     cudaStream_t st = (cudaStream_t)stream;
+    if (st != nullptr && st != cudaStreamLegacy && st != cudaStreamPerThread) {
+        // the scratch address is per device: the stream must belong to the current one
+        int cur = 0, sdev = 0;
+        e = cudaGetDevice(&cur);
+        if (e == cudaSuccess) e = cudaStreamGetDevice(st, &sdev);
+        if (e != cudaSuccess) {
+            hfmm_set_last_error(std::string("hfmm_point_sum_noalloc: stream device: ") + cudaGetErrorString(e));
+            return HFMM_E_CUDA;
+        }
+        if (sdev != cur) {
+            hfmm_set_last_error("hfmm_point_sum_noalloc: the stream belongs to device " + std::to_string(sdev) +
+                                ", not the current device " + std::to_string(cur));
+            return HFMM_E_INVALID;
+        }
+    }
     unsigned nb = (unsigned)((n + 255) / 256);
     k_noalloc_stage<<<nb, 256, 0, st>>>(n, xyz, w, (const float2*)density, k, scratch);
     k_noalloc_sum<<<nb, 256, 0, st>>>(n, scratch, (float2*)potential);

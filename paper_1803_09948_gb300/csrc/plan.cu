@@ -514,6 +514,13 @@ static void build_plan(hfmm_plan* P, const double* V, int64_t nv, const int32_t*
         }
         P->coef_total = off;
         P->cost[5] = (double)off;
+        // tree-pass byte model: leaf-level coefficients (P2M writes, L2P reads), level-2 and
+        // all-level multipole coefficients (M2M / L2L read one side and write the other)
+        for (int32_t l : leaf_lev)
+            if (l >= 2) P->cost[8] += (double)P->lev[l].P;
+        P->cost[9] = (double)(P->lev[2].nbox * P->lev[2].P);
+        for (int l = 2; l <= L; ++l) P->cost[10] += (double)(P->lev[l].nbox * P->lev[l].P);
+        P->cost[11] = (double)(P->lev[L].nbox * P->lev[L].P);
         if (P->adaptive) {
             std::vector<AdLevel> al(L + 1);
             for (int l = 2; l <= L; ++l) al[l] = AdLevel{P->lev[l].mofs, P->lev[l].lofs, P->lev[l].p, (float)P->lev[l].s};
@@ -949,6 +956,29 @@ int hfmm_matvec(hfmm_plan* P, const void* density, void* potential, int nrhs, vo
     return hfmm_matvec_parts(P, density, potential, nrhs, 7, stream);
 }
 
+int hfmm_matvec_host(hfmm_plan* P, const void* density, void* potential, int nrhs, void* stream) {
+    if (!P || !density || !potential || nrhs < 1) return HFMM_E_INVALID;
+    HFMM_GUARD_BEGIN
+    cudaStream_t st = (cudaStream_t)stream;
+    const int R = std::min(nrhs, 64);
+    const size_t need = (size_t)R * (size_t)P->N;
+    if (P->hio_in.n < need) {
+        P->hio_in.alloc(need, &P->dev_bytes);
+        P->hio_out.alloc(need, &P->dev_bytes);
+    }
+    for (int r0 = 0; r0 < nrhs; r0 += R) {
+        const int Rc = std::min(R, nrhs - r0);
+        const size_t off = (size_t)r0 * (size_t)P->N, bytes = sizeof(float2) * (size_t)Rc * (size_t)P->N;
+        HFMM_CUDA(cudaMemcpyAsync(P->hio_in.p, (const float2*)density + off, bytes, cudaMemcpyHostToDevice, st));
+        const int s = hfmm_matvec_parts(P, P->hio_in.p, P->hio_out.p, Rc, 7, stream);
+        if (s != HFMM_OK) return s;
+        HFMM_CUDA(cudaMemcpyAsync((float2*)potential + off, P->hio_out.p, bytes, cudaMemcpyDeviceToHost, st));
+    }
+    HFMM_CUDA(cudaStreamSynchronize(st));
+    return HFMM_OK;
+    HFMM_GUARD_END
+}
+
 int hfmm_matvec_timed(hfmm_plan* P, const void* density, void* potential, float* stage_ms, void* stream) {
     if (!P || !density || !potential || !stage_ms) return HFMM_E_INVALID;
     cudaEvent_t ev[HFMM_NUM_STAGES + 1] = {};
@@ -996,7 +1026,7 @@ int hfmm_device_status(hfmm_plan* P, void* stream) {
 
 int hfmm_plan_costs(const hfmm_plan* P, double* costs) {
     if (!P || !costs) return HFMM_E_INVALID;
-    for (int q = 0; q < 8; ++q) costs[q] = P->cost[q];
+    for (int q = 0; q < HFMM_NUM_COSTS; ++q) costs[q] = P->cost[q];
     return HFMM_OK;
 }
 

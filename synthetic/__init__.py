@@ -12,6 +12,8 @@ from .meshes import (  # noqa: F401
     ellipsoid_mesh,
     star_mesh,
     geodesic_sphere,
+    triangle_soup,
+    corner_lattice_soup,
     serving_shape,
     serving_requests,
     workload_mesh,

@@ -153,6 +153,33 @@ def star_mesh(level: int, seed: int, amplitude: float = 0.2):
     return v * (1.0 + amplitude * s)[:, None], f
 
 
+def triangle_soup(n_tri: int, seed: int, size: float = 0.02, extent: float = 0.99):
+    """n_tri small random triangles (edges about `size`) with centres uniform in the
+    cube [-extent, extent]^3: points fill a volume, so the leaves of an octree over
+    them are full and neighbouring leaves meet at every relative position."""
+    rng = np.random.default_rng(seed)
+    c = rng.uniform(-extent, extent, (n_tri, 3))
+    v = c[:, None, :] + size * rng.standard_normal((n_tri, 3, 3))
+    f = np.arange(3 * n_tri, dtype=np.int64).reshape(n_tri, 3)
+    return v.reshape(-1, 3), f
+
+
+def corner_lattice_soup(cells: int, margin: float, seed: int, size: float = 3e-4):
+    """Tiny random triangles centred near the 8 corners of every cell of a
+    cells^3 grid over [-1, 1]^3 (a fraction `margin` of the cell side inside
+    each corner): points of neighbouring cells then sit at every relative
+    position up to the far corners of a 2 x 2 x 2 block of cells."""
+    rng = np.random.default_rng(seed)
+    h = 2.0 / cells
+    one = np.array([margin, 1.0 - margin]) * h
+    base = -1.0 + h * np.arange(cells)
+    ax = (base[:, None] + one[None, :]).ravel()
+    c = np.stack(np.meshgrid(ax, ax, ax, indexing="ij"), axis=-1).reshape(-1, 3)
+    v = c[:, None, :] + size * rng.standard_normal((c.shape[0], 3, 3))
+    f = np.arange(3 * c.shape[0], dtype=np.int64).reshape(-1, 3)
+    return v.reshape(-1, 3), f
+
+
 def geodesic_sphere(nu: int):
     """Unit sphere from the icosahedron with every face cut into nu^2 triangles
     (geodesic frequency nu): 20 nu^2 triangles, 10 nu^2 + 2 vertices."""

@@ -73,6 +73,31 @@ def test_fullsize_matvec_sampled_rows_against_direct_sum(name, k):
         plan.close()
 
 
+def test_fullsize_solve_true_residual_against_oracle():
+    """GMRES(50) to 1e-4 on the 1.97 M-point sphere at k = 20 (the single large solve):
+    the solution's true residual b - Z x, with Z the oracle's exact FP64 operator, on
+    1,024 sampled rows (plus the two ends), is within 1e-4 + 10 %."""
+    name, k = WORKLOADS[1]
+    V, F = synthetic.workload_mesh(name)
+    plan = pkg.Plan(V, F, k, restart=50, tol=1e-4)
+    try:
+        b = torch.empty(plan.n, dtype=torch.complex64, device="cuda")
+        plan.rhs_planewave([0.0, 0.0, 1.0], b)
+        x = torch.empty_like(b)
+        st, its, rr = plan.solve(b, x)
+        assert st == pkg.HFMM_OK and rr[0] <= 1e-4
+        torch.cuda.synchronize()
+        xg = x.cpu().numpy().astype(np.complex128)
+        rng = np.random.default_rng(21)
+        rows = np.unique(np.concatenate([rng.choice(plan.n, 1024, replace=False), [0, plan.n - 1]]))
+        X, _, _ = oracle.points(V, F)
+        zx = oracle.direct_rows(V, F, k, oracle.near_radius(V, F, plan.cfg.near_factor), rows, xg)
+        bb = oracle.plane_wave(X[rows], k, (0.0, 0.0, 1.0))
+        assert np.linalg.norm(zx - bb) / np.linalg.norm(bb) <= 1.1e-4
+    finally:
+        plan.close()
+
+
 def test_fullsize_tensor_core_far_field_against_simt():
     name, k = WORKLOADS[0]
     V, F = synthetic.workload_mesh(name)

@@ -346,6 +346,25 @@ def test_green_kernel_symmetry():
     assert abs(v @ Ku - u @ Kv) < 1e-12 * abs(v @ Ku)
 
 
+def test_point_sum_rows_brute_force():
+    """Sampled rows of the raw kernel sum against a numpy double loop written here."""
+    rng = np.random.default_rng(8)
+    X = rng.standard_normal((300, 3))
+    X[7] = X[3]  # a coincident pair: R = 0 is skipped
+    W = rng.uniform(0.5, 1.5, 300)
+    s = synthetic.random_density(300, 9)
+    rows = np.array([0, 3, 7, 150, 299])
+    got = oracle.point_sum_rows(X, W, 4.0, s, rows)
+    for q, i in enumerate(rows):
+        acc = 0j
+        for j in range(300):
+            R = np.sqrt(((X[i] - X[j]) ** 2).sum())
+            if j != i and R > 0:
+                acc += W[j] * np.exp(4j * R) / (4 * np.pi * R) * s[j]
+        assert abs(got[q] - acc) < 1e-13 * abs(acc)
+    assert np.allclose(oracle.point_sum(X, W, 4.0, s)[rows], got, rtol=1e-14, atol=0)
+
+
 def test_operator_forms_agree():
     """dense Z, the row-by-row definition, and point part + sparse correction."""
     V, F = synthetic.sphere_mesh(1)
