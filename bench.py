@@ -39,6 +39,7 @@ WORKLOADS = {
 
 
 DRAM_PROFILE = os.path.join(ROOT, "profiles", "dram_sphere_655360.md")
+DRAM_WORKLOAD = "sphere_655360"  # the workload that capture ran
 
 
 def _source_sha(fname):
@@ -48,9 +49,12 @@ def _source_sha(fname):
         return hashlib.sha256(f.read()).hexdigest()[:16]
 
 
-def _ncu_dram(kernel):
+def _ncu_dram(kernel, workload):
     """DRAM bytes (read + write) of one launch of `kernel` on the 1.97 M-point sphere, from the
-    committed ncu summary; None when the kernel's source file changed since the capture."""
+    committed ncu summary; None on another workload or when the kernel's source file changed
+    since the capture."""
+    if workload != DRAM_WORKLOAD:
+        return None, f"no ncu capture of this workload (the committed one is {DRAM_WORKLOAD})"
     try:
         with open(DRAM_PROFILE) as f:
             kv = dict(line.strip().split(" = ", 1) for line in f if " = " in line and line.startswith("    "))
@@ -499,6 +503,12 @@ def main():
                     help="mixed-precision refinement to 1e-6 beside plain GMRES to 1e-4 (default workload: the ellipsoid)")
     ap.add_argument("--refine-pmin", type=int, default=12, help="minimum order of the outer (residual) plan")
     ap.add_argument("--restart", type=int, default=0, help="> 0: GMRES restart length instead of the workload's")
+    ap.add_argument("--p2p-kernel", type=int, default=None, help="near-field kernel (0 staged, 1 packed)")
+    ap.add_argument("--overlap", type=int, default=None, help="1: two-branch captured matvec, 0: sequential")
+    ap.add_argument("--m2l-kernel", type=int, default=None,
+                    help="tensor-core M2L (0 source-stationary items, 1 target-stationary tiles)")
+    ap.add_argument("--tc-group", type=int, default=None, help="work items per tensor-core block (8, 16, 32)")
+    ap.add_argument("--autotune", type=int, default=None, help="1: tune the kernel choices at plan creation")
     ap.add_argument("--serve", type=int, default=0, help="> 0: serving workload with this many requests")
     ap.add_argument("--serve-nmax", type=int, default=1_000_000)
     ap.add_argument("--serve-kmax", type=float, default=30.0)
@@ -540,6 +550,9 @@ def main():
         cfg["adaptive"] = 1
     if args.leaf_max > 0:
         cfg["leaf_max"] = args.leaf_max
+    for key in ("p2p_kernel", "m2l_kernel", "overlap", "tc_group", "autotune"):
+        if getattr(args, key) is not None:
+            cfg[key] = getattr(args, key)
     V, F = synthetic.workload_mesh(mesh)
     N = 3 * F.shape[0]
     stream = torch.cuda.current_stream()
@@ -669,15 +682,17 @@ def main():
     fp32_peak = props.multi_processor_count * 128 * 2 * smax * 1e6 / 1e12  # TFLOP/s
     dom = max(stages, key=stages.get)
     tc_cmacs = costs["m2l_tc_cmacs"]
+    tuning = plan.tuning()
     # stage -> (bound, algorithmic amount per launch, unit, peak, convention, kernel name for ncu)
     work = {
         "p2p": ("alu", costs["p2p_pairs"] * 24 / 1e12, "TFLOP/s", fp32_peak, "24 flop per source-target pair",
-                "k_p2p_staged"),
+                "k_p2p_packed" if tuning["p2p_kernel"]["choice"] == 1 else "k_p2p_staged"),
         "m2l_simt": ("alu", (costs["m2l_cmacs"] - tc_cmacs) * 8 / 1e12, "TFLOP/s", fp32_peak,
                      "8 flop per complex multiply-add, P_l^2 per translation (SIMT levels)", None),
         "m2l": ("tensor", tc_cmacs * 8 / 1e12, "TFLOP/s", bf16_peak,
                 "the method's flops: 8 per complex multiply-add, P^2 per translation "
-                f"({int(costs['m2l_tc_translations'])} translations per launch)", "k_m2l_tc"),
+                f"({int(costs['m2l_tc_translations'])} translations per launch)",
+                "k_m2l_ts" if tuning["m2l_kernel"]["choice"] == 1 else "k_m2l_tc"),
         "corr": ("hbm", (costs["corr_nnz"] * 12 + costs["n_points"] * 16) / 1e9, "GB/s", hbm,
                  "12 B per nonzero + 16 B per row", "k_corr"),
     }
@@ -687,7 +702,7 @@ def main():
     def _roof(stage):
         bound, amount, unit, peak, note, kname = work[stage]
         achieved = amount / (stages[stage] / 1e3)
-        traffic, tnote = _ncu_dram(kname) if kname else (None, "no ncu capture")
+        traffic, tnote = _ncu_dram(kname, args.workload) if kname else (None, "no ncu capture")
         return {"kernel": kname or stage, "stage": stage, "bound": bound, "achieved": achieved, "peak": peak,
                 "unit": unit, "frac": achieved / peak, "traffic": traffic, "traffic_source": tnote,
                 "peak_source": peak_source[bound], "work_per_launch": note}
@@ -712,7 +727,7 @@ def main():
     tree = {}
     for stg, (kname, nbytes, note) in tree_model.items():
         gbs = nbytes / 1e9 / (stages[stg] / 1e3)
-        traffic, tnote = _ncu_dram(kname)
+        traffic, tnote = _ncu_dram(kname, args.workload)
         tree[stg] = {"ms": stages[stg], "algorithmic_bytes": nbytes, "achieved_gbs": gbs, "frac_of_hbm": gbs / hbm,
                      "model": note, "traffic": traffic, "traffic_source": tnote,
                      "dram_gbs": traffic / 1e9 / (stages[stg] / 1e3) if traffic else None}
@@ -746,7 +761,8 @@ def main():
                        "m2l_translations": info["m2l_translations"], "device_bytes": info["device_bytes"],
                        "tree": "adaptive" if args.adaptive else "uniform", "leaves": info["n_leaves"],
                        "parallelism": "replicas" if world > 1 else "single GPU",
-                       "l2": f"inputs larger than L2 (plan holds {info['device_bytes'] / 1e9:.2f} GB)"},
+                       "l2": f"inputs larger than L2 (plan holds {info['device_bytes'] / 1e9:.2f} GB)",
+                       "kernels": tuning, "autotune": plan.cfg.autotune},
             "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99)),
                            "mean": statistics.mean(step_ms),
                            "std": statistics.pstdev(step_ms) if len(step_ms) > 1 else 0.0},

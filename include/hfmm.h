@@ -83,6 +83,23 @@ typedef struct {
                            level touch, every other pair through M2L between same-level boxes
                            (the interaction lists of Sec. 2.3 read for unequal leaves).  Batched
                            right-hand sides then run one at a time.  0: uniform depth (0) */
+    int autotune;       /* 1: at plan creation, time each tunable choice below that is left at -1
+                           (or 0 for tc_group) on the plan's own data with CUDA events and keep the
+                           fastest (the GPU counterpart of the paper's search for task size and
+                           leaf size, Sec. 3.2 / 6.2); hfmm_plan_tuning reports the result.
+                           0: use the defaults (0) */
+    int p2p_kernel;     /* near-field kernel: 0 staged (four lanes per target), 1 packed FP32x2
+                           (one lane per target, two sources per instruction), -1 default/tuned (-1) */
+    int m2l_kernel;     /* tensor-core M2L: 0 source-stationary work items (one offset's operator
+                           applied to gathered multipoles, bulk reductions into the locals);
+                           1 target-stationary tiles (a block keeps 256 targets' locals on chip and
+                           applies the 56 canonical operators of the offsets' reflection classes,
+                           writing each local once); -1 default/tuned (-1) */
+    int tc_group;       /* work items per tensor-core block: 8, 16 or 32; 0 default/tuned (0) */
+    int overlap;        /* single right-hand-side matvec on a uniform tree: 1 near field and
+                           correction on a second branch beside the far field, the whole matvec
+                           captured once as a CUDA graph and replayed; 0 one stage after another;
+                           -1 default/tuned (-1) */
 } hfmm_config;
 
 /* Fills *cfg with the defaults shown in parentheses above (p_min = 7). */
@@ -239,6 +256,29 @@ int hfmm_plan_costs(const hfmm_plan* plan, double* costs);
  * Returns HFMM_OK or HFMM_E_TIMEOUT.
  */
 int hfmm_device_status(hfmm_plan* plan, void* stream);
+
+/*
+ * The plan's kernel choices (HOST, HFMM_NUM_TUNABLES ints): 0 near-field kernel
+ * (p2p_kernel), 1 tensor-core M2L kernel (m2l_kernel), 2 work items per tensor-core
+ * block (tc_group), 3 two-branch captured matvec (overlap) -- the configured value,
+ * or when that was left open the default or, with autotune = 1, the fastest measured.
+ * tuned_ms (HOST, HFMM_NUM_TUNABLES x HFMM_TUNE_CANDIDATES floats, may be NULL): the
+ * device time of one matvec with each candidate of each tunable, in the order of the
+ * candidates (near field: 0, 1; M2L kernel: 0, 1; tc_group: 8, 16, 32; overlap: 0, 1),
+ * -1 where not measured.
+ */
+#define HFMM_NUM_TUNABLES 4
+#define HFMM_TUNE_CANDIDATES 4
+int hfmm_plan_tuning(const hfmm_plan* plan, int* choices, float* tuned_ms);
+
+/*
+ * The plan-time tuner's rule, on its own (host only, no device work): given the measured
+ * time ms[c] of candidate c of `tunable` (n candidates in the order above; a negative or
+ * non-finite entry means not measured), *value = the fastest measured candidate's value,
+ * except that the default stays unless the fastest is at least 2 % faster.  Returns
+ * HFMM_E_INVALID for a bad tunable or count, or when nothing was measured.
+ */
+int hfmm_tune_choose(int tunable, const float* ms, int n, int* value);
 
 /* Number of kernels this plan has launched on the device since it was created. */
 int64_t hfmm_launch_count(const hfmm_plan* plan);

@@ -30,7 +30,7 @@ EXPORTED = [
     "hfmm_plan_info", "hfmm_matvec", "hfmm_matvec_parts", "hfmm_direct", "hfmm_rhs_planewave",
     "hfmm_solve", "hfmm_solve_refined", "hfmm_status_string", "hfmm_last_error", "hfmm_matvec_timed",
     "hfmm_launch_count", "hfmm_plan_costs", "hfmm_point_sum_noalloc", "hfmm_device_status", "hfmm_field",
-    "hfmm_matvec_host",
+    "hfmm_matvec_host", "hfmm_plan_tuning", "hfmm_tune_choose",
 ]
 HFMM_NOALLOC_MAX_POINTS = 262144
 STAGES = ["prep", "p2p", "p2m", "m2m", "m2l_simt", "m2l", "l2l", "l2p", "corr", "output"]
@@ -50,6 +50,11 @@ class hfmm_config(ctypes.Structure):
         ("mem_budget_bytes", ctypes.c_double),
         ("m2l_tensor", ctypes.c_int),
         ("adaptive", ctypes.c_int),
+        ("autotune", ctypes.c_int),
+        ("p2p_kernel", ctypes.c_int),
+        ("m2l_kernel", ctypes.c_int),
+        ("tc_group", ctypes.c_int),
+        ("overlap", ctypes.c_int),
     ]
 
 
@@ -83,6 +88,9 @@ def lib():
         L.hfmm_matvec.argtypes = [vp, vp, vp, ctypes.c_int, vp]
         L.hfmm_matvec_parts.argtypes = [vp, vp, vp, ctypes.c_int, ctypes.c_int, vp]
         L.hfmm_matvec_host.argtypes = [vp, vp, vp, ctypes.c_int, vp]
+        L.hfmm_plan_tuning.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_float)]
+        L.hfmm_tune_choose.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_float), ctypes.c_int,
+                                       ctypes.POINTER(ctypes.c_int)]
         L.hfmm_direct.argtypes = [vp, vp, vp, ctypes.c_int, vp]
         L.hfmm_rhs_planewave.argtypes = [vp, dp, ctypes.c_int, vp, vp]
         L.hfmm_solve.argtypes = [vp, vp, vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), dp, vp]
@@ -248,6 +256,29 @@ def hfmm_plan_costs(plan):
     return dict(zip(keys, [float(v) for v in c]))
 
 
+TUNABLES = [("p2p_kernel", [0, 1]), ("m2l_kernel", [0, 1]), ("tc_group", [8, 16, 32]), ("overlap", [0, 1])]
+
+
+def hfmm_plan_tuning(plan):
+    """{tunable: {"choice": value, "ms": {candidate: device ms of one matvec}}} (timed ones only)."""
+    ch = (ctypes.c_int * 4)()
+    ms = (ctypes.c_float * 16)()
+    _check(lib().hfmm_plan_tuning(plan, ch, ms), "hfmm_plan_tuning")
+    out = {}
+    for a, (name, cands) in enumerate(TUNABLES):
+        timed = {c: float(ms[4 * a + q]) for q, c in enumerate(cands) if ms[4 * a + q] >= 0}
+        out[name] = {"choice": int(ch[a]), "ms": timed}
+    return out
+
+
+def hfmm_tune_choose(tunable, ms):
+    """The tuner's rule on given timings (ms per candidate, negative = not measured)."""
+    arr = (ctypes.c_float * len(ms))(*[float(v) for v in ms])
+    v = ctypes.c_int()
+    _check(lib().hfmm_tune_choose(int(tunable), arr, len(ms), ctypes.byref(v)), "hfmm_tune_choose")
+    return int(v.value)
+
+
 def hfmm_point_sum_noalloc(xyz, w, density, potential, k, stream=None):
     """Point sum through the scratch-free entry point; xyz [n,3] and w [n] are
     float64 CUDA tensors, density / potential complex64 CUDA tensors."""
@@ -367,6 +398,9 @@ class Plan:
 
     def costs(self):
         return hfmm_plan_costs(self.handle)
+
+    def tuning(self):
+        return hfmm_plan_tuning(self.handle)
 
     def device_status(self, stream=None):
         return hfmm_device_status(self.handle, stream)

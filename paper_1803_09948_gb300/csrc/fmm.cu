@@ -179,6 +179,78 @@ __device__ __forceinline__ void p2p_span(float tx, float ty, float tz, int k0, i
 }
 
 constexpr int kStagedNbr = 64;  // most source leaves the staged kernel takes (27 in a uniform tree)
+
+// Neighbourhood table of target leaf b for the staged near-field kernels, built by one warp
+// in parallel (one neighbour per lane, counts prefix-summed with shuffles): entry q names
+// the first point s_j0[q] and count s_cnt[q] of source leaf q (q = 0: the target leaf
+// itself), its first staged index s_off[q] and the shift s_sh[q] of its frame into b's.
+// pad: the self segment and the total are rounded up to even lengths.  *s_nl = entries;
+// s_off[*s_nl] = total.
+struct NbrTable {
+    int off[kStagedNbr + 1], j0[kStagedNbr], cnt[kStagedNbr], nl;
+    float4 sh[kStagedNbr];
+};
+
+__device__ void build_nbr_table(int b, const int32_t* __restrict__ leaf_start, const int4* __restrict__ leaf_ijk,
+                                const int32_t* __restrict__ nbr_ptr, const int32_t* __restrict__ nbr, float shift,
+                                bool pad, NbrTable& T) {
+    const int lane = threadIdx.x & 31;
+    const int nb0 = __ldg(nbr_ptr + b), nn = __ldg(nbr_ptr + b + 1) - nb0;
+    const int4 tij = __ldg(leaf_ijk + b);
+    const int j0b = __ldg(leaf_start + b), nself = __ldg(leaf_start + b + 1) - j0b;
+    if (lane == 0) {
+        T.j0[0] = j0b;
+        T.cnt[0] = nself;
+        T.off[0] = 0;
+        T.sh[0] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    int base = pad ? ((nself + 1) & ~1) : nself, k = 1;
+    for (int q0 = 0; q0 < nn; q0 += 32) {
+        const int q = q0 + lane;
+        int sl = -1, cnt = 0, j0 = 0;
+        if (q < nn) {
+            sl = __ldg(nbr + nb0 + q);
+            if (sl == b) sl = -1;
+        }
+        if (sl >= 0) {
+            j0 = __ldg(leaf_start + sl);
+            cnt = __ldg(leaf_start + sl + 1) - j0;
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, sl >= 0);
+        int x = cnt;  // inclusive scan of the counts over the lanes
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, x, d);
+            if (lane >= d) x += y;
+        }
+        const int slot = k + __popc(m & ((1u << lane) - 1u));
+        if (sl >= 0 && slot < kStagedNbr) {
+            const int4 sij = __ldg(leaf_ijk + sl);
+            T.j0[slot] = j0;
+            T.cnt[slot] = cnt;
+            T.off[slot] = base + x - cnt;
+            T.sh[slot] = make_float4((float)(sij.x - tij.x) * shift, (float)(sij.y - tij.y) * shift,
+                                     (float)(sij.z - tij.z) * shift, 0.f);
+        }
+        base += __shfl_sync(0xffffffffu, x, 31);
+        k += __popc(m);
+    }
+    if (lane == 0) {
+        T.off[k] = pad ? ((base + 1) & ~1) : base;
+        T.nl = k;
+    }
+}
+
+// segment q of staged index p: the last q with T.off[q] <= p
+__device__ __forceinline__ int nbr_segment(const NbrTable& T, int p) {
+    int lo = 0, hi = T.nl;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (T.off[mid] <= p) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
 template <bool POLY>
 __global__ void __launch_bounds__(128) k_p2p_staged(const int32_t* __restrict__ leaf_start,
                                                     const int4* __restrict__ leaf_ijk,
@@ -189,42 +261,23 @@ __global__ void __launch_bounds__(128) k_p2p_staged(const int32_t* __restrict__ 
                                                     float2* __restrict__ phi) {
     extern __shared__ float4 sp[];  // [cap]: shifted position, Re sigma
     float* sim = reinterpret_cast<float*>(sp + cap);  // [cap]: Im sigma
-    __shared__ int s_off[kStagedNbr + 1], s_leaf[kStagedNbr], s_nl;
+    __shared__ NbrTable T;
     const int b = blockIdx.x, tid = threadIdx.x;
-    const int4 tij = __ldg(leaf_ijk + b);
-    const int nb0 = __ldg(nbr_ptr + b), nn = __ldg(nbr_ptr + b + 1) - nb0;
-    if (tid == 0) {
-        int k = 0, o = 0;
-        s_leaf[k++] = b;  // self first
-        for (int q = 0; q < nn; ++q) {
-            const int sl = __ldg(nbr + nb0 + q);
-            if (sl != b) s_leaf[k++] = sl;
-        }
-        for (int q = 0; q < k; ++q) {
-            s_off[q] = o;
-            o += __ldg(leaf_start + s_leaf[q] + 1) - __ldg(leaf_start + s_leaf[q]);
-        }
-        s_off[k] = o;
-        s_nl = k;
-    }
+    if (tid < 32) build_nbr_table(b, leaf_start, leaf_ijk, nbr_ptr, nbr, shift, false, T);
     __syncthreads();
-    const int nl = s_nl, total = s_off[nl];
-    for (int q = 0; q < nl; ++q) {
-        const int sl = s_leaf[q];
-        const int j0 = __ldg(leaf_start + sl), n = s_off[q + 1] - s_off[q];
-        const int4 sij = __ldg(leaf_ijk + sl);
-        const float ox = (float)(sij.x - tij.x) * shift, oy = (float)(sij.y - tij.y) * shift,
-                    oz = (float)(sij.z - tij.z) * shift;
-        for (int e = tid; e < n; e += blockDim.x) {
-            const float4 p = __ldg(pts + j0 + e);
-            const float2 g = __ldg(sig + j0 + e);
-            sp[s_off[q] + e] = make_float4(p.x + ox, p.y + oy, p.z + oz, g.x);
-            sim[s_off[q] + e] = g.y;
-        }
+    const int total = T.off[T.nl];
+    for (int p = tid; p < total; p += blockDim.x) {  // one flat pass: loads of all leaves in flight
+        const int q = nbr_segment(T, p);
+        const int e = p - T.off[q];
+        const float4 pt = __ldg(pts + T.j0[q] + e);
+        const float2 g = __ldg(sig + T.j0[q] + e);
+        const float4 o = T.sh[q];
+        sp[p] = make_float4(pt.x + o.x, pt.y + o.y, pt.z + o.z, g.x);
+        sim[p] = g.y;
     }
     __syncthreads();
     const int warp = tid >> 5, lane = tid & 31;
-    const int nself = s_off[1];
+    const int nself = T.cnt[0];
     const int tloc = lane / kP2PSub, sub = lane % kP2PSub;
     for (int tile = warp; tile * kP2PTile < nself; tile += 4) {
         const int it = tile * kP2PTile + tloc;
@@ -306,58 +359,37 @@ __global__ void __launch_bounds__(kPkThreads) k_p2p_packed(const int32_t* __rest
                                                            float2* __restrict__ phi) {
     extern __shared__ float4 sq[];                                   // [2 cap_pairs]
     float2* sim = reinterpret_cast<float2*>(sq + 2 * cap_pairs);    // [cap_pairs]
-    __shared__ int s_off[kStagedNbr + 1], s_leaf[kStagedNbr], s_nl;
+    __shared__ NbrTable T;
     __shared__ float2 s_red[kPkThreads];
     const int b = blockIdx.x, tid = threadIdx.x;
-    const int4 tij = __ldg(leaf_ijk + b);
-    const int nb0 = __ldg(nbr_ptr + b), nn = __ldg(nbr_ptr + b + 1) - nb0;
-    if (tid == 0) {
-        int k = 0, o = 0;
-        s_leaf[k++] = b;  // self first
-        for (int q = 0; q < nn; ++q) {
-            const int sl = __ldg(nbr + nb0 + q);
-            if (sl != b) s_leaf[k++] = sl;
-        }
-        for (int q = 0; q < k; ++q) {
-            s_off[q] = o;
-            o += __ldg(leaf_start + s_leaf[q] + 1) - __ldg(leaf_start + s_leaf[q]);
-            if (q == 0) o = (o + 1) & ~1;  // the self segment ends on a pair boundary
-        }
-        s_off[k] = (o + 1) & ~1;
-        s_nl = k;
-    }
+    if (tid < 32) build_nbr_table(b, leaf_start, leaf_ijk, nbr_ptr, nbr, shift, true, T);
     __syncthreads();
-    const int nl = s_nl, npair = s_off[nl] >> 1;
-    const int nself = __ldg(leaf_start + b + 1) - __ldg(leaf_start + b);
-    const int qself = s_off[1] >> 1;  // pairs of the self segment
+    const int total = T.off[T.nl], npair = total >> 1;
+    const int nself = T.cnt[0];
+    const int qself = T.off[1] >> 1;  // pairs of the self segment (padded to even)
     float* sf = reinterpret_cast<float*>(sq);
     float* sfi = reinterpret_cast<float*>(sim);
-    for (int q = 0; q < nl; ++q) {
-        const int sl = s_leaf[q];
-        const int j0 = __ldg(leaf_start + sl), n = __ldg(leaf_start + sl + 1) - j0;
-        const int4 sij = __ldg(leaf_ijk + sl);
-        const float ox = (float)(sij.x - tij.x) * shift, oy = (float)(sij.y - tij.y) * shift,
-                    oz = (float)(sij.z - tij.z) * shift;
-        const int end = (q + 1 < nl) ? s_off[q + 1] : s_off[nl];
-        for (int e = tid; e < end - s_off[q]; e += kPkThreads) {
-            const int p = s_off[q] + e, pq = p >> 1, h = p & 1;
-            float x = kPkPad, y = kPkPad, z = kPkPad, sr = 0.f, si = 0.f;
-            if (e < n) {
-                const float4 pt = __ldg(pts + j0 + e);
-                const float2 g = __ldg(sig + j0 + e);
-                x = pt.x + ox;
-                y = pt.y + oy;
-                z = pt.z + oz;
-                sr = g.x;
-                si = g.y;
-            }
-            float* r = sf + 8 * pq;
-            r[h] = x;
-            r[2 + h] = y;
-            r[4 + h] = z;
-            r[6 + h] = sr;
-            sfi[2 * pq + h] = si;
+    for (int p = tid; p < total; p += kPkThreads) {  // one flat pass: loads of all leaves in flight
+        const int q = nbr_segment(T, p);
+        const int e = p - T.off[q];
+        float x = kPkPad, y = kPkPad, z = kPkPad, sr = 0.f, si = 0.f;
+        if (e < T.cnt[q]) {
+            const float4 pt = __ldg(pts + T.j0[q] + e);
+            const float2 g = __ldg(sig + T.j0[q] + e);
+            const float4 o = T.sh[q];
+            x = pt.x + o.x;
+            y = pt.y + o.y;
+            z = pt.z + o.z;
+            sr = g.x;
+            si = g.y;
         }
+        const int pq = p >> 1, h = p & 1;
+        float* r = sf + 8 * pq;
+        r[h] = x;
+        r[2 + h] = y;
+        r[4 + h] = z;
+        r[6 + h] = sr;
+        sfi[2 * pq + h] = si;
     }
     __syncthreads();
     const int TT = min(nself, kPkThreads);  // target slots per round
@@ -1296,24 +1328,16 @@ static void launch_translate(hfmm_plan* P, const TransItem* items, float2* coef,
     ++P->launches;
 }
 
-void run_matvec_sorted(hfmm_plan* P, int parts, cudaStream_t st) {
+// Near field (P2P between neighbouring leaves, or zeros): the first writer of P->phi.
+static void near_stage(hfmm_plan* P, int parts, cudaStream_t st) {
     int64_t N = P->N;
     mark_stage(P, 1, st);
     if (parts & 1) {
         const size_t staged = (size_t)P->p2p_cap * (sizeof(float4) + sizeof(float));
         if (P->p2p_cap > 0 && staged <= 96 * 1024 && P->p2p_maxnbr <= kStagedNbr) {
-            if (staged > 48 * 1024) {
-                HFMM_CUDA(cudaFuncSetAttribute(k_p2p_staged<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               (int)staged));
-                HFMM_CUDA(cudaFuncSetAttribute(k_p2p_staged<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               (int)staged));
-            }
             const int cap_pairs = P->p2p_cap / 2 + 2;
             const size_t pk_smem = (size_t)cap_pairs * (2 * sizeof(float4) + sizeof(float2));
             if (P->poly_p2p && P->p2p_variant == 1) {
-                if (pk_smem > 48 * 1024)
-                    HFMM_CUDA(cudaFuncSetAttribute(k_p2p_packed, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                   (int)pk_smem));
                 k_p2p_packed<<<(unsigned)P->nleaf, kPkThreads, pk_smem, st>>>(
                     P->leaf_start.p, P->leaf_ijk.p, P->nbr_ptr.p, P->nbr.p, P->pts.p, P->sig.p, P->p2p_shift,
                     cap_pairs, P->phi.p);
@@ -1338,6 +1362,11 @@ void run_matvec_sorted(hfmm_plan* P, int parts, cudaStream_t st) {
     } else {
         HFMM_CUDA(cudaMemsetAsync(P->phi.p, 0, sizeof(float2) * N, st));
     }
+}
+
+// Far field up to the leaves' locals: P2M (and P2L), M2M (and M2P), M2L, L2L.
+static void far_stage(hfmm_plan* P, int parts, cudaStream_t st) {
+    int64_t N = P->N;
     mark_stage(P, 2, st);
     int L = P->L;
     bool far = (parts & 2) && L >= 2;
@@ -1349,8 +1378,6 @@ void run_matvec_sorted(hfmm_plan* P, int parts, cudaStream_t st) {
             const LeafFilter f = leaf_filter(P, l);
             if (!p2m_l2p_fixed(true, P, lv, f, st)) {
                 const size_t smem = p2m_smem_bytes(lv.p);
-                if (smem > 48 * 1024)
-                    HFMM_CUDA(cudaFuncSetAttribute(k_p2m, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
                 k_p2m<<<(unsigned)P->nleaf, 128, smem, st>>>(P->leaf_start.p, P->pts.p, P->sig.p, lv.p, (float)lv.s,
                                                                P->coef.p + lv.mofs, f.lev, f.l, f.box);
             }
@@ -1390,7 +1417,11 @@ void run_matvec_sorted(hfmm_plan* P, int parts, cudaStream_t st) {
                              r.pout_max >= 200 ? 3 : r.pout_max >= 100 ? 2 : 1);
     mark_stage(P, 5, st);
     if (far) {
-        if (P->n_tc_groups > 0) {
+        if (P->m2l_variant == 1 && P->n_ts_tiles > 0) {
+            m2l_ts_launch(P->ts_tiles.p, P->n_ts_tiles, P->ts_max_tile_floats, P->ts_max_chunks, P->ts_chunks.p,
+                          P->ts_cols.p, P->m2l_canon.p, P->coef.p, P->dev_err.p, st);
+            ++P->launches;
+        } else if (P->n_tc_groups > 0) {
             m2l_tc_launch(P->tc_groups.p, P->n_tc_groups, P->items.p, P->item_cols.p, P->aops.p, P->coef.p,
                           P->dev_err.p, 1, st);
             ++P->launches;
@@ -1409,6 +1440,13 @@ void run_matvec_sorted(hfmm_plan* P, int parts, cudaStream_t st) {
                                  HFMM_TRANS_NB, st);
             }
         }
+}
+
+// L2P: the leaves' locals at their points, added into P->phi.
+static void l2p_stage(hfmm_plan* P, int parts, cudaStream_t st) {
+    int64_t N = P->N;
+    const int L = P->L;
+    const bool far = (parts & 2) && L >= 2;
     mark_stage(P, 7, st);
     if (far) {
         for (int l : P->leaf_levels) {
@@ -1420,12 +1458,99 @@ void run_matvec_sorted(hfmm_plan* P, int parts, cudaStream_t st) {
             ++P->launches;
         }
     }
+}
+
+// Near/self correction added into P->phi.
+static void corr_stage(hfmm_plan* P, int parts, cudaStream_t st) {
     mark_stage(P, 8, st);
     if ((parts & 4) && P->corr_nnz > 0) {
         launch_corr(P, st);
     }
     mark_stage(P, 9, st);
     HFMM_CUDA(cudaGetLastError());
+}
+
+
+// Once per device, before any capture: the near-field and P2M kernels may take up to the
+// device's opt-in shared memory per block (the launch decides how much it actually uses).
+void matvec_kernels_init() {
+    static bool done[64] = {};
+    int dev = 0;
+    HFMM_CUDA(cudaGetDevice(&dev));
+    if (dev >= 0 && dev < 64 && done[dev]) return;
+    int optin = 0;
+    HFMM_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    // the dynamic limit is what the opt-in maximum leaves beside the kernel's static shared memory
+    auto allow = [&](const void* fn) {
+        cudaFuncAttributes fa{};
+        HFMM_CUDA(cudaFuncGetAttributes(&fa, fn));
+        HFMM_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       optin - (int)fa.sharedSizeBytes));
+    };
+    allow((const void*)k_p2p_staged<true>);
+    allow((const void*)k_p2p_staged<false>);
+    allow((const void*)k_p2p_packed);
+    allow((const void*)k_p2m);
+    if (dev >= 0 && dev < 64) done[dev] = true;
+}
+
+// The four stages in order: every partial matvec and the stage-timed one run this way.
+static void matvec_sequential(hfmm_plan* P, int parts, cudaStream_t st) {
+    near_stage(P, parts, st);
+    far_stage(P, parts, st);
+    l2p_stage(P, parts, st);
+    corr_stage(P, parts, st);
+}
+
+// Two branches: the near field and the correction (both only touch sig and phi) on a side
+// stream beside the far field (sig -> coef); L2P, the last writer of phi, joins them.
+static void matvec_branches(hfmm_plan* P, cudaStream_t st, cudaStream_t side) {
+    MatvecGraph& G = P->mvg;
+    HFMM_CUDA(cudaEventRecord(G.fork, st));
+    HFMM_CUDA(cudaStreamWaitEvent(side, G.fork, 0));
+    near_stage(P, 7, side);
+    corr_stage(P, 7, side);
+    HFMM_CUDA(cudaEventRecord(G.join, side));
+    far_stage(P, 7, st);
+    HFMM_CUDA(cudaStreamWaitEvent(st, G.join, 0));
+    l2p_stage(P, 7, st);
+}
+
+// sig (sorted, pre-scaled densities) -> phi (sorted potentials) for the whole operator.
+// With mv_mode 1 (uniform trees) the two-branch form is captured once per plan into a CUDA
+// graph on a plan-owned stream and replayed on `st`: it reads and writes only plan-owned
+// buffers, so one capture serves every later matvec, including the solver's.
+void run_matvec_sorted(hfmm_plan* P, int parts, cudaStream_t st) {
+    if (parts != 7 || P->stage_ev || P->mv_mode == 0 || P->adaptive) {
+        matvec_sequential(P, parts, st);
+        return;
+    }
+    MatvecGraph& G = P->mvg;
+    if (!G.graph) {
+        if (!G.cap) HFMM_CUDA(cudaStreamCreateWithFlags(&G.cap, cudaStreamNonBlocking));
+        if (!G.side) HFMM_CUDA(cudaStreamCreateWithFlags(&G.side, cudaStreamNonBlocking));
+        if (!G.fork) HFMM_CUDA(cudaEventCreateWithFlags(&G.fork, cudaEventDisableTiming));
+        if (!G.join) HFMM_CUDA(cudaEventCreateWithFlags(&G.join, cudaEventDisableTiming));
+        const int64_t l0 = P->launches;
+        cudaGraph_t g = nullptr;
+        HFMM_CUDA(cudaStreamBeginCapture(G.cap, cudaStreamCaptureModeThreadLocal));
+        try {
+            matvec_branches(P, G.cap, G.side);
+        } catch (...) {
+            cudaStreamEndCapture(G.cap, &g);
+            if (g) cudaGraphDestroy(g);
+            P->launches = l0;
+            throw;
+        }
+        HFMM_CUDA(cudaStreamEndCapture(G.cap, &g));
+        const cudaError_t e = cudaGraphInstantiate(&G.graph, g, 0);
+        cudaGraphDestroy(g);
+        HFMM_CUDA(e);
+        G.launches = P->launches - l0;
+        P->launches = l0;
+    }
+    HFMM_CUDA(cudaGraphLaunch(G.graph, st));
+    P->launches += G.launches;
 }
 
 void run_direct_sorted(hfmm_plan* P, cudaStream_t st) {
@@ -1549,40 +1674,21 @@ __global__ void __launch_bounds__(256) k_p2p_b(const int32_t* __restrict__ leaf_
     int* sj = reinterpret_cast<int*>(sp + cap4);              // [cap4] sorted index of each staged source
     float2* G = reinterpret_cast<float2*>(sj + cap4);         // [kBChunk][64]
     float2* Sg = G + kBChunk * 64;                            // [kBChunk][kBMax]
-    __shared__ int s_off[29], s_leaf[28];
+    __shared__ NbrTable T;
     const int b = blockIdx.x, tid = threadIdx.x;
-    const int4 tij = __ldg(leaf_ijk + b);
-    const int nb0 = __ldg(nbr_ptr + b), nn = __ldg(nbr_ptr + b + 1) - nb0;
-    if (tid == 0) {
-        int k = 0, o = 0;
-        s_leaf[k++] = b;  // self first
-        for (int q = 0; q < nn; ++q) {
-            const int sl = __ldg(nbr + nb0 + q);
-            if (sl != b) s_leaf[k++] = sl;
-        }
-        for (int q = 0; q < k; ++q) {
-            s_off[q] = o;
-            o += __ldg(leaf_start + s_leaf[q] + 1) - __ldg(leaf_start + s_leaf[q]);
-        }
-        s_off[k] = o;
-        s_off[28] = k;
-    }
+    if (tid < 32) build_nbr_table(b, leaf_start, leaf_ijk, nbr_ptr, nbr, shift, false, T);
     __syncthreads();
-    const int nl = s_off[28], total = s_off[nl];
-    for (int q = 0; q < nl; ++q) {
-        const int sl = s_leaf[q];
-        const int j0 = __ldg(leaf_start + sl), n = s_off[q + 1] - s_off[q];
-        const int4 sij = __ldg(leaf_ijk + sl);
-        const float ox = (float)(sij.x - tij.x) * shift, oy = (float)(sij.y - tij.y) * shift,
-                    oz = (float)(sij.z - tij.z) * shift;
-        for (int e = tid; e < n; e += blockDim.x) {
-            const float4 p = __ldg(pts + j0 + e);
-            sp[s_off[q] + e] = make_float4(p.x + ox, p.y + oy, p.z + oz, 0.f);
-            sj[s_off[q] + e] = j0 + e;
-        }
+    const int total = T.off[T.nl];
+    for (int p = tid; p < total; p += blockDim.x) {  // one flat pass: loads of all leaves in flight
+        const int q = nbr_segment(T, p);
+        const int j = T.j0[q] + (p - T.off[q]);
+        const float4 pt = __ldg(pts + j);
+        const float4 o = T.sh[q];
+        sp[p] = make_float4(pt.x + o.x, pt.y + o.y, pt.z + o.z, 0.f);
+        sj[p] = j;
     }
     __syncthreads();  // staged positions and indices visible
-    const int nself = s_off[1], out0 = __ldg(leaf_start + b);
+    const int nself = T.cnt[0], out0 = __ldg(leaf_start + b);
     // thread (tt, rg): targets tt + 16a (a < 2, or < 4 for more than 32 targets), right-hand
     // sides rg + 16q (q < 4); per source 2-4 G loads and 4 density loads for 8-16 complex MACs
     const int tt = tid & 15, rg = tid >> 4;

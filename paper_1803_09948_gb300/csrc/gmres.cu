@@ -13,9 +13,11 @@
 // the working precision.  This keeps the orthogonalisation FP64-class
 // (relative errors near 2^-48) while the FP32 pipe, about 70 times faster than
 // this GPU's FP64 pipe, leaves the kernels bound by HBM.  Per-block partial
-// sums are combined in FP64; the (m+1) x m Hessenberg matrix, its Givens
-// rotations and the triangular solve live on the host in FP64, with one small
-// device-to-host copy per Gram-Schmidt pass.  The matvec is the FP32 FMM.
+// sums are combined in FP64.  For one right-hand side the Gram-Schmidt
+// coefficients, the (m+1) x m Hessenberg matrix, its Givens rotations and the
+// triangular solve stay on the device in FP64 (single-thread kernels), and the
+// host reads one residual estimate per iteration; the lockstep solver for several
+// right-hand sides keeps them on the host.  The matvec is the FP32 FMM.
 #include <cmath>
 #include <complex>
 #include <vector>
@@ -212,14 +214,148 @@ __global__ void k_axpy_df(int64_t N, const float4* __restrict__ V, int nvec, con
     x[r] = o;
 }
 
+// ------------------------------------------------------------ device-side Arnoldi bookkeeping
+// The Hessenberg column, the Givens rotations, the least-squares right-hand side and the
+// triangular solve live in device memory (FP64); the host reads one residual estimate per
+// iteration instead of every coefficient.
+
+__device__ __forceinline__ float4 to_df4(double2 v) {
+    const float rh = (float)v.x, ih = (float)v.y;
+    return make_float4(rh, ih, (float)(v.x - (double)rh), (float)(v.y - (double)ih));
+}
+
+// block i: h_i = sum of its RG partials; coeff[i] = h_i as double-float (the update
+// w -= V h); hsum[i] += h_i (the Hessenberg column, summed over the two passes)
+__global__ void __launch_bounds__(RB) k_reduce_h(const double2* __restrict__ partial, float4* __restrict__ coeff,
+                                                 double2* __restrict__ hsum) {
+    __shared__ double2 sh[RB / 32];
+    double2 acc = make_double2(0, 0);
+    for (int b = threadIdx.x; b < RG; b += RB) {
+        const double2 v = partial[(int64_t)blockIdx.x * RG + b];
+        acc.x += v.x;
+        acc.y += v.y;
+    }
+    const double2 s = block_sum2(acc, sh);
+    if (threadIdx.x == 0) {
+        coeff[blockIdx.x] = to_df4(s);
+        hsum[blockIdx.x].x += s.x;
+        hsum[blockIdx.x].y += s.y;
+    }
+}
+
+// one block: nrm = sqrt(sum of the RG partials of |w|^2); hsum[j1] = nrm (when j1 >= 0);
+// scale = 1 / nrm as (hi, lo) (0 when nrm = 0); out[0] = nrm
+__global__ void __launch_bounds__(RB) k_norm_finish(const double2* __restrict__ partial, int j1,
+                                                    double2* __restrict__ hsum, float2* __restrict__ scale,
+                                                    double* __restrict__ out) {
+    __shared__ double2 sh[RB / 32];
+    double2 acc = make_double2(0, 0);
+    for (int b = threadIdx.x; b < RG; b += RB) acc.x += partial[b].x;
+    const double2 s = block_sum2(acc, sh);
+    if (threadIdx.x == 0) {
+        const double n = sqrt(s.x);
+        if (j1 >= 0) hsum[j1] = make_double2(n, 0.0);
+        const double inv = n > 0.0 ? 1.0 / n : 0.0;
+        const float ih = (float)inv;
+        *scale = make_float2(ih, (float)(inv - (double)ih));
+        out[0] = n;
+    }
+}
+
+// b = s a with s = (hi, lo) read from device memory
+__global__ void k_scale_df_dev(int64_t N, const float4* __restrict__ a, const float2* __restrict__ s,
+                               float4* __restrict__ b) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const float sh = s->x, sl = s->y;
+    const float4 v = a[i];
+    float4 o;
+    {
+        const float p = __fmul_rn(v.x, sh);
+        const float q = __fmaf_rn(v.x, sl, __fmaf_rn(v.z, sh, __fmaf_rn(v.x, sh, -p)));
+        fast_two_sum(p, q, o.x, o.z);
+    }
+    {
+        const float p = __fmul_rn(v.y, sh);
+        const float q = __fmaf_rn(v.y, sl, __fmaf_rn(v.w, sh, __fmaf_rn(v.y, sh, -p)));
+        fast_two_sum(p, q, o.y, o.w);
+    }
+    b[i] = o;
+}
+
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+    return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ double2 cconj(double2 a) { return make_double2(a.x, -a.y); }
+__device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+
+struct Arnoldi {     // device state of one GMRES cycle (FP64)
+    double2* H;      // (m + 1) x m Hessenberg matrix, rotated, row-major
+    double2* cs;     // m rotations (c, s), each acting on rows (i, i+1) as [[conj c, conj s], [-s, c]]
+    double2* sn;
+    double2* g;      // m + 1: rotated right-hand side, g[0] = beta at the cycle's start
+    double* res;     // [0] |g[j+1]| / ||b||, [1] the new column's subdiagonal norm
+};
+
+// Column j: previous rotations, a new rotation for rows (j, j+1), g, the residual estimate.
+__global__ void k_givens(int j, int m, const double2* __restrict__ hsum, Arnoldi A, double bnorm) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double2 h[2];  // rows i, i + 1 as the rotations sweep down
+    h[0] = hsum[0];
+    for (int i = 0; i < j; ++i) {
+        const double2 hi1 = hsum[i + 1];
+        const double2 t = cadd(cmul(cconj(A.cs[i]), h[0]), cmul(cconj(A.sn[i]), hi1));
+        const double2 b = cadd(cmul(make_double2(-A.sn[i].x, -A.sn[i].y), h[0]), cmul(A.cs[i], hi1));
+        A.H[(size_t)i * m + j] = t;
+        h[0] = b;
+    }
+    const double2 hj = h[0], hj1 = hsum[j + 1];
+    const double den = sqrt(hj.x * hj.x + hj.y * hj.y + hj1.x * hj1.x + hj1.y * hj1.y);
+    double2 c = make_double2(1.0, 0.0), s = make_double2(0.0, 0.0);
+    if (den != 0.0) {
+        c = make_double2(hj.x / den, hj.y / den);
+        s = make_double2(hj1.x / den, hj1.y / den);
+    }
+    A.cs[j] = c;
+    A.sn[j] = s;
+    A.H[(size_t)j * m + j] = cadd(cmul(cconj(c), hj), cmul(cconj(s), hj1));
+    const double2 gj = A.g[j];
+    A.g[j + 1] = cmul(make_double2(-s.x, -s.y), gj);
+    A.g[j] = cmul(cconj(c), gj);
+    A.res[0] = sqrt(A.g[j + 1].x * A.g[j + 1].x + A.g[j + 1].y * A.g[j + 1].y) / bnorm;
+    A.res[1] = sqrt(hj1.x * hj1.x + hj1.y * hj1.y);
+}
+
+// cycle start: g = (beta, 0, ..., 0) with beta = nrm[0]
+__global__ void k_cycle_start(int m, Arnoldi A, const double* __restrict__ nrm) {
+    for (int i = threadIdx.x; i <= m; i += blockDim.x) A.g[i] = make_double2(i == 0 ? nrm[0] : 0.0, 0.0);
+}
+
+// y = H[0..n)^{-1} g (upper triangular) as double-float coefficients
+__global__ void k_backsolve(int n, int m, Arnoldi A, double2* __restrict__ y, float4* __restrict__ coeff) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    for (int i = n - 1; i >= 0; --i) {
+        double2 s = A.g[i];
+        for (int q = i + 1; q < n; ++q) {
+            const double2 t = cmul(A.H[(size_t)i * m + q], y[q]);
+            s.x -= t.x;
+            s.y -= t.y;
+        }
+        const double2 d = A.H[(size_t)i * m + i];
+        const double dd = d.x * d.x + d.y * d.y;
+        y[i] = make_double2((s.x * d.x + s.y * d.y) / dd, (s.y * d.x - s.x * d.y) / dd);
+        coeff[i] = to_df4(y[i]);
+    }
+}
+
 namespace {
 struct Ctx {
     hfmm_plan* P;
     cudaStream_t st;
     int64_t N;
     unsigned nb;
-    double2* partial;  // RG * (m + 1)
-    double2* small;    // m + 2 values
+    double2* partial;  // RG * (m + 2)
+    double2* small;    // at least one value
     float4* coeff;     // m + 2 double-float complex coefficients
 
     void count(int n = 1) { P->launches += n; }
@@ -237,40 +373,6 @@ struct Ctx {
         HFMM_CUDA(cudaStreamSynchronize(st));
         return std::sqrt(h.x);
     }
-    void scale(const float4* a, double s, float4* b) {
-        float sh, sl;
-        split_df(s, sh, sl);
-        k_scale_df<<<nb, 256, 0, st>>>(N, a, sh, sl, b);
-        count();
-    }
-    // x += sign * V[0..nvec) c  (c on the host, FP64)
-    void axpy(const float4* V, int nvec, const std::vector<cd>& c, float sign, float4* x) {
-        std::vector<float4> cf(nvec);
-        for (int i = 0; i < nvec; ++i) {
-            float rh, rl, ih, il;
-            split_df(c[i].real(), rh, rl);
-            split_df(c[i].imag(), ih, il);
-            cf[i] = make_float4(rh, ih, rl, il);
-        }
-        HFMM_CUDA(cudaMemcpyAsync(coeff, cf.data(), sizeof(float4) * nvec, cudaMemcpyHostToDevice, st));
-        k_axpy_df<<<nb, 256, sizeof(float4) * nvec, st>>>(N, V, nvec, coeff, sign, x);
-        count();
-    }
-    // h = V[0..nvec)^H w, then w -= V h; adds h into hsum
-    void cgs_pass(const float4* V, int nvec, float4* w, std::vector<cd>& hsum) {
-        k_dots_df<<<dim3(RG, (nvec + kDotVecs - 1) / kDotVecs), RB, 0, st>>>(N, V, nvec, w, partial);
-        k_reduce<<<nvec, RB, 0, st>>>(partial, small);
-        count(2);
-        std::vector<double2> h(nvec);
-        HFMM_CUDA(cudaMemcpyAsync(h.data(), small, sizeof(double2) * nvec, cudaMemcpyDeviceToHost, st));
-        HFMM_CUDA(cudaStreamSynchronize(st));
-        std::vector<cd> hc(nvec);
-        for (int i = 0; i < nvec; ++i) {
-            hc[i] = cd(h[i].x, h[i].y);
-            hsum[i] += hc[i];
-        }
-        axpy(V, nvec, hc, -1.f, w);
-    }
 };
 }  // namespace
 
@@ -279,18 +381,47 @@ int run_gmres(hfmm_plan* P, const void* rhs, void* x_out, int* iters, double* re
     const int m = P->cfg.restart;
     const double tol = P->cfg.tol;
     const int maxit = P->cfg.max_iter;
+    // workspace (doubles): partials RG (m + 2) complex, hsum m + 2, H (m + 1) m, cs m, sn m,
+    // g m + 1, y m (complex each), coefficients m + 2 (double-float complex), residual pair,
+    // norm, scale
+    const size_t n_part = 2 * (size_t)RG * (m + 2), n_hsum = 2 * (size_t)(m + 2), n_H = 2 * (size_t)(m + 1) * m,
+                 n_cs = 2 * (size_t)m, n_g = 2 * (size_t)(m + 1), n_y = 2 * (size_t)m, n_coef = 2 * (size_t)(m + 2);
+    const size_t n_ws = n_part + n_hsum + n_H + 2 * n_cs + n_g + n_y + n_coef + 4;
     if (P->kry_m != m) {
         P->kry.alloc((size_t)(m + 1) * N, nullptr);
         P->gw.alloc(N, nullptr);
         P->gx.alloc(N, nullptr);
         P->gb.alloc(N, nullptr);
-        P->gred.alloc((size_t)2 * RG * (m + 2) + 2 * (m + 2) + 4 * (m + 2), nullptr);
+        P->gred.alloc(n_ws, nullptr);
         P->kry_m = m;
     }
-    double2* red = (double2*)P->gred.p;
-    Ctx c{P, st, N, (unsigned)((N + 255) / 256), red, red + (size_t)RG * (m + 2),
-          reinterpret_cast<float4*>(red + (size_t)RG * (m + 2) + (m + 2))};
+    double* ws = P->gred.p;
+    double2* partial = (double2*)ws;
+    double2* hsum = (double2*)(ws + n_part);
+    Arnoldi A;
+    A.H = (double2*)(ws + n_part + n_hsum);
+    A.cs = (double2*)(ws + n_part + n_hsum + n_H);
+    A.sn = A.cs + m;
+    A.g = (double2*)(ws + n_part + n_hsum + n_H + 2 * n_cs);
+    double2* y = (double2*)(ws + n_part + n_hsum + n_H + 2 * n_cs + n_g);
+    float4* coeff = (float4*)(ws + n_part + n_hsum + n_H + 2 * n_cs + n_g + n_y);
+    double* tail = ws + n_part + n_hsum + n_H + 2 * n_cs + n_g + n_y + n_coef;
+    A.res = tail;             // 2 doubles
+    double* nrm = tail + 2;   // 1 double
+    float2* scale = (float2*)(tail + 3);
+    Ctx c{P, st, N, (unsigned)((N + 255) / 256), partial, hsum, coeff};
     float4* V = P->kry.p;
+    auto launch_norm = [&](const float4* w, int j1) {  // nrm, scale = 1 / nrm, hsum[j1] = nrm
+        k_norm2_df<<<RG, RB, 0, st>>>(N, w, partial);
+        k_norm_finish<<<1, RB, 0, st>>>(partial, j1, hsum, scale, nrm);
+        c.count(2);
+    };
+    auto cgs_pass = [&](int nvec, float4* w) {  // h = V^H w; w -= V h; hsum += h
+        k_dots_df<<<dim3(RG, (nvec + kDotVecs - 1) / kDotVecs), RB, 0, st>>>(N, V, nvec, w, partial);
+        k_reduce_h<<<nvec, RB, 0, st>>>(partial, coeff, hsum);
+        k_axpy_df<<<c.nb, 256, sizeof(float4) * nvec, st>>>(N, V, nvec, coeff, -1.f, w);
+        c.count(3);
+    };
     k_c64_to_df<<<c.nb, 256, 0, st>>>(N, (const float2*)rhs, P->gb.p);
     c.count();
     HFMM_CUDA(cudaMemsetAsync(P->gx.p, 0, sizeof(float4) * N, st));
@@ -309,50 +440,33 @@ int run_gmres(hfmm_plan* P, const void* rhs, void* x_out, int* iters, double* re
     int it = 0;
     bool converged = false;
     while (it < maxit && !converged) {
-        c.scale(P->gw.p, 1.0 / beta, V);
-        std::vector<cd> H((size_t)(m + 1) * m, cd(0)), cs(m), sn(m), g(m + 1, cd(0));
-        g[0] = beta;
+        // V_0 = r / beta, g = (beta, 0, ...)
+        launch_norm(P->gw.p, -1);
+        k_scale_df_dev<<<c.nb, 256, 0, st>>>(N, P->gw.p, scale, V);
+        k_cycle_start<<<1, 64, 0, st>>>(m, A, nrm);
+        c.count(2);
         int jdone = 0;
         for (int j = 0; j < m && it < maxit; ++j) {
             float4* w = P->gw.p;
             c.matvec(V + (int64_t)j * N, w);
-            std::vector<cd> h(j + 2, cd(0));
-            c.cgs_pass(V, j + 1, w, h);
-            c.cgs_pass(V, j + 1, w, h);
-            double hn = c.norm(w);
-            h[j + 1] = hn;
-            if (hn > 0.0) c.scale(w, 1.0 / hn, V + (int64_t)(j + 1) * N);
-            // previous rotations, each acting on rows (i, i+1) as [[conj c, conj s], [-s, c]]
-            for (int i = 0; i < j; ++i) {
-                cd t = std::conj(cs[i]) * h[i] + std::conj(sn[i]) * h[i + 1];
-                h[i + 1] = -sn[i] * h[i] + cs[i] * h[i + 1];
-                h[i] = t;
-            }
-            double den = std::sqrt(std::norm(h[j]) + std::norm(h[j + 1]));
-            if (den == 0.0) {
-                cs[j] = 1.0;
-                sn[j] = 0.0;
-            } else {
-                cs[j] = h[j] / den;
-                sn[j] = h[j + 1] / den;
-            }
-            h[j] = std::conj(cs[j]) * h[j] + std::conj(sn[j]) * h[j + 1];
-            h[j + 1] = 0.0;
-            g[j + 1] = -sn[j] * g[j];
-            g[j] = std::conj(cs[j]) * g[j];
-            for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = h[i];
+            HFMM_CUDA(cudaMemsetAsync(hsum, 0, sizeof(double2) * (j + 2), st));
+            cgs_pass(j + 1, w);  // classical Gram-Schmidt, twice
+            cgs_pass(j + 1, w);
+            launch_norm(w, j + 1);
+            k_scale_df_dev<<<c.nb, 256, 0, st>>>(N, w, scale, V + (int64_t)(j + 1) * N);
+            k_givens<<<1, 32, 0, st>>>(j, m, hsum, A, bnorm);
+            c.count(2);
+            double rh[2];
+            HFMM_CUDA(cudaMemcpyAsync(rh, A.res, sizeof(rh), cudaMemcpyDeviceToHost, st));
+            HFMM_CUDA(cudaStreamSynchronize(st));
             ++it;
             jdone = j + 1;
-            if (std::abs(g[j + 1]) / bnorm <= tol || hn == 0.0) break;
+            if (rh[0] <= tol || rh[1] == 0.0) break;
         }
-        // y = H^{-1} g (upper triangular, FP64), x += V y
-        std::vector<cd> y(jdone);
-        for (int i = jdone - 1; i >= 0; --i) {
-            cd s = g[i];
-            for (int q = i + 1; q < jdone; ++q) s -= H[(size_t)i * m + q] * y[q];
-            y[i] = s / H[(size_t)i * m + i];
-        }
-        c.axpy(V, jdone, y, 1.f, P->gx.p);
+        // y = H^{-1} g (upper triangular, FP64, on the device), x += V y
+        k_backsolve<<<1, 32, 0, st>>>(jdone, m, A, y, coeff);
+        k_axpy_df<<<c.nb, 256, sizeof(float4) * jdone, st>>>(N, V, jdone, coeff, 1.f, P->gx.p);
+        c.count(2);
         // true residual r = b - A x
         c.matvec(P->gx.p, P->gw.p);
         k_sub_df<<<c.nb, 256, 0, st>>>(N, P->gb.p, P->gw.p, P->gw.p);

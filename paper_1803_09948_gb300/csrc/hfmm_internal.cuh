@@ -15,6 +15,9 @@
 #define HFMM_TRANS_NB 64      // columns per translation work item
 constexpr int kP2PTile = 8;   // targets per near-field warp
 constexpr int kP2PSub = 4;    // lanes sharing one target (kP2PTile * kP2PSub == 32)
+constexpr int kDefaultP2PKernel = 1;  // near-field kernel when the configuration leaves it open
+constexpr int kDefaultOverlap = 0;    // two-branch captured matvec when the configuration leaves it open
+constexpr int kDefaultM2LKernel = 0;  // tensor-core M2L kernel when the configuration leaves it open
 
 // ---------------------------------------------------------------- errors
 struct HfmmError {
@@ -76,6 +79,26 @@ struct TransItem {
     int16_t pad[2];
 };
 
+// Target-stationary tensor-core M2L (m2l_ts.cu).  A tile holds up to kTsTile consecutive
+// target boxes of one level; its translations are grouped by canonical operator (the
+// offsets' reflection classes) into chunks of up to 64 columns.
+constexpr int kTsTile = 256;
+struct TsTile {
+    int64_t dst;     // coef offset (complex elements) of the tile's first local expansion
+    int64_t src;     // coef offset of the level's multipoles
+    int32_t P;       // (p+1)^2 of the level (<= 64)
+    int32_t ntgt;    // target boxes in the tile
+    int32_t chunk0;  // first chunk
+    int32_t nchunk;  // chunks
+};
+struct TsChunk {
+    int64_t op;      // offset (complex elements) of the canonical operator [P][P]
+    int32_t col0;    // first column (even): int2 {source box of the level, target slot | reflection << 16};
+                     // every chunk's range is padded to an even length (16-byte bulk copies)
+    int16_t ncol;    // columns, 1..64
+    int16_t newop;   // 1: first chunk of its operator group
+};
+
 // A run of SIMT translation items of one column width (64, 16 or 8).
 struct SimtRange {
     int64_t begin, end;
@@ -100,6 +123,7 @@ struct LevelInfo {
     int64_t m2l_op = 0;     // offset of 343 M2L operators (316 used) [343][P][P]
     int64_t pc_op = 0;      // offset of 8 L2L operators [8][P][P_parent] (levels >= 3)
     int64_t m2m_op = 0;     // offset of 8 M2M operators [8][P_parent][P] (levels >= 3)
+    int64_t canon_op = -1;  // offset of the canonical M2L operators in m2l_canon (tensor-core levels)
 };
 
 // State of the batched (multiple right-hand side) matvec for R = 2..64 right-hand sides.
@@ -123,6 +147,26 @@ struct BatchState {
     ~BatchState() {
         if (graph) cudaGraphExecDestroy(graph);
         if (cap_stream) cudaStreamDestroy(cap_stream);
+    }
+};
+
+// The single right-hand-side matvec (sorted densities -> sorted potentials) captured as a
+// CUDA graph with the near field on a side branch (see run_matvec_sorted).
+struct MatvecGraph {
+    cudaStream_t cap = nullptr, side = nullptr;  // capture stream and the near-field branch
+    cudaEvent_t fork = nullptr, join = nullptr;
+    cudaGraphExec_t graph = nullptr;
+    int64_t launches = 0;  // kernels in one replay
+    void reset() {
+        if (graph) cudaGraphExecDestroy(graph);
+        graph = nullptr;
+    }
+    ~MatvecGraph() {
+        reset();
+        if (fork) cudaEventDestroy(fork);
+        if (join) cudaEventDestroy(join);
+        if (side) cudaStreamDestroy(side);
+        if (cap) cudaStreamDestroy(cap);
     }
 };
 
@@ -184,6 +228,13 @@ struct hfmm_plan {
     std::vector<SimtRange> m2l_simt;  // M2L item ranges on the SIMT kernel
     DBuf<uint16_t> aops;       // tensor-core M2L operators (BF16 hi/lo, packed)
     DBuf<int4> tc_groups;      // (first item, item count, operator, P) per tensor-core block
+    DBuf<float2> m2l_canon;    // canonical M2L operators [ncanon][P][P] of the tensor-core levels
+    DBuf<TsTile> ts_tiles;     // target-stationary M2L work (m2l_ts.cu)
+    DBuf<TsChunk> ts_chunks;
+    DBuf<int2> ts_cols;
+    int64_t n_ts_tiles = 0;
+    int ts_max_tile_floats = 0;
+    int ts_max_chunks = 0;
     int64_t n_tc_groups = 0;   // the first n_tc_groups groups are M2L
     std::vector<std::pair<int64_t, int64_t>> m2m_tc, l2l_tc;  // tensor-core group ranges per level
     DBuf<int> dev_err;         // set by kernels whose bounded waits gave up
@@ -216,6 +267,14 @@ struct hfmm_plan {
     double cost[HFMM_NUM_COSTS] = {};  // see hfmm_plan_costs
     cudaEvent_t* stage_ev = nullptr;  // set by hfmm_matvec_timed: events after each stage
     BatchState batch;
+    int mv_mode = 1;    // 0: stages launched one after another; 1: two-branch captured graph
+    int m2l_variant = 0;   // tensor-core M2L: 0 source-stationary items, 1 target-stationary tiles
+    int tc_group_used = 32;
+    int64_t tc_m2l_base = 0;  // source-stationary M2L groups as built (at most m2l_tc_max_group() items)
+    std::vector<std::pair<int64_t, int64_t>> m2m_tc_base, l2l_tc_base;
+    float tune_ms[HFMM_NUM_TUNABLES][HFMM_TUNE_CANDIDATES] = {{-1, -1, -1, -1}, {-1, -1, -1, -1},
+                                                             {-1, -1, -1, -1}, {-1, -1, -1, -1}};
+    MatvecGraph mvg;
 };
 
 // ---------------------------------------------------------------- kernels: FMM matvec
@@ -235,6 +294,8 @@ void launch_density_prep(hfmm_plan* P, const void* density, VecKind kind, float2
 void launch_output(hfmm_plan* P, const float2* phi, void* out, VecKind kind, cudaStream_t st);
 // parts bit 0 near, 1 far, 2 correction; writes P->phi
 void run_matvec_sorted(hfmm_plan* P, int parts, cudaStream_t st);
+// sets the matvec kernels' shared-memory limits on the current device (once; before any capture)
+void matvec_kernels_init();
 // records stage event q (if timing is active)
 void mark_stage(hfmm_plan* P, int q, cudaStream_t st);
 void run_direct_sorted(hfmm_plan* P, cudaStream_t st);
@@ -327,6 +388,11 @@ void m2l_tc_init();        // sets the kernel's shared-memory limit on the curre
 // standing for the rhs columns (box * rhs + r); their src / dst offsets are already scaled
 void m2l_tc_launch(const int4* groups, int64_t ngroups, const TransItem* items, const int2* cols,
                    const uint16_t* aops, float2* coef, int* err, int rhs, cudaStream_t st);
+// target-stationary M2L: one block per tile; canon holds the canonical FP32 operators
+void m2l_ts_init();  // shared-memory limit on the current device (idempotent; before any capture)
+size_t m2l_ts_smem(int max_tile_floats, int max_chunks);
+void m2l_ts_launch(const TsTile* tiles, int64_t ntiles, int max_tile_floats, int max_chunks, const TsChunk* chunks,
+                   const int2* cols, const float2* canon, float2* coef, int* err, cudaStream_t st);
 
 // ---------------------------------------------------------------- GMRES
 int run_gmres(hfmm_plan* P, const void* rhs, void* x, int* iters, double* relres, cudaStream_t st);

@@ -26,6 +26,7 @@
 #include <cuda_bf16.h>
 
 #include "hfmm_internal.cuh"
+#include "tc_common.cuh"
 
 namespace hfmm {
 
@@ -41,87 +42,21 @@ constexpr uint32_t kLBO = kCoreBytes;                // next 8-element K group
 constexpr uint32_t kBBytes = kN * kK * 2;            // 16 KiB per BF16 part
 constexpr uint32_t kTmemCols = 64;    // one accumulator (N = 64 FP32 columns)
 constexpr uint32_t kTmemA = 128;      // A hi (64 columns) and lo (64 columns): 128 x 128 BF16 each
-constexpr long long kWaitLimit = 1ll << 26;          // try_wait polls before giving up
 
 // element (r, k) of a K-major core-matrix tile with kKc core matrices per 8-row group
 __host__ __device__ constexpr uint32_t core_index(uint32_t r, uint32_t k) {
     return ((r >> 3) * kKc + (k >> 3)) * 64 + (r & 7) * 8 + (k & 7);
 }
 
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
+using namespace tc;
 
-__device__ __forceinline__ uint64_t umma_desc(uint32_t addr) {
-    uint64_t d = 0;
-    d |= (uint64_t)((addr >> 4) & 0x3FFF);
-    d |= (uint64_t)((kLBO >> 4) & 0x3FFF) << 16;
-    d |= (uint64_t)((kSBO >> 4) & 0x3FFF) << 32;
-    d |= (uint64_t)1 << 46;  // descriptor version for this architecture; no swizzle, base offset 0
-    return d;
-}
+__device__ __forceinline__ uint64_t umma_desc(uint32_t addr) { return tc::umma_desc(addr, kLBO, kSBO); }
 
 // kind::f16 instruction descriptor: D f32, A/B bf16, both K-major, N = 64, M = 128
-constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kN >> 3) << 17) |
-                            ((uint32_t)(kM >> 4) << 24);
+constexpr uint32_t kIdesc = idesc_bf16(kM, kN);
 
 __device__ __forceinline__ void mma_bf16_ta(uint32_t tmem_d, uint32_t tmem_a, uint64_t b, uint32_t accumulate) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}\n"
-        :
-        : "r"(tmem_d), "r"(tmem_a), "l"(b), "r"(kIdesc), "r"(accumulate)
-        : "memory");
-}
-
-// 16 consecutive 32-bit columns of this thread's lane
-__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&v)[16]) {
-    asm volatile(
-        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
-        "%14, %15, %16};" ::"r"(taddr),
-        "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]), "r"(v[9]),
-        "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15])
-        : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint32_t addr, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}\n"
-        : "=r"(ok)
-        : "r"(addr), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-
-// 64 consecutive columns of this thread's lane: four loads in flight, one wait
-__device__ __forceinline__ void tmem_ld64(uint32_t taddr, float (&v)[64]) {
-    uint32_t r[64];
-#pragma unroll
-    for (int b = 0; b < 4; ++b)
-        asm volatile(
-            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
-            "%14, %15}, [%16];"
-            : "=r"(r[16 * b + 0]), "=r"(r[16 * b + 1]), "=r"(r[16 * b + 2]), "=r"(r[16 * b + 3]),
-              "=r"(r[16 * b + 4]), "=r"(r[16 * b + 5]), "=r"(r[16 * b + 6]), "=r"(r[16 * b + 7]),
-              "=r"(r[16 * b + 8]), "=r"(r[16 * b + 9]), "=r"(r[16 * b + 10]), "=r"(r[16 * b + 11]),
-              "=r"(r[16 * b + 12]), "=r"(r[16 * b + 13]), "=r"(r[16 * b + 14]), "=r"(r[16 * b + 15])
-            : "r"(taddr + (uint32_t)(16 * b)));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int q = 0; q < 64; ++q) v[q] = __uint_as_float(r[q]);
-}
-
-__device__ __forceinline__ void split_bf16(float x, __nv_bfloat16& hi, __nv_bfloat16& lo) {
-    hi = __float2bfloat16_rn(x);
-    lo = __float2bfloat16_rn(x - __bfloat162float(hi));
+    tc::mma_bf16_ta(tmem_d, tmem_a, b, kIdesc, accumulate);
 }
 
 // Operator conversion (plan time): FP32 complex T [P][P] -> A_hi, A_lo (row-major BF16).
@@ -174,45 +109,8 @@ struct TcSmem {
     int abort;
 };
 
-__device__ __forceinline__ void mbar_arrive(uint32_t addr) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(addr) : "memory");
-}
-
-__device__ __forceinline__ void mbar_init(uint32_t addr, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(addr), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void tc_commit(uint32_t bar) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
-                 : "memory");
-}
-
-// Bounded wait that also gives up when another role has aborted; on a timeout
-// it raises the block's abort flag and the device error flag.
-__device__ __forceinline__ bool wait_or_abort(uint32_t bar, uint32_t parity, volatile int* abort, int* err) {
-    for (long long it = 0; it < kWaitLimit; ++it) {
-        if (mbar_try_wait(bar, parity)) return true;
-        if ((it & 255) == 255 && *abort) return false;
-    }
-    *abort = 1;
-    atomicExch(err, 1);
-    return false;
-}
-
-// AND of v over the 128 epilogue threads (named barrier 1); every epilogue thread
-// takes the same branch afterwards, so no later barrier can be left waiting.
-__device__ __forceinline__ bool epilogue_all(bool v) {
-    uint32_t r;
-    asm volatile(
-        "{\n\t.reg .pred p, q;\n\t"
-        "setp.ne.u32 q, %1, 0;\n\t"
-        "bar.red.and.pred p, 1, 128, q;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}\n"
-        : "=r"(r)
-        : "r"((uint32_t)v)
-        : "memory");
-    return r != 0;
-}
+// AND of v over the 128 epilogue threads (named barrier 1)
+__device__ __forceinline__ bool epilogue_all(bool v) { return bar_and(v, 1, 128); }
 
 __global__ void __launch_bounds__(kThreads, 1)
     k_m2l_tc(const int4* __restrict__ groups, const TransItem* __restrict__ items, const int2* __restrict__ cols,

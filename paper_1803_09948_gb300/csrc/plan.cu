@@ -11,6 +11,7 @@
 // Sec. 2.2 (discretisation, singular treatment), Sec. 2.3 (octree, sweeps),
 // Sec. 3.1-3.2 (Morton order, cell = index + count).
 #include <algorithm>
+#include <functional>
 #include <cmath>
 #include <cstring>
 #include <memory>
@@ -124,6 +125,74 @@ struct PairBuckets {
     }
 };
 
+// Target-stationary M2L work of one level (m2l_ts.cu): tiles of tt (<= kTsTile) consecutive target
+// boxes; in each tile the translations grouped by canonical operator (refl[slot].x) into
+// chunks of up to 64 columns {source box, target slot | reflection code << 16}, the code's
+// bits being the x, y, z flips that carry the canonical offset onto the slot's offset.
+void emit_ts_level(const PairBuckets& pb, const std::vector<int4>& refl, int ncanon, int64_t nbox, int Pl,
+                   int64_t mofs, int64_t lofs, int64_t canon_op, int tt, std::vector<TsTile>& tiles,
+                   std::vector<TsChunk>& chunks, std::vector<int2>& cols) {
+    const int64_t ntile = (nbox + tt - 1) / tt;
+    std::vector<int64_t> start((size_t)(ntile * ncanon + 1), 0);
+    for (size_t g = 0; g + 1 < pb.start.size(); ++g)
+        for (int64_t e = pb.start[g]; e < pb.start[g + 1]; ++e)
+            ++start[(size_t)((pb.pairs[e].y / tt) * ncanon + refl[g].x) + 1];
+    for (size_t q = 1; q < start.size(); ++q) start[q] += start[q - 1];
+    std::vector<int2> tmp((size_t)start.back());
+    std::vector<int64_t> fill(start.begin(), start.end() - 1);
+    for (size_t g = 0; g + 1 < pb.start.size(); ++g) {
+        const int rc = refl[g].y | (refl[g].z << 1) | (refl[g].w << 2);
+        for (int64_t e = pb.start[g]; e < pb.start[g + 1]; ++e) {
+            const int2 pr = pb.pairs[e];  // (source, target)
+            tmp[(size_t)fill[(size_t)((pr.y / tt) * ncanon + refl[g].x)]++] =
+                make_int2(pr.x, (pr.y % tt) | (rc << 16));
+        }
+    }
+    for (int64_t t = 0; t < ntile; ++t) {
+        TsTile tl{};
+        tl.dst = lofs + t * tt * (int64_t)Pl;
+        tl.src = mofs;
+        tl.P = Pl;
+        tl.ntgt = (int32_t)std::min<int64_t>(tt, nbox - t * tt);
+        tl.chunk0 = (int32_t)chunks.size();
+        for (int c = 0; c < ncanon; ++c) {
+            const int64_t b = start[(size_t)(t * ncanon + c)], e = start[(size_t)(t * ncanon + c) + 1];
+            // chunks of up to 64 columns in which no target repeats (a target can meet one
+            // canonical operator through several reflections), so the kernel adds a chunk's
+            // columns into the tile without atomics; repeats move to a later chunk
+            std::vector<int2> rest(tmp.begin() + b, tmp.begin() + e), later;
+            std::vector<char> seen((size_t)tt);
+            bool first = true;
+            while (!rest.empty()) {
+                TsChunk ch{};
+                ch.op = canon_op + (int64_t)c * Pl * Pl;
+                ch.col0 = (int32_t)cols.size();
+                ch.newop = (int16_t)first;
+                first = false;
+                std::fill(seen.begin(), seen.end(), 0);
+                later.clear();
+                int n = 0;
+                for (const int2& col : rest) {
+                    const int j = col.y & 0xffff;
+                    if (n < 64 && !seen[(size_t)j]) {
+                        seen[(size_t)j] = 1;
+                        cols.push_back(col);
+                        ++n;
+                    } else {
+                        later.push_back(col);
+                    }
+                }
+                ch.ncol = (int16_t)n;
+                if (n & 1) cols.push_back(make_int2(0, 0));  // even length: 16-byte bulk copies
+                chunks.push_back(ch);
+                rest.swap(later);
+            }
+        }
+        tl.nchunk = (int32_t)chunks.size() - tl.chunk0;
+        if (tl.nchunk > 0) tiles.push_back(tl);
+    }
+}
+
 void emit_items(const PairBuckets& pb, const std::vector<int64_t>& op_of_bucket, int64_t src, int64_t dst, int pin,
                 int pout, int atomic, std::vector<TransItem>& items, std::vector<int2>& cols,
                 int width = HFMM_TRANS_NB) {
@@ -146,6 +215,96 @@ void emit_items(const PairBuckets& pb, const std::vector<int64_t>& op_of_bucket,
     }
 }
 }  // namespace
+
+// candidates of each tunable (the order of hfmm_plan_tuning's tuned_ms) and the defaults
+constexpr int kTuneCount[HFMM_NUM_TUNABLES] = {2, 2, 3, 2};
+constexpr int kTuneValue[HFMM_NUM_TUNABLES][HFMM_TUNE_CANDIDATES] = {{0, 1}, {0, 1}, {8, 16, 32}, {0, 1}};
+constexpr int kTuneDefault[HFMM_NUM_TUNABLES] = {kDefaultP2PKernel, kDefaultM2LKernel, 32, kDefaultOverlap};
+
+// Splits the source-stationary M2L groups (built with at most m2l_tc_max_group() items,
+// one operator each) into groups of at most g items; the M2M / L2L groups follow unchanged.
+static void apply_tc_group(hfmm_plan* P, int g, cudaStream_t st) {
+    std::vector<int4> out;
+    for (int64_t q = 0; q < P->tc_m2l_base; ++q) {
+        const int4 b = P->host_groups[(size_t)q];
+        for (int o = 0; o < b.y; o += g) out.push_back(make_int4(b.x + o, std::min(g, b.y - o), b.z, b.w));
+    }
+    const int64_t n_m2l = (int64_t)out.size(), shift = n_m2l - P->tc_m2l_base;
+    out.insert(out.end(), P->host_groups.begin() + P->tc_m2l_base, P->host_groups.end());
+    P->tc_groups.upload(out, nullptr, st);
+    HFMM_CUDA(cudaStreamSynchronize(st));  // `out` is freed on return
+    P->n_tc_groups = n_m2l;
+    for (size_t l = 0; l < P->m2m_tc_base.size(); ++l) {
+        const auto& a = P->m2m_tc_base[l];
+        P->m2m_tc[l] = a.second > a.first ? std::make_pair(a.first + shift, a.second + shift) : a;
+    }
+    for (size_t l = 0; l < P->l2l_tc_base.size(); ++l) {
+        const auto& a = P->l2l_tc_base[l];
+        P->l2l_tc[l] = a.second > a.first ? std::make_pair(a.first + shift, a.second + shift) : a;
+    }
+    P->tc_group_used = g;
+    P->mvg.reset();
+}
+
+__global__ void k_tune_fill(int64_t N, float2* __restrict__ sig) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    uint32_t h = (uint32_t)i * 2654435761u + 12345u;  // a multiplicative hash: values in [-1, 1)
+    h ^= h >> 15;
+    h *= 2246822519u;
+    h ^= h >> 13;
+    sig[i] = make_float2((float)(h & 0xffff) / 32768.f - 1.f, (float)(h >> 16) / 32768.f - 1.f);
+}
+
+// Plan-time tuning (cfg.autotune = 1), the counterpart of the paper's search for its task size
+// and leaf size (Sec. 3.2, 6.2): every choice the configuration left open is timed on this
+// plan's own tree and operators, one whole matvec per measurement (CUDA events on the plan's
+// stream, one warm-up then the mean of three), and the fastest is kept.  Order: near-field
+// kernel, M2L kernel, tensor-core group size (source-stationary M2L only), matvec form.
+static void tune_plan(hfmm_plan* P, cudaStream_t st) {
+    const hfmm_config& cfg = P->cfg;
+    k_tune_fill<<<(unsigned)((P->N + 255) / 256), 256, 0, st>>>(P->N, P->sig.p);
+    HFMM_CUDA(cudaGetLastError());
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    HFMM_CUDA(cudaEventCreate(&e0));
+    struct Ev {
+        cudaEvent_t* a;
+        cudaEvent_t* b;
+        ~Ev() {
+            if (*a) cudaEventDestroy(*a);
+            if (*b) cudaEventDestroy(*b);
+        }
+    } guard{&e0, &e1};
+    HFMM_CUDA(cudaEventCreate(&e1));
+    const int64_t launches0 = P->launches;
+    auto time_matvec = [&]() -> float {
+        P->mvg.reset();
+        run_matvec_sorted(P, 7, st);  // warm-up (and the graph capture of the two-branch form)
+        HFMM_CUDA(cudaEventRecord(e0, st));
+        for (int r = 0; r < 3; ++r) run_matvec_sorted(P, 7, st);
+        HFMM_CUDA(cudaEventRecord(e1, st));
+        HFMM_CUDA(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        HFMM_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        return ms / 3.f;
+    };
+    auto pick = [&](int a, const std::function<void(int)>& set) {
+        for (int c = 0; c < kTuneCount[a]; ++c) {
+            set(kTuneValue[a][c]);
+            P->tune_ms[a][c] = time_matvec();
+        }
+        int v = 0;
+        if (hfmm_tune_choose(a, P->tune_ms[a], kTuneCount[a], &v) != HFMM_OK) v = kTuneDefault[a];
+        set(v);
+    };
+    const bool staged_p2p = P->poly_p2p && P->p2p_cap > 0 && P->p2p_maxnbr <= 64;
+    if (cfg.p2p_kernel < 0 && staged_p2p) pick(0, [&](int v) { P->p2p_variant = v; });
+    if (cfg.m2l_kernel < 0 && P->n_ts_tiles > 0 && P->n_tc_groups > 0) pick(1, [&](int v) { P->m2l_variant = v; });
+    if (cfg.tc_group == 0 && P->m2l_variant == 0 && P->tc_m2l_base > 0) pick(2, [&](int g) { apply_tc_group(P, g, st); });
+    if (cfg.overlap < 0 && !P->adaptive) pick(3, [&](int v) { P->mv_mode = v; });
+    P->mvg.reset();
+    P->launches = launches0;  // tuning launches are not the caller's
+}
 
 static void build_plan(hfmm_plan* P, const double* V, int64_t nv, const int32_t* F, int64_t nt, cudaStream_t st) {
     const hfmm_config& cfg = P->cfg;
@@ -318,6 +477,12 @@ static void build_plan(hfmm_plan* P, const double* V, int64_t nv, const int32_t*
                                leaf_lev[b]);
     }
     upload_legendre_tables();
+    matvec_kernels_init();
+    m2l_tc_init();
+    P->p2p_variant = cfg.p2p_kernel >= 0 ? cfg.p2p_kernel : kDefaultP2PKernel;
+    P->mv_mode = cfg.overlap >= 0 ? cfg.overlap : kDefaultOverlap;
+    P->m2l_variant = cfg.m2l_kernel >= 0 ? cfg.m2l_kernel : kDefaultM2LKernel;
+    m2l_ts_init();
     DBuf<double> d_w, d_x64s, d_w64s, d_V;
     DBuf<int32_t> d_t, d_tri, d_F, d_sstart;
     DBuf<uint64_t> d_leafkey, d_skey;
@@ -587,6 +752,16 @@ static void build_plan(hfmm_plan* P, const double* V, int64_t nv, const int32_t*
         const int ncanon = (int)(canon_unit.size() / 3);
         DBuf<int4> d_refl;
         d_refl.upload(refl, nullptr, st);
+        // the canonical operators of the tensor-core levels stay resident (target-stationary M2L)
+        {
+            int64_t coff = 0;
+            for (int l = 2; l <= L; ++l)
+                if (cfg.m2l_tensor && P->lev[l].P <= 64) {
+                    P->lev[l].canon_op = coff;
+                    coff += (int64_t)ncanon * P->lev[l].P * P->lev[l].P;
+                }
+            if (coff > 0) P->m2l_canon.alloc((size_t)coff, cnt);
+        }
         for (int l = 2; l <= L; ++l) {
             const LevelInfo& li = P->lev[l];
             double a = 0.5 * std::sqrt(3.0) * li.side;
@@ -607,6 +782,9 @@ static void build_plan(hfmm_plan* P, const double* V, int64_t nv, const int32_t*
             job.out2 = nullptr;
             build_projection_ops(job, k, st);
             expand_m2l_reflections(canon.p, li.P, 316, d_refl.p, P->ops.p + li.m2l_op, st);
+            if (li.canon_op >= 0)
+                HFMM_CUDA(cudaMemcpyAsync(P->m2l_canon.p + li.canon_op, canon.p, sizeof(float2) * (size_t)ncanon * li.P * li.P,
+                                          cudaMemcpyDeviceToDevice, st));
             HFMM_CUDA(cudaStreamSynchronize(st));  // canon is freed at the end of this scope
             if (l >= 3) {
                 const LevelInfo& lp = P->lev[l - 1];
@@ -657,6 +835,26 @@ static void build_plan(hfmm_plan* P, const double* V, int64_t nv, const int32_t*
         std::vector<int16_t> slot16(slot, slot + 343);
         DBuf<int16_t> d_slot;
         d_slot.upload(slot16, nullptr, st);
+        std::vector<TsTile> ts_tiles;
+        std::vector<TsChunk> ts_chunks;
+        std::vector<int2> ts_cols;
+        // tile size of the target-stationary M2L: the largest of 256, 128, 64, 32 targets that
+        // still gives every SM two tiles (one block per SM at a time)
+        int ts_tt = 32;
+        {
+            int dev = 0, nsm = 1;
+            HFMM_CUDA(cudaGetDevice(&dev));
+            HFMM_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+            for (int tt = kTsTile; tt >= 32; tt /= 2) {
+                int64_t tiles = 0;
+                for (int l = 2; l <= L; ++l)
+                    if (P->lev[l].canon_op >= 0) tiles += ((int64_t)lv[l].key.size() + tt - 1) / tt;
+                if (tiles >= 2 * (int64_t)nsm) {
+                    ts_tt = tt;
+                    break;
+                }
+            }
+        }
         for (int l = 2; l <= L; ++l) {
             lev_item_b[l] = (int64_t)items.size();
             // interaction lists (children of the parent's neighbours that are not
@@ -682,11 +880,44 @@ static void build_plan(hfmm_plan* P, const double* V, int64_t nv, const int32_t*
                 width = mean <= 12 ? 8 : mean <= 28 ? 16 : HFMM_TRANS_NB;
             }
             lev_width[l] = width;
+            if (P->lev[l].canon_op >= 0)
+                emit_ts_level(pb, refl, ncanon, (int64_t)lv[l].key.size(), P->lev[l].P, P->lev[l].mofs, P->lev[l].lofs,
+                              P->lev[l].canon_op, ts_tt, ts_tiles, ts_chunks, ts_cols);
             emit_items(pb, ops, P->lev[l].mofs, P->lev[l].lofs, P->lev[l].P, P->lev[l].P, 1, items, cols, width);
             lev_item_e[l] = (int64_t)items.size();
         }
         P->m2l_items_end = (int64_t)items.size();
         P->m2l_count = m2l_count;
+        if (!ts_tiles.empty()) {
+            // longest tiles first, so that the last wave is short
+            std::vector<int64_t> work(ts_tiles.size());
+            for (size_t t = 0; t < ts_tiles.size(); ++t) {
+                int64_t n = 0;
+                for (int c = 0; c < ts_tiles[t].nchunk; ++c) n += ts_chunks[(size_t)(ts_tiles[t].chunk0 + c)].ncol;
+                work[t] = n;
+            }
+            std::vector<size_t> order(ts_tiles.size());
+            for (size_t t = 0; t < order.size(); ++t) order[t] = t;
+            std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b) { return work[a] > work[b]; });
+            std::vector<TsTile> sorted;
+            sorted.reserve(order.size());
+            for (size_t t : order) {
+                sorted.push_back(ts_tiles[t]);
+                P->ts_max_tile_floats = std::max(P->ts_max_tile_floats, 2 * ts_tiles[t].P * ts_tiles[t].ntgt);
+                P->ts_max_chunks = std::max(P->ts_max_chunks, ts_tiles[t].nchunk);
+            }
+            P->ts_tiles.upload(sorted, cnt, st);
+            P->ts_chunks.upload(ts_chunks, cnt, st);
+            P->ts_cols.upload(ts_cols, cnt, st);
+            P->n_ts_tiles = (int64_t)sorted.size();
+            int optin = 0, dev = 0;
+            HFMM_CUDA(cudaGetDevice(&dev));
+            HFMM_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+            if (m2l_ts_smem(P->ts_max_tile_floats, P->ts_max_chunks) > (size_t)optin) {
+                // a tile with more chunks than fit beside its locals: keep the source-stationary kernel
+                P->n_ts_tiles = 0;
+            }
+        }
         for (int l = 3; l <= L; ++l) {  // L2L: parents at l-1 -> children at l
             std::vector<std::vector<int2>> b8(8);
             const HostLevel& ch = lv[l];
@@ -740,7 +971,7 @@ static void build_plan(hfmm_plan* P, const double* V, int64_t nv, const int32_t*
                 at += pack[q].second;
             }
         }
-        const int kGroupItems = m2l_tc_max_group();
+        const int kGroupItems = m2l_tc_max_group();  // split further by apply_tc_group
         const int kSmallGroup = 4;  // M2M/L2L have 8 operators per level: small groups keep every SM busy
         auto make_groups = [&](int64_t ib, int64_t ie, int64_t op0, int64_t opsz, int64_t base, int Pl,
                                int gmax) {
@@ -792,6 +1023,10 @@ static void build_plan(hfmm_plan* P, const double* V, int64_t nv, const int32_t*
         P->host_items = std::move(items);
         P->host_cols = std::move(cols);
         P->host_groups = std::move(groups);
+        P->tc_m2l_base = P->n_tc_groups;
+        P->m2m_tc_base = P->m2m_tc;
+        P->l2l_tc_base = P->l2l_tc;
+        apply_tc_group(P, cfg.tc_group > 0 ? cfg.tc_group : m2l_tc_max_group(), st);
     }
 
     // ---------------------------------------------------------- self / near correction (Sec. 2.2)
@@ -861,6 +1096,11 @@ void hfmm_default_config(hfmm_config* c) {
     c->mem_budget_bytes = 0.0;
     c->m2l_tensor = 1;
     c->adaptive = 0;
+    c->autotune = 0;
+    c->p2p_kernel = -1;
+    c->m2l_kernel = -1;
+    c->tc_group = 0;
+    c->overlap = -1;
 }
 
 const char* hfmm_last_error(void) { return g_last_error.c_str(); }
@@ -887,7 +1127,11 @@ int hfmm_plan_create(const hfmm_config* cfg, const double* vertices, int64_t n_v
     if (cfg->leaf_max < 1 || cfg->depth < 0 || cfg->depth > 20 || cfg->p_fixed < 0 || cfg->p_fixed > HFMM_PMAX ||
         cfg->p_min < 0 || cfg->p_min > HFMM_PMAX || !(cfg->near_factor >= 0.0) || cfg->quad_order < 2 ||
         cfg->quad_order > 64 || cfg->restart < 1 || cfg->max_iter < 1 || !(cfg->tol > 0.0) ||
-        (cfg->m2l_tensor != 0 && cfg->m2l_tensor != 1) || (cfg->adaptive != 0 && cfg->adaptive != 1))
+        (cfg->m2l_tensor != 0 && cfg->m2l_tensor != 1) || (cfg->adaptive != 0 && cfg->adaptive != 1) ||
+        (cfg->autotune != 0 && cfg->autotune != 1) || cfg->p2p_kernel < -1 || cfg->p2p_kernel > 1 ||
+        cfg->m2l_kernel < -1 || cfg->m2l_kernel > 1 ||
+        (cfg->tc_group != 0 && cfg->tc_group != 8 && cfg->tc_group != 16 && cfg->tc_group != 32) ||
+        cfg->overlap < -1 || cfg->overlap > 1)
         return HFMM_E_INVALID;
     if (3 * n_tri > (int64_t)INT32_MAX / 2) return HFMM_E_INVALID;
     HFMM_GUARD_BEGIN
@@ -895,6 +1139,7 @@ int hfmm_plan_create(const hfmm_config* cfg, const double* vertices, int64_t n_v
     P->cfg = *cfg;
     P->k = k_re;
     build_plan(P.get(), vertices, n_vert, tris, n_tri, (cudaStream_t)stream);
+    if (cfg->autotune) tune_plan(P.get(), (cudaStream_t)stream);
     *out = P.release();
     return HFMM_OK;
     HFMM_GUARD_END
@@ -1007,6 +1252,34 @@ int hfmm_matvec_timed(hfmm_plan* P, const void* density, void* potential, float*
 }
 
 int64_t hfmm_launch_count(const hfmm_plan* P) { return P ? P->launches : -1; }
+
+int hfmm_tune_choose(int tunable, const float* ms, int n, int* value) {
+    if (tunable < 0 || tunable >= HFMM_NUM_TUNABLES || !ms || !value || n < 1 || n > kTuneCount[tunable])
+        return HFMM_E_INVALID;
+    int best = -1, def = -1;
+    for (int c = 0; c < n; ++c) {
+        if (!(ms[c] >= 0.f) || !std::isfinite(ms[c])) continue;  // not measured
+        if (best < 0 || ms[c] < ms[best]) best = c;
+        if (kTuneValue[tunable][c] == kTuneDefault[tunable]) def = c;
+    }
+    if (best < 0) return HFMM_E_INVALID;
+    // the default stays unless another candidate is at least 2 % faster (timing noise)
+    if (def >= 0 && ms[best] > 0.98f * ms[def]) best = def;
+    *value = kTuneValue[tunable][best];
+    return HFMM_OK;
+}
+
+int hfmm_plan_tuning(const hfmm_plan* P, int* choices, float* tuned_ms) {
+    if (!P || !choices) return HFMM_E_INVALID;
+    choices[0] = P->p2p_variant;
+    choices[1] = (P->m2l_variant == 1 && P->n_ts_tiles > 0) ? 1 : 0;
+    choices[2] = P->tc_group_used;
+    choices[3] = P->mv_mode;
+    if (tuned_ms)
+        for (int a = 0; a < HFMM_NUM_TUNABLES; ++a)
+            for (int c = 0; c < HFMM_TUNE_CANDIDATES; ++c) tuned_ms[a * HFMM_TUNE_CANDIDATES + c] = P->tune_ms[a][c];
+    return HFMM_OK;
+}
 
 int hfmm_device_status(hfmm_plan* P, void* stream) {
     if (!P) return HFMM_E_INVALID;

@@ -40,6 +40,7 @@ def test_default_config_and_status_strings():
     assert c.leaf_max == 64 and c.restart == 30 and abs(c.tol - 1e-4) < 1e-18
     assert c.near_factor == 1.0 and c.p_min == 7
     assert c.m2l_tensor == 1 and c.adaptive == 0  # tensor-core M2L, uniform tree
+    assert c.autotune == 0 and c.p2p_kernel == -1 and c.m2l_kernel == -1 and c.tc_group == 0 and c.overlap == -1
     for s in [0, 1, -1, -2, -3, -4, -5, -6]:
         assert pkg.hfmm_status_string(s) != "unknown status"
     assert pkg.hfmm_status_string(12345) == "unknown status"
@@ -64,6 +65,10 @@ def test_invalid_arguments_are_rejected_on_the_host():
     assert _create(V, F, quad_order=1)[0] == pkg.HFMM_E_INVALID
     assert _create(V, F, adaptive=2)[0] == pkg.HFMM_E_INVALID
     assert _create(V, F, m2l_tensor=-1)[0] == pkg.HFMM_E_INVALID
+    assert _create(V, F, autotune=2)[0] == pkg.HFMM_E_INVALID
+    assert _create(V, F, p2p_kernel=2)[0] == pkg.HFMM_E_INVALID
+    assert _create(V, F, tc_group=12)[0] == pkg.HFMM_E_INVALID
+    assert _create(V, F, overlap=3)[0] == pkg.HFMM_E_INVALID
     assert _create(V[:0], F)[0] == pkg.HFMM_E_INVALID          # no vertices
     assert _create(V, F[:0])[0] == pkg.HFMM_E_INVALID          # N = 0
     st, out = _create(V, F, k=0.0)
@@ -108,3 +113,27 @@ def test_package_does_not_reference_the_oracle():
                 txt = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in txt and "from oracle" not in txt, f
                 assert "hfmm_oracle" not in txt, f
+
+
+def test_tuner_rule_with_fake_timings():
+    """The plan-time tuner keeps the fastest measured candidate, but keeps the default
+    unless the fastest is at least 2 % faster; unmeasured entries (negative) are skipped."""
+    P2P, M2L, GROUP, OVERLAP = 0, 1, 2, 3
+    # near field: the default is the packed kernel (1)
+    assert pkg.hfmm_tune_choose(P2P, [0.90, 1.00]) == 0           # staged 10 % faster
+    assert pkg.hfmm_tune_choose(P2P, [0.99, 1.00]) == 1           # within noise: default kept
+    assert pkg.hfmm_tune_choose(P2P, [1.20, 1.00]) == 1
+    # M2L: the default is the source-stationary kernel (0)
+    assert pkg.hfmm_tune_choose(M2L, [2.0, 0.5]) == 1
+    assert pkg.hfmm_tune_choose(M2L, [1.0, 0.99]) == 0
+    assert pkg.hfmm_tune_choose(GROUP, [1.2, 0.9, 1.0]) == 16     # default 32 at 1.0
+    assert pkg.hfmm_tune_choose(GROUP, [0.99, 1.05, 1.0]) == 32   # 1 % faster only: default stays
+    assert pkg.hfmm_tune_choose(GROUP, [-1.0, 0.7, -1.0]) == 16   # the only measured one
+    assert pkg.hfmm_tune_choose(OVERLAP, [1.0, float("nan")]) == 0
+    for bad in ([-1.0, -1.0], []):
+        with pytest.raises(pkg.HfmmError):
+            pkg.hfmm_tune_choose(P2P, bad)
+    with pytest.raises(pkg.HfmmError):
+        pkg.hfmm_tune_choose(7, [1.0, 2.0])
+    with pytest.raises(pkg.HfmmError):
+        pkg.hfmm_tune_choose(P2P, [1.0, 2.0, 3.0])  # more values than candidates
