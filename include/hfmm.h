@@ -92,7 +92,7 @@ typedef struct {
                            (one lane per target, two sources per instruction), -1 default/tuned (-1) */
     int m2l_kernel;     /* tensor-core M2L: 0 source-stationary work items (one offset's operator
                            applied to gathered multipoles, bulk reductions into the locals);
-                           1 target-stationary tiles (a block keeps 256 targets' locals on chip and
+                           1 target-stationary tiles (a block keeps 128 targets' locals on chip and
                            applies the 56 canonical operators of the offsets' reflection classes,
                            writing each local once); -1 default/tuned (-1) */
     int tc_group;       /* work items per tensor-core block: 8, 16 or 32; 0 default/tuned (0) */
@@ -100,6 +100,10 @@ typedef struct {
                            correction on a second branch beside the far field, the whole matvec
                            captured once as a CUDA graph and replayed; 0 one stage after another;
                            -1 default/tuned (-1) */
+    int precision;      /* 1: the plan also keeps an FP64 near field and correction: FP64 positions
+                           and weights, correction integrals with FP64 quadrature nodes kept in
+                           FP64, used by hfmm_matvec_df and by the outer residual of
+                           hfmm_solve_refined (the far field stays FP32); 0: FP32 only (0) */
 } hfmm_config;
 
 /* Fills *cfg with the defaults shown in parentheses above (p_min = 7). */
@@ -223,6 +227,17 @@ int hfmm_field(hfmm_plan* plan, const void* density, const double* targets, int6
  */
 int hfmm_solve_refined(hfmm_plan* inner, hfmm_plan* outer, const void* rhs, void* x_out, double tol_outer,
                        int max_outer, int* outer_iters, int* inner_iters, double* relres_out, void* stream);
+
+/*
+ * Double-float matvec for one right-hand side: density_df and potential_df are device arrays
+ * of N float4 (re_hi, im_hi, re_lo, im_lo), user order, the value being hi + lo.  On a plan
+ * created with precision = 1, the near field (the point sum over each leaf's own and
+ * neighbouring leaves, Eq. 7) and the near/self correction (Sec. 2.2) are evaluated in FP64 on
+ * the full hi + lo density; the far field (Sec. 2.3's FMM) in FP32 on the high part.  parts:
+ * bit 0 near field, 1 far field, 2 correction (7: the whole operator).  Stream-ordered.
+ * HFMM_E_INVALID on a precision-0 plan or bad arguments.
+ */
+int hfmm_matvec_df(hfmm_plan* plan, const void* density_df, void* potential_df, int parts, void* stream);
 
 /*
  * hfmm_matvec for one right-hand side with CUDA events recorded on `stream`

@@ -30,7 +30,7 @@ EXPORTED = [
     "hfmm_plan_info", "hfmm_matvec", "hfmm_matvec_parts", "hfmm_direct", "hfmm_rhs_planewave",
     "hfmm_solve", "hfmm_solve_refined", "hfmm_status_string", "hfmm_last_error", "hfmm_matvec_timed",
     "hfmm_launch_count", "hfmm_plan_costs", "hfmm_point_sum_noalloc", "hfmm_device_status", "hfmm_field",
-    "hfmm_matvec_host", "hfmm_plan_tuning", "hfmm_tune_choose",
+    "hfmm_matvec_host", "hfmm_plan_tuning", "hfmm_tune_choose", "hfmm_matvec_df",
 ]
 HFMM_NOALLOC_MAX_POINTS = 262144
 STAGES = ["prep", "p2p", "p2m", "m2m", "m2l_simt", "m2l", "l2l", "l2p", "corr", "output"]
@@ -55,6 +55,7 @@ class hfmm_config(ctypes.Structure):
         ("m2l_kernel", ctypes.c_int),
         ("tc_group", ctypes.c_int),
         ("overlap", ctypes.c_int),
+        ("precision", ctypes.c_int),
     ]
 
 
@@ -88,6 +89,7 @@ def lib():
         L.hfmm_matvec.argtypes = [vp, vp, vp, ctypes.c_int, vp]
         L.hfmm_matvec_parts.argtypes = [vp, vp, vp, ctypes.c_int, ctypes.c_int, vp]
         L.hfmm_matvec_host.argtypes = [vp, vp, vp, ctypes.c_int, vp]
+        L.hfmm_matvec_df.argtypes = [vp, vp, vp, ctypes.c_int, vp]
         L.hfmm_plan_tuning.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_float)]
         L.hfmm_tune_choose.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_float), ctypes.c_int,
                                        ctypes.POINTER(ctypes.c_int)]
@@ -227,6 +229,44 @@ def hfmm_matvec_host(plan, density, potential, nrhs=1, stream=None):
             raise ValueError(f"{name}: expected a contiguous complex64 CPU tensor of {n * nrhs} elements")
     _check(lib().hfmm_matvec_host(plan, _ptr(density), _ptr(potential), int(nrhs), _stream(stream)),
            "hfmm_matvec_host")
+
+
+def _df_vec(t, n, name):
+    import torch
+
+    if isinstance(t, int):
+        return
+    if not (t.is_cuda and t.dtype == torch.float32 and t.is_contiguous() and t.numel() == 4 * n):
+        raise ValueError(f"{name}: expected a contiguous float32 CUDA tensor of N x 4 (re_hi, im_hi, re_lo, im_lo)")
+
+
+def df_from_complex(x, device="cuda"):
+    """complex128 numpy vector -> N x 4 float32 tensor (re_hi, im_hi, re_lo, im_lo), hi + lo = x."""
+    import numpy as np
+    import torch
+
+    x = np.asarray(x, dtype=np.complex128)
+    hi = x.astype(np.complex64)
+    lo = (x - hi.astype(np.complex128)).astype(np.complex64)
+    out = np.stack([hi.real, hi.imag, lo.real, lo.imag], axis=1).astype(np.float32)
+    return torch.from_numpy(np.ascontiguousarray(out)).to(device)
+
+
+def df_to_complex(t):
+    """N x 4 float32 tensor (re_hi, im_hi, re_lo, im_lo) -> complex128 numpy vector hi + lo."""
+    import numpy as np
+
+    a = t.detach().cpu().numpy().astype(np.float64).reshape(-1, 4)
+    return (a[:, 0] + a[:, 2]) + 1j * (a[:, 1] + a[:, 3])
+
+
+def hfmm_matvec_df(plan, density_df, potential_df, parts=7, stream=None):
+    """Double-float matvec (precision = 1 plans): N x 4 float32 CUDA tensors in and out."""
+    n = hfmm_num_points(plan)
+    _df_vec(density_df, n, "density_df")
+    _df_vec(potential_df, n, "potential_df")
+    _check(lib().hfmm_matvec_df(plan, _ptr(density_df), _ptr(potential_df), int(parts), _stream(stream)),
+           "hfmm_matvec_df")
 
 
 def hfmm_matvec_parts(plan, density, potential, parts, nrhs=1, stream=None):
@@ -389,6 +429,9 @@ class Plan:
 
     def matvec_host(self, density, potential, nrhs=1, stream=None):
         hfmm_matvec_host(self.handle, density, potential, nrhs, stream)
+
+    def matvec_df(self, density_df, potential_df, parts=7, stream=None):
+        hfmm_matvec_df(self.handle, density_df, potential_df, parts, stream)
 
     def matvec_parts(self, density, potential, parts, nrhs=1, stream=None):
         hfmm_matvec_parts(self.handle, density, potential, parts, nrhs, stream)

@@ -430,18 +430,29 @@ __device__ static d3 closest_on_triangle(d3 p, d3 a, d3 b, d3 c) {
     return a + (vb * den) * ab + (vc * den) * ac;
 }
 
-__device__ __forceinline__ float3 f3(d3 a) { return make_float3((float)a.x, (float)a.y, (float)a.z); }
+template <typename T>
+struct v3 {
+    T x, y, z;
+};
+template <typename T>
+__device__ __forceinline__ v3<T> cv(d3 a) {
+    return {(T)a.x, (T)a.y, (T)a.z};
+}
+__device__ __forceinline__ void sc(float a, float* s, float* c) { sincosf(a, s, c); }
+__device__ __forceinline__ void sc(double a, double* s, double* c) { sincos(a, s, c); }
 
 // out[a] = int_T G(x,y) (2 lambda_a(y) - 1/3) dS_y
 //
 // The geometry of each sub-triangle (nearest point, edge frame, the limits of the
-// sinh-graded edge coordinate) is taken in FP64; the 3 nq^2 quadrature nodes run in
-// FP32 in coordinates relative to x (lengths of the order of the mesh size, so the
-// node positions keep FP32's relative precision), each row of nq nodes summed in FP32
-// and the rows in FP64.  Every node term is positive apart from the phase, so the
-// integrals carry about 1e-6 relative error against 1e-7 for FP32 storage.
+// sinh-graded edge coordinate) is taken in FP64; the 3 nq^2 quadrature nodes run in T in
+// coordinates relative to x (lengths of the order of the mesh size, so the node positions
+// keep T's relative precision), each row of nq nodes summed in T and the rows in FP64.  With
+// T = float every node term is positive apart from the phase, so the integrals carry about
+// 1e-6 relative error against 1e-7 for FP32 storage; T = double (the accurate operator)
+// leaves the rule's own error.
+template <typename T>
 __device__ static void tri_integrals(d3 x, d3 v0, d3 v1, d3 v2, double k, bool self, int nq,
-                                     const float* gx, const float* gw, double2 out[3]) {
+                                     const T* gx, const T* gw, double2 out[3]) {
     d3 nn = cross(v1 - v0, v2 - v0);
     double twoA = nrm(nn);
     d3 nh = (1.0 / twoA) * nn;
@@ -454,10 +465,10 @@ __device__ static void tri_integrals(d3 x, d3 v0, d3 v1, d3 v2, double k, bool s
     d3 vv[3] = {v0, v1, v2};
     double acc_r[3] = {0, 0, 0}, acc_i[3] = {0, 0, 0};
     // node-loop constants: positions relative to x, barycentric gradients
-    const float3 pcx = f3(pc - x), pcv = f3(pc - v0);
-    const float3 gf[3] = {f3(g[0]), f3(g[1]), f3(g[2])};
-    const float kf = (float)k, deltaf = (float)delta;
-    const float inv4pi = (float)(1.0 / (4.0 * kPi));
+    const v3<T> pcx = cv<T>(pc - x), pcv = cv<T>(pc - v0);
+    const v3<T> gf[3] = {cv<T>(g[0]), cv<T>(g[1]), cv<T>(g[2])};
+    const T kf = (T)k, deltaf = (T)delta;
+    const T inv4pi = (T)(1.0 / (4.0 * kPi));
     for (int e = 0; e < 3; ++e) {
         d3 a = vv[e], b = vv[(e + 1) % 3];
         d3 ed = b - a;
@@ -469,42 +480,42 @@ __device__ static void tri_integrals(d3 x, d3 v0, d3 v1, d3 v2, double k, bool s
         double de = nrm(perp);
         if (de <= 1e-12 * len) continue;  // pc on this edge: empty sub-triangle
         double s0 = asinh(lm / de), s1 = asinh(lp / de);
-        const float s0f = (float)s0, dsf = (float)(s1 - s0), def = (float)de;
-        const float3 pf = f3(perp), lf = f3(lh);
+        const T s0f = (T)s0, dsf = (T)(s1 - s0), def = (T)de;
+        const v3<T> pf = cv<T>(perp), lf = cv<T>(lh);
         for (int iq = 0; iq < nq; ++iq) {
-            const float s = s0f + dsf * gx[iq];
-            const float ws = dsf * gw[iq];
-            const float l = def * sinhf(s);
-            const float3 E = make_float3(pf.x + l * lf.x, pf.y + l * lf.y, pf.z + l * lf.z);
-            const float En = sqrtf(E.x * E.x + E.y * E.y + E.z * E.z);  // = de cosh(s) = dl/ds
-            const float tmax_tau = delta > 0.0 ? asinhf(En / deltaf) : 1.0f;
-            const float rowc = def * En * ws;
-            float rr[3] = {0.f, 0.f, 0.f}, ri[3] = {0.f, 0.f, 0.f};
+            const T s = s0f + dsf * gx[iq];
+            const T ws = dsf * gw[iq];
+            const T l = def * sinh(s);
+            const v3<T> E = {pf.x + l * lf.x, pf.y + l * lf.y, pf.z + l * lf.z};
+            const T En = sqrt(E.x * E.x + E.y * E.y + E.z * E.z);  // = de cosh(s) = dl/ds
+            const T tmax_tau = delta > 0.0 ? asinh(En / deltaf) : (T)1;
+            const T rowc = def * En * ws;
+            T rr[3] = {0, 0, 0}, ri[3] = {0, 0, 0};
             for (int jq = 0; jq < nq; ++jq) {
-                float t, wt;
+                T t, wt;
                 if (delta > 0.0) {
-                    const float tau = tmax_tau * gx[jq];
-                    const float q = deltaf / En;
-                    t = q * sinhf(tau);
-                    wt = tmax_tau * gw[jq] * q * coshf(tau);
+                    const T tau = tmax_tau * gx[jq];
+                    const T q = deltaf / En;
+                    t = q * sinh(tau);
+                    wt = tmax_tau * gw[jq] * q * cosh(tau);
                 } else {
                     t = gx[jq];
                     wt = gw[jq];
                 }
                 // y - x and y - v0 for y = pc + t E
-                const float3 yx = make_float3(pcx.x + t * E.x, pcx.y + t * E.y, pcx.z + t * E.z);
-                const float3 yv = make_float3(pcv.x + t * E.x, pcv.y + t * E.y, pcv.z + t * E.z);
-                const float R = sqrtf(yx.x * yx.x + yx.y * yx.y + yx.z * yx.z);
+                const v3<T> yx = {pcx.x + t * E.x, pcx.y + t * E.y, pcx.z + t * E.z};
+                const v3<T> yv = {pcv.x + t * E.x, pcv.y + t * E.y, pcv.z + t * E.z};
+                const T R = sqrt(yx.x * yx.x + yx.y * yx.y + yx.z * yx.z);
                 // dS = t * de * dl * dt = t * de * En * ds * dt
-                float sn, cs;
-                sincosf(kf * R, &sn, &cs);
-                const float f = t * rowc * wt * inv4pi / R;
-                const float lam[3] = {1.0f + gf[0].x * yv.x + gf[0].y * yv.y + gf[0].z * yv.z,
-                                      gf[1].x * yv.x + gf[1].y * yv.y + gf[1].z * yv.z,
-                                      gf[2].x * yv.x + gf[2].y * yv.y + gf[2].z * yv.z};
+                T sn, cs;
+                sc(kf * R, &sn, &cs);
+                const T f = t * rowc * wt * inv4pi / R;
+                const T lam[3] = {(T)1 + gf[0].x * yv.x + gf[0].y * yv.y + gf[0].z * yv.z,
+                                  gf[1].x * yv.x + gf[1].y * yv.y + gf[1].z * yv.z,
+                                  gf[2].x * yv.x + gf[2].y * yv.y + gf[2].z * yv.z};
 #pragma unroll
                 for (int q = 0; q < 3; ++q) {
-                    const float L = 2.0f * lam[q] - (1.0f / 3.0f);
+                    const T L = (T)2 * lam[q] - (T)1 / (T)3;
                     rr[q] += f * cs * L;
                     ri[q] += f * sn * L;
                 }
@@ -591,11 +602,14 @@ __global__ void k_corr_count(CorrInputs in, int64_t* __restrict__ rowptr, int* _
 
 __global__ void k_corr_fill(CorrInputs in, const double* __restrict__ gx, const double* __restrict__ gw,
                             const int64_t* __restrict__ rowptr, int32_t* __restrict__ col,
-                            float2* __restrict__ val, int* __restrict__ overflow) {
-    __shared__ float sgx[64], sgw[64];  // the rule on [0, 1] (quad_order <= 64)
+                            float2* __restrict__ val, double2* __restrict__ val64, int* __restrict__ overflow) {
+    __shared__ double sgx[64], sgw[64];  // the rule on [0, 1] (quad_order <= 64)
+    __shared__ float sgxf[64], sgwf[64];
     for (int q = threadIdx.x; q < in.quad_order; q += blockDim.x) {
-        sgx[q] = (float)gx[q];
-        sgw[q] = (float)gw[q];
+        sgx[q] = gx[q];
+        sgw[q] = gw[q];
+        sgxf[q] = (float)gx[q];
+        sgwf[q] = (float)gw[q];
     }
     __syncthreads();
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -613,7 +627,10 @@ __global__ void k_corr_fill(CorrInputs in, const double* __restrict__ gx, const 
             v[a] = mk(in.V[3 * (int64_t)vi], in.V[3 * (int64_t)vi + 1], in.V[3 * (int64_t)vi + 2]);
         }
         double2 I3[3];
-        tri_integrals(x, v[0], v[1], v[2], in.k, n == own, in.quad_order, sgx, sgw, I3);
+        if (val64)  // the accurate operator: FP64 nodes
+            tri_integrals<double>(x, v[0], v[1], v[2], in.k, n == own, in.quad_order, sgx, sgw, I3);
+        else
+            tri_integrals<float>(x, v[0], v[1], v[2], in.k, n == own, in.quad_order, sgxf, sgwf, I3);
         for (int a = 0; a < 3; ++a) {
             int32_t js = in.iperm[3 * (int64_t)n + a];
             double re = I3[a].x, im = I3[a].y;
@@ -631,6 +648,7 @@ __global__ void k_corr_fill(CorrInputs in, const double* __restrict__ gx, const 
             double sc = 4.0 * kPi / (in.k * wj);
             col[o + a] = js;
             val[o + a] = make_float2((float)(re * sc), (float)(im * sc));
+            if (val64) val64[o + a] = make_double2(re * sc, im * sc);
         }
         o += 3;
     }
@@ -669,7 +687,9 @@ int64_t build_correction(hfmm_plan* P, const CorrInputs& in, cudaStream_t st) {
     DBuf<double> d_gx, d_gw;
     d_gx.upload(gx, nullptr, st);
     d_gw.upload(gw, nullptr, st);
-    k_corr_fill<<<nb, 128, 0, st>>>(in, d_gx.p, d_gw.p, P->corr_ptr.p, P->corr_col.p, P->corr_val.p, ovf.p);
+    if (P->cfg.precision == 1) P->corr_val64.alloc(nnz, &P->dev_bytes);
+    k_corr_fill<<<nb, 128, 0, st>>>(in, d_gx.p, d_gw.p, P->corr_ptr.p, P->corr_col.p, P->corr_val.p,
+                                     P->cfg.precision == 1 ? P->corr_val64.p : nullptr, ovf.p);
     HFMM_CUDA(cudaGetLastError());
     HFMM_CUDA(cudaStreamSynchronize(st));
     return nnz;

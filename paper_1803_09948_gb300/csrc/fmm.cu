@@ -1418,9 +1418,10 @@ static void far_stage(hfmm_plan* P, int parts, cudaStream_t st) {
     mark_stage(P, 5, st);
     if (far) {
         if (P->m2l_variant == 1 && P->n_ts_tiles > 0) {
-            m2l_ts_launch(P->ts_tiles.p, P->n_ts_tiles, P->ts_max_tile_floats, P->ts_max_chunks, P->ts_chunks.p,
-                          P->ts_cols.p, P->m2l_canon.p, P->coef.p, P->dev_err.p, st);
-            ++P->launches;
+            m2l_ts_split(P->ts_split, P->ts_split_boxes, P->coef.p, P->ts_bx.p, st);
+            m2l_ts_launch(P->ts_tiles.p, P->n_ts_tiles, P->ts_max_chunks, P->ts_chunks.p, P->ts_cols.p,
+                          P->m2l_canon.p, P->ts_bx.p, P->coef.p, P->dev_err.p, st);
+            P->launches += 2;
         } else if (P->n_tc_groups > 0) {
             m2l_tc_launch(P->tc_groups.p, P->n_tc_groups, P->items.p, P->item_cols.p, P->aops.p, P->coef.p,
                           P->dev_err.p, 1, st);

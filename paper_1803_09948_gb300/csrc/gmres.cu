@@ -817,11 +817,17 @@ int run_refinement(hfmm_plan* Pi, hfmm_plan* Po, const float2* rhs, float2* x_ou
         HFMM_CUDA(cudaStreamSynchronize(st));
         return std::sqrt(h.x);
     };
-    // A_outer applied to the iterate (its FP32 rounding; the FMM computes in FP32)
+    // A_outer applied to the iterate: on a precision = 1 plan the near field and correction in
+    // FP64 on the whole double-float iterate (far field FP32); else the FP32 operator on its
+    // high part
     auto outer_residual = [&]() {
-        launch_density_prep(Po, Pi->rx.p, VecKind::DoubleFloat, Po->sig.p, st);
-        run_matvec_sorted(Po, 7, st);
-        launch_output(Po, Po->phi.p, Pi->rr.p, VecKind::DoubleFloat, st);
+        if (Po->cfg.precision == 1) {
+            run_matvec_df(Po, Pi->rx.p, Pi->rr.p, 7, st);
+        } else {
+            launch_density_prep(Po, Pi->rx.p, VecKind::DoubleFloat, Po->sig.p, st);
+            run_matvec_sorted(Po, 7, st);
+            launch_output(Po, Po->phi.p, Pi->rr.p, VecKind::DoubleFloat, st);
+        }
         k_sub_df<<<nb, 256, 0, st>>>(N, Pi->rb.p, Pi->rr.p, Pi->rr.p);
         Pi->launches += 1;
         return norm(Pi->rr.p);

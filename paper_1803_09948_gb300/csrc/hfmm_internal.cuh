@@ -81,22 +81,37 @@ struct TransItem {
 
 // Target-stationary tensor-core M2L (m2l_ts.cu).  A tile holds up to kTsTile consecutive
 // target boxes of one level; its translations are grouped by canonical operator (the
-// offsets' reflection classes) into chunks of up to 64 columns.
-constexpr int kTsTile = 256;
+// offsets' reflection classes) into chunks of up to kTsChunkCols columns.
+constexpr int kTsTile = 128;
+constexpr int kTsChunkCols = 128;
+constexpr int kTsRows = 128;           // rows of a local in the kernel's real slot form
+constexpr int kTsTrash = kTsTile;      // spare row of a tile: padding columns add into it
 struct TsTile {
     int64_t dst;     // coef offset (complex elements) of the tile's first local expansion
-    int64_t src;     // coef offset of the level's multipoles
+    int64_t bx;      // offset (16-byte units) of the level's split multipoles (1 KiB per box)
     int32_t P;       // (p+1)^2 of the level (<= 64)
     int32_t ntgt;    // target boxes in the tile
     int32_t chunk0;  // first chunk
     int32_t nchunk;  // chunks
 };
 struct TsChunk {
-    int64_t op;      // offset (complex elements) of the canonical operator [P][P]
-    int32_t col0;    // first column (even): int2 {source box of the level, target slot | reflection << 16};
-                     // every chunk's range is padded to an even length (16-byte bulk copies)
-    int16_t ncol;    // columns, 1..64
+    int64_t op;      // offset (BF16 elements) of the canonical operator in the kernel's packed form
+    int32_t col0;    // first column: int2 {source box | rc << 24, target slot * kTsRows | rc << 24}, rc
+                     // the reflection code (bit 0 x, 1 y, 2 z flipped)
+    int16_t ncol;    // columns, a multiple of 8 in 8..kTsChunkCols (padding columns included)
     int16_t newop;   // 1: first chunk of its operator group
+};
+// a level whose multipoles the target-stationary kernel reads in split form
+struct TsSplitLevel {
+    int64_t src;   // coef offset of the level's multipoles
+    int64_t bx;    // offset (16-byte units) of its split form
+    int32_t P;
+    int32_t nbox;
+};
+constexpr int kTsMaxLevels = 16;
+struct TsSplitTable {
+    TsSplitLevel lev[kTsMaxLevels];
+    int nlev;
 };
 
 // A run of SIMT translation items of one column width (64, 16 or 8).
@@ -170,6 +185,10 @@ struct MatvecGraph {
     }
 };
 
+struct alignas(32) PointW64 {
+    double x, y, z, w;
+};
+
 struct hfmm_plan {
     hfmm_config cfg;
     double k = 0.0;
@@ -228,12 +247,14 @@ struct hfmm_plan {
     std::vector<SimtRange> m2l_simt;  // M2L item ranges on the SIMT kernel
     DBuf<uint16_t> aops;       // tensor-core M2L operators (BF16 hi/lo, packed)
     DBuf<int4> tc_groups;      // (first item, item count, operator, P) per tensor-core block
-    DBuf<float2> m2l_canon;    // canonical M2L operators [ncanon][P][P] of the tensor-core levels
+    DBuf<uint16_t> m2l_canon;  // canonical M2L operators of the tensor-core levels, packed BF16 (m2l_ts.cu)
     DBuf<TsTile> ts_tiles;     // target-stationary M2L work (m2l_ts.cu)
     DBuf<TsChunk> ts_chunks;
     DBuf<int2> ts_cols;
+    DBuf<uint4> ts_bx;         // split multipoles of the tensor-core levels (1 KiB per box)
+    TsSplitTable ts_split{};
+    int64_t ts_split_boxes = 0;
     int64_t n_ts_tiles = 0;
-    int ts_max_tile_floats = 0;
     int ts_max_chunks = 0;
     int64_t n_tc_groups = 0;   // the first n_tc_groups groups are M2L
     std::vector<std::pair<int64_t, int64_t>> m2m_tc, l2l_tc;  // tensor-core group ranges per level
@@ -242,6 +263,10 @@ struct hfmm_plan {
     DBuf<int64_t> corr_ptr;
     DBuf<int32_t> corr_col;
     DBuf<float2> corr_val;
+    DBuf<double2> corr_val64;  // precision = 1: the same values in FP64
+    // precision = 1: FP64 near field and correction (accurate.cu)
+    DBuf<PointW64> acc_xw;     // sorted FP64 positions and k w / (4 pi)
+    DBuf<double2> acc_sig, acc_phi;
     // scratch (one matvec at a time per plan)
     DBuf<float2> sig, phi;
     // device staging of hfmm_matvec_host (allocated on first use, kept)
@@ -294,6 +319,10 @@ void launch_density_prep(hfmm_plan* P, const void* density, VecKind kind, float2
 void launch_output(hfmm_plan* P, const float2* phi, void* out, VecKind kind, cudaStream_t st);
 // parts bit 0 near, 1 far, 2 correction; writes P->phi
 void run_matvec_sorted(hfmm_plan* P, int parts, cudaStream_t st);
+// precision = 1 plans (accurate.cu): FP64 point data at plan creation; the double-float matvec
+// (user-order float4 in / out; parts as in hfmm_matvec_parts), FP64 near field and correction
+void accurate_setup(hfmm_plan* P, cudaStream_t st);
+void run_matvec_df(hfmm_plan* P, const float4* in, float4* out, int parts, cudaStream_t st);
 // sets the matvec kernels' shared-memory limits on the current device (once; before any capture)
 void matvec_kernels_init();
 // records stage event q (if timing is active)
@@ -390,9 +419,16 @@ void m2l_tc_launch(const int4* groups, int64_t ngroups, const TransItem* items, 
                    const uint16_t* aops, float2* coef, int* err, int rhs, cudaStream_t st);
 // target-stationary M2L: one block per tile; canon holds the canonical FP32 operators
 void m2l_ts_init();  // shared-memory limit on the current device (idempotent; before any capture)
-size_t m2l_ts_smem(int max_tile_floats, int max_chunks);
-void m2l_ts_launch(const TsTile* tiles, int64_t ntiles, int max_tile_floats, int max_chunks, const TsChunk* chunks,
-                   const int2* cols, const float2* canon, float2* coef, int* err, cudaStream_t st);
+size_t m2l_ts_smem(int max_chunks);
+// the canonical operators T [nops][P][P] (P <= 64) in the kernel's packed form: per operator the
+// real-form A (128 rows, K = 128, BF16 hi then lo) in 16 pieces of 4 KiB (kTsOpElems BF16 each op)
+constexpr int64_t kTsOpElems = 128 * 256;
+void m2l_ts_pack_ops(const float2* T, int P, int nops, uint16_t* out, cudaStream_t st);
+// the levels' multipoles in the kernel's split form (BF16 hi / lo of Re and -Im in slot order,
+// plain and with the orders reversed), `boxes` boxes in all
+void m2l_ts_split(const TsSplitTable& t, int64_t boxes, const float2* coef, uint4* bx, cudaStream_t st);
+void m2l_ts_launch(const TsTile* tiles, int64_t ntiles, int max_chunks, const TsChunk* chunks, const int2* cols,
+                   const uint16_t* canon, const uint4* bx, float2* coef, int* err, cudaStream_t st);
 
 // ---------------------------------------------------------------- GMRES
 int run_gmres(hfmm_plan* P, const void* rhs, void* x, int* iters, double* relres, cudaStream_t st);

@@ -127,10 +127,16 @@ struct PairBuckets {
 
 // Target-stationary M2L work of one level (m2l_ts.cu): tiles of tt (<= kTsTile) consecutive target
 // boxes; in each tile the translations grouped by canonical operator (refl[slot].x) into
-// chunks of up to 64 columns {source box, target slot | reflection code << 16}, the code's
-// bits being the x, y, z flips that carry the canonical offset onto the slot's offset.
+// chunks of up to kTsChunkCols columns {source box | rc << 24, target slot * kTsRows | rc << 24},
+// the reflection code rc's bits being the x, y, z flips that carry the canonical offset onto
+// the slot's offset.  The kernel adds a chunk's columns into the tile eight at a time without
+// atomics, so no target may repeat within an aligned group of eight columns (a target meets one
+// canonical operator through up to eight reflections): the columns are ordered by (occurrence
+// of their target, target), which keeps equal targets apart, and where a repeat would still
+// fall into one group the group is closed with padding columns.  Padding columns (source box 0,
+// the tile's spare row kTsTrash) also fill every chunk to a multiple of eight columns.
 void emit_ts_level(const PairBuckets& pb, const std::vector<int4>& refl, int ncanon, int64_t nbox, int Pl,
-                   int64_t mofs, int64_t lofs, int64_t canon_op, int tt, std::vector<TsTile>& tiles,
+                   int64_t bxofs, int64_t lofs, int64_t canon_op, int tt, std::vector<TsTile>& tiles,
                    std::vector<TsChunk>& chunks, std::vector<int2>& cols) {
     const int64_t ntile = (nbox + tt - 1) / tt;
     std::vector<int64_t> start((size_t)(ntile * ncanon + 1), 0);
@@ -148,45 +154,55 @@ void emit_ts_level(const PairBuckets& pb, const std::vector<int4>& refl, int nca
                 make_int2(pr.x, (pr.y % tt) | (rc << 16));
         }
     }
+    const int2 pad = make_int2(0, kTsTrash * kTsRows);
+    std::vector<int> occ((size_t)tt);
+    std::vector<std::pair<int64_t, int2>> keyed;
+    std::vector<int2> cur;
     for (int64_t t = 0; t < ntile; ++t) {
         TsTile tl{};
         tl.dst = lofs + t * tt * (int64_t)Pl;
-        tl.src = mofs;
+        tl.bx = bxofs;
         tl.P = Pl;
         tl.ntgt = (int32_t)std::min<int64_t>(tt, nbox - t * tt);
         tl.chunk0 = (int32_t)chunks.size();
         for (int c = 0; c < ncanon; ++c) {
             const int64_t b = start[(size_t)(t * ncanon + c)], e = start[(size_t)(t * ncanon + c) + 1];
-            // chunks of up to 64 columns in which no target repeats (a target can meet one
-            // canonical operator through several reflections), so the kernel adds a chunk's
-            // columns into the tile without atomics; repeats move to a later chunk
-            std::vector<int2> rest(tmp.begin() + b, tmp.begin() + e), later;
-            std::vector<char> seen((size_t)tt);
+            if (b == e) continue;
+            std::fill(occ.begin(), occ.end(), 0);
+            keyed.clear();
+            for (int64_t q = b; q < e; ++q) {
+                const int j = tmp[(size_t)q].y & 0xffff, rc = tmp[(size_t)q].y >> 16;
+                const int2 col = make_int2(tmp[(size_t)q].x | (rc << 24), j * kTsRows | (rc << 24));
+                keyed.push_back({(int64_t)occ[(size_t)j]++ * tt + j, col});
+            }
+            std::stable_sort(keyed.begin(), keyed.end(),
+                             [](const std::pair<int64_t, int2>& x, const std::pair<int64_t, int2>& y) {
+                                 return x.first < y.first;
+                             });
             bool first = true;
-            while (!rest.empty()) {
+            cur.clear();
+            auto flush = [&]() {
                 TsChunk ch{};
-                ch.op = canon_op + (int64_t)c * Pl * Pl;
+                while (cur.size() & 7) cur.push_back(pad);
+                ch.op = canon_op + (int64_t)c * kTsOpElems;
                 ch.col0 = (int32_t)cols.size();
+                ch.ncol = (int16_t)cur.size();
                 ch.newop = (int16_t)first;
                 first = false;
-                std::fill(seen.begin(), seen.end(), 0);
-                later.clear();
-                int n = 0;
-                for (const int2& col : rest) {
-                    const int j = col.y & 0xffff;
-                    if (n < 64 && !seen[(size_t)j]) {
-                        seen[(size_t)j] = 1;
-                        cols.push_back(col);
-                        ++n;
-                    } else {
-                        later.push_back(col);
-                    }
-                }
-                ch.ncol = (int16_t)n;
-                if (n & 1) cols.push_back(make_int2(0, 0));  // even length: 16-byte bulk copies
+                cols.insert(cols.end(), cur.begin(), cur.end());
                 chunks.push_back(ch);
-                rest.swap(later);
+                cur.clear();
+            };
+            for (const auto& kc : keyed) {
+                const int j = kc.second.y & 0xffffff;
+                bool rep = false;
+                for (size_t q = cur.size() & ~(size_t)7; q < cur.size(); ++q) rep |= (cur[q].y & 0xffffff) == j;
+                if (rep)
+                    while (cur.size() & 7) cur.push_back(pad);
+                if ((int)cur.size() == kTsChunkCols) flush();
+                cur.push_back(kc.second);
             }
+            if (!cur.empty()) flush();
         }
         tl.nchunk = (int32_t)chunks.size() - tl.chunk0;
         if (tl.nchunk > 0) tiles.push_back(tl);
@@ -244,6 +260,14 @@ static void apply_tc_group(hfmm_plan* P, int g, cudaStream_t st) {
     }
     P->tc_group_used = g;
     P->mvg.reset();
+}
+
+// *bad = 1 if any entry is not finite (grid-stride)
+__global__ void k_flag_nonfinite(const float2* __restrict__ a, int64_t n, int* __restrict__ bad) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float2 v = a[i];
+        if (!isfinite(v.x) || !isfinite(v.y)) *bad = 1;
+    }
 }
 
 __global__ void k_tune_fill(int64_t N, float2* __restrict__ sig) {
@@ -758,7 +782,7 @@ static void build_plan(hfmm_plan* P, const double* V, int64_t nv, const int32_t*
             for (int l = 2; l <= L; ++l)
                 if (cfg.m2l_tensor && P->lev[l].P <= 64) {
                     P->lev[l].canon_op = coff;
-                    coff += (int64_t)ncanon * P->lev[l].P * P->lev[l].P;
+                    coff += (int64_t)ncanon * kTsOpElems;  // packed BF16 (m2l_ts.cu)
                 }
             if (coff > 0) P->m2l_canon.alloc((size_t)coff, cnt);
         }
@@ -782,9 +806,7 @@ static void build_plan(hfmm_plan* P, const double* V, int64_t nv, const int32_t*
             job.out2 = nullptr;
             build_projection_ops(job, k, st);
             expand_m2l_reflections(canon.p, li.P, 316, d_refl.p, P->ops.p + li.m2l_op, st);
-            if (li.canon_op >= 0)
-                HFMM_CUDA(cudaMemcpyAsync(P->m2l_canon.p + li.canon_op, canon.p, sizeof(float2) * (size_t)ncanon * li.P * li.P,
-                                          cudaMemcpyDeviceToDevice, st));
+            if (li.canon_op >= 0) m2l_ts_pack_ops(canon.p, li.P, ncanon, P->m2l_canon.p + li.canon_op, st);
             HFMM_CUDA(cudaStreamSynchronize(st));  // canon is freed at the end of this scope
             if (l >= 3) {
                 const LevelInfo& lp = P->lev[l - 1];
@@ -808,6 +830,23 @@ static void build_plan(hfmm_plan* P, const double* V, int64_t nv, const int32_t*
                 pj.out2 = P->ops.p + li.m2m_op;
                 build_projection_ops(pj, k, st);
             }
+        }
+        {
+            // FP32 translation operators: at high orders on small boxes (k a well below p) the
+            // outgoing functions exceed FP32's range; such a plan would return NaN
+            DBuf<int> bad;
+            bad.alloc(1, nullptr);
+            HFMM_CUDA(cudaMemsetAsync(bad.p, 0, sizeof(int), st));
+            k_flag_nonfinite<<<(unsigned)std::min<int64_t>((ooff + 255) / 256, 65535), 256, 0, st>>>(P->ops.p, ooff,
+                                                                                                 bad.p);
+            HFMM_CUDA(cudaGetLastError());
+            int h_bad = 0;
+            HFMM_CUDA(cudaMemcpyAsync(&h_bad, bad.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+            HFMM_CUDA(cudaStreamSynchronize(st));
+            if (h_bad)
+                throw HfmmError{HFMM_E_INVALID,
+                                "translation operators overflow FP32 at this expansion order and box size: "
+                                "lower p_fixed / p_min"};
         }
         // work items
         std::vector<TransItem> items;
@@ -838,9 +877,10 @@ static void build_plan(hfmm_plan* P, const double* V, int64_t nv, const int32_t*
         std::vector<TsTile> ts_tiles;
         std::vector<TsChunk> ts_chunks;
         std::vector<int2> ts_cols;
-        // tile size of the target-stationary M2L: the largest of 256, 128, 64, 32 targets that
-        // still gives every SM two tiles (one block per SM at a time)
+        // tile size of the target-stationary M2L: the largest of 128, 64, 32 targets that still
+        // gives every SM a tile (one block per SM at a time; larger tiles fill the chunks better)
         int ts_tt = 32;
+        std::vector<int64_t> ts_bxofs(L + 1, -1);
         {
             int dev = 0, nsm = 1;
             HFMM_CUDA(cudaGetDevice(&dev));
@@ -849,11 +889,25 @@ static void build_plan(hfmm_plan* P, const double* V, int64_t nv, const int32_t*
                 int64_t tiles = 0;
                 for (int l = 2; l <= L; ++l)
                     if (P->lev[l].canon_op >= 0) tiles += ((int64_t)lv[l].key.size() + tt - 1) / tt;
-                if (tiles >= 2 * (int64_t)nsm) {
+                if (tiles >= (int64_t)nsm) {
                     ts_tt = tt;
                     break;
                 }
             }
+            // the split multipoles of the tensor-core levels, 64 x 16 bytes per box
+            P->ts_split = TsSplitTable{};
+            P->ts_split_boxes = 0;
+            for (int l = 2; l <= L; ++l)
+                if (P->lev[l].canon_op >= 0 && P->ts_split.nlev < kTsMaxLevels &&
+                    lv[l].key.size() < ((size_t)1 << 24)) {  // column entries hold 24-bit box indices
+                    TsSplitLevel& e = P->ts_split.lev[P->ts_split.nlev++];
+                    e.src = P->lev[l].mofs;
+                    e.bx = P->ts_split_boxes * 64;
+                    e.P = P->lev[l].P;
+                    e.nbox = (int32_t)lv[l].key.size();
+                    ts_bxofs[l] = e.bx;
+                    P->ts_split_boxes += e.nbox;
+                }
         }
         for (int l = 2; l <= L; ++l) {
             lev_item_b[l] = (int64_t)items.size();
@@ -880,8 +934,8 @@ static void build_plan(hfmm_plan* P, const double* V, int64_t nv, const int32_t*
                 width = mean <= 12 ? 8 : mean <= 28 ? 16 : HFMM_TRANS_NB;
             }
             lev_width[l] = width;
-            if (P->lev[l].canon_op >= 0)
-                emit_ts_level(pb, refl, ncanon, (int64_t)lv[l].key.size(), P->lev[l].P, P->lev[l].mofs, P->lev[l].lofs,
+            if (ts_bxofs[l] >= 0)
+                emit_ts_level(pb, refl, ncanon, (int64_t)lv[l].key.size(), P->lev[l].P, ts_bxofs[l], P->lev[l].lofs,
                               P->lev[l].canon_op, ts_tt, ts_tiles, ts_chunks, ts_cols);
             emit_items(pb, ops, P->lev[l].mofs, P->lev[l].lofs, P->lev[l].P, P->lev[l].P, 1, items, cols, width);
             lev_item_e[l] = (int64_t)items.size();
@@ -903,17 +957,19 @@ static void build_plan(hfmm_plan* P, const double* V, int64_t nv, const int32_t*
             sorted.reserve(order.size());
             for (size_t t : order) {
                 sorted.push_back(ts_tiles[t]);
-                P->ts_max_tile_floats = std::max(P->ts_max_tile_floats, 2 * ts_tiles[t].P * ts_tiles[t].ntgt);
                 P->ts_max_chunks = std::max(P->ts_max_chunks, ts_tiles[t].nchunk);
             }
             P->ts_tiles.upload(sorted, cnt, st);
             P->ts_chunks.upload(ts_chunks, cnt, st);
             P->ts_cols.upload(ts_cols, cnt, st);
+            P->ts_bx.alloc((size_t)P->ts_split_boxes * 64, cnt);
             P->n_ts_tiles = (int64_t)sorted.size();
             int optin = 0, dev = 0;
             HFMM_CUDA(cudaGetDevice(&dev));
             HFMM_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-            if (m2l_ts_smem(P->ts_max_tile_floats, P->ts_max_chunks) > (size_t)optin) {
+            bool all_levels = true;  // every tensor-core level must be in the tiles
+            for (int l = 2; l <= L; ++l) all_levels &= P->lev[l].canon_op < 0 || ts_bxofs[l] >= 0;
+            if (!all_levels || m2l_ts_smem(P->ts_max_chunks) > (size_t)optin) {
                 // a tile with more chunks than fit beside its locals: keep the source-stationary kernel
                 P->n_ts_tiles = 0;
             }
@@ -1058,6 +1114,7 @@ static void build_plan(hfmm_plan* P, const double* V, int64_t nv, const int32_t*
     ci.quad_order = cfg.quad_order;
     P->corr_nnz = build_correction(P, ci, st);
     P->cost[3] = (double)P->corr_nnz;
+    if (cfg.precision == 1) accurate_setup(P, st);
     HFMM_CUDA(cudaStreamSynchronize(st));
     if (cfg.mem_budget_bytes > 0 && (double)P->dev_bytes > cfg.mem_budget_bytes)
         throw HfmmError{HFMM_E_NOMEM, "plan exceeds the configured device memory budget"};
@@ -1101,6 +1158,7 @@ void hfmm_default_config(hfmm_config* c) {
     c->m2l_kernel = -1;
     c->tc_group = 0;
     c->overlap = -1;
+    c->precision = 0;
 }
 
 const char* hfmm_last_error(void) { return g_last_error.c_str(); }
@@ -1131,7 +1189,7 @@ int hfmm_plan_create(const hfmm_config* cfg, const double* vertices, int64_t n_v
         (cfg->autotune != 0 && cfg->autotune != 1) || cfg->p2p_kernel < -1 || cfg->p2p_kernel > 1 ||
         cfg->m2l_kernel < -1 || cfg->m2l_kernel > 1 ||
         (cfg->tc_group != 0 && cfg->tc_group != 8 && cfg->tc_group != 16 && cfg->tc_group != 32) ||
-        cfg->overlap < -1 || cfg->overlap > 1)
+        cfg->overlap < -1 || cfg->overlap > 1 || (cfg->precision != 0 && cfg->precision != 1))
         return HFMM_E_INVALID;
     if (3 * n_tri > (int64_t)INT32_MAX / 2) return HFMM_E_INVALID;
     HFMM_GUARD_BEGIN
@@ -1193,6 +1251,18 @@ int hfmm_matvec_parts(hfmm_plan* P, const void* density, void* potential, int nr
         ++r0;
     }
     HFMM_CUDA(cudaGetLastError());
+    return HFMM_OK;
+    HFMM_GUARD_END
+}
+
+int hfmm_matvec_df(hfmm_plan* P, const void* density_df, void* potential_df, int parts, void* stream) {
+    if (!P || !density_df || !potential_df || parts < 0 || parts > 7) return HFMM_E_INVALID;
+    if (P->cfg.precision != 1) {
+        g_last_error = "hfmm_matvec_df needs a plan created with precision = 1";
+        return HFMM_E_INVALID;
+    }
+    HFMM_GUARD_BEGIN
+    run_matvec_df(P, (const float4*)density_df, (float4*)potential_df, parts, (cudaStream_t)stream);
     return HFMM_OK;
     HFMM_GUARD_END
 }

@@ -102,6 +102,26 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t addr, uint32_t parity) {
     return ok != 0;
 }
 
+// non-blocking: has the phase of this parity completed?
+__device__ __forceinline__ bool mbar_test_wait(uint32_t addr, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(addr), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// asynchronous copy of a 128-row x 256-bit shared-memory matrix (descriptor `src`, K-major
+// core matrices) into tensor-memory lanes 0..127, columns taddr .. taddr + 7; ordered before
+// later MMAs of the issuing thread, completion tracked by tc_commit
+__device__ __forceinline__ void tc_cp_128x256(uint32_t taddr, uint64_t src) {
+    asm volatile("tcgen05.cp.cta_group::1.128x256b [%0], %1;" ::"r"(taddr), "l"(src) : "memory");
+}
+
 __device__ __forceinline__ void mbar_arrive(uint32_t addr) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(addr) : "memory");
 }
