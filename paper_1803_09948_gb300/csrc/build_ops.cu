@@ -19,6 +19,7 @@
 // the radius when x_i is off the triangle), minus the point-rule term (FP64) that
 // the FMM already added.
 #include <cmath>
+#include <cstdlib>
 #include <cstdio>
 #include <vector>
 
@@ -295,6 +296,71 @@ __global__ void k_proj_gemm(int Pb, int Pf, int64_t Q, const double2* __restrict
     }
 }
 
+// The same product in double-float arithmetic on the FP32 pipes (GB300's FP64 rate is a
+// small fraction of its FP32 rate): each FP64 input is split into an FP32 pair hi + lo, every
+// real multiply-add is an error-free product (hi * hi and its FMA residual, plus the two
+// cross terms) added with Knuth's two-sum, so the accumulators keep about 48 significant
+// bits; the result is rounded to FP32 like the FP64 kernel's.  Inputs or products beyond FP32's
+// range give a non-finite value; the caller then repeats the batch with the FP64 kernel.
+__device__ __forceinline__ void df_mad(float& sh, float& sl, float ah, float al, float bh, float bl) {
+    const float p = __fmul_rn(ah, bh);
+    float e = __fmaf_rn(ah, bh, -p);
+    e = __fmaf_rn(ah, bl, e);
+    e = __fmaf_rn(al, bh, e);
+    const float t = __fadd_rn(sh, p);
+    const float bb = __fsub_rn(t, sh);
+    float err = __fadd_rn(__fsub_rn(sh, __fsub_rn(t, bb)), __fsub_rn(p, bb));
+    err = __fadd_rn(err, __fadd_rn(sl, e));
+    sh = __fadd_rn(t, err);
+    sl = __fsub_rn(err, __fsub_rn(sh, t));
+}
+
+__device__ __forceinline__ float4 df_split2(double2 v) {  // (re_hi, re_lo, im_hi, im_lo)
+    const float rh = (float)v.x, ih = (float)v.y;
+    return make_float4(rh, (float)(v.x - (double)rh), ih, (float)(v.y - (double)ih));
+}
+
+__global__ void k_proj_gemm_df(int Pb, int Pf, int64_t Q, const double2* __restrict__ Bw,
+                               const double2* __restrict__ E, float2* __restrict__ out,
+                               float2* __restrict__ out2) {
+    __shared__ float4 sa[16][17];
+    __shared__ float4 sb[16][17];
+    const int op = blockIdx.z;
+    const int i = blockIdx.y * 16 + threadIdx.y;
+    const int j = blockIdx.x * 16 + threadIdx.x;
+    const double2* Eo = E + (int64_t)op * Q * Pf;
+    float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
+    for (int64_t q0 = 0; q0 < Q; q0 += 16) {
+        const int ai = blockIdx.y * 16 + threadIdx.y;
+        const int64_t aq = q0 + threadIdx.x;
+        sa[threadIdx.y][threadIdx.x] = df_split2((ai < Pb && aq < Q) ? Bw[(int64_t)ai * Q + aq] : make_double2(0, 0));
+        const int64_t bq = q0 + threadIdx.y;
+        const int bj = blockIdx.x * 16 + threadIdx.x;
+        sb[threadIdx.y][threadIdx.x] = df_split2((bj < Pf && bq < Q) ? Eo[bq * Pf + bj] : make_double2(0, 0));
+        __syncthreads();
+#pragma unroll 4
+        for (int t = 0; t < 16; ++t) {
+            const float4 a = sa[threadIdx.y][t], b = sb[t][threadIdx.x];
+            df_mad(rh, rl, a.x, a.y, b.x, b.y);     // + Re a Re b
+            df_mad(rh, rl, -a.z, -a.w, b.z, b.w);   // - Im a Im b
+            df_mad(ih, il, a.x, a.y, b.z, b.w);     // + Re a Im b
+            df_mad(ih, il, a.z, a.w, b.x, b.y);     // + Im a Re b
+        }
+        __syncthreads();
+    }
+    if (i < Pb && j < Pf) {
+        const float re = __fadd_rn(rh, rl), im = __fadd_rn(ih, il);
+        out[(int64_t)op * Pb * Pf + (int64_t)i * Pf + j] = make_float2(re, im);
+        if (out2) out2[(int64_t)op * Pb * Pf + (int64_t)j * Pb + i] = make_float2(re, -im);
+    }
+}
+
+// *bad = 1 if any of the n entries is not finite (grid-stride)
+__global__ void k_any_nonfinite(const float2* __restrict__ a, int64_t n, int* __restrict__ bad) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+        if (!isfinite(a[e].x) || !isfinite(a[e].y)) *bad = 1;
+}
+
 static void gauss_legendre_host(int n, std::vector<double>& x, std::vector<double>& w) {
     x.resize(n);
     w.resize(n);
@@ -341,6 +407,11 @@ void build_projection_ops(const ProjectionJob& job, double k, cudaStream_t st) {
     int batch = (int)std::max<int64_t>(1, std::min<int64_t>(job.nops, (512ll << 20) / per_op));
     DBuf<double2> E;
     E.alloc((size_t)batch * Q * Pf, nullptr);
+    DBuf<int> bad;
+    bad.alloc(1, nullptr);
+    // HFMM_PROJECTION_FP64=1 forces the FP64 kernel (the reference the double-float one is tested against)
+    const char* env = std::getenv("HFMM_PROJECTION_FP64");
+    const bool fp64_only = env && env[0] == '1';
     for (int o0 = 0; o0 < job.nops; o0 += batch) {
         int nb = std::min(batch, job.nops - o0);
         int64_t nthreads = Q * nb;
@@ -348,8 +419,21 @@ void build_projection_ops(const ProjectionJob& job, double k, cudaStream_t st) {
             job.type, job.pf, job.sf, k, job.rho, job.nth, job.nph, d_gx.p, d_d0.p + 3 * o0, nb, E.p);
         HFMM_CUDA(cudaGetLastError());
         dim3 grid((Pf + 15) / 16, (Pb + 15) / 16, nb);
-        k_proj_gemm<<<grid, dim3(16, 16), 0, st>>>(Pb, Pf, Q, Bw.p, E.p, job.out + (int64_t)o0 * Pb * Pf,
-                                                   job.out2 ? job.out2 + (int64_t)o0 * Pb * Pf : nullptr);
+        float2* o = job.out + (int64_t)o0 * Pb * Pf;
+        float2* o2 = job.out2 ? job.out2 + (int64_t)o0 * Pb * Pf : nullptr;
+        bool redo = fp64_only;
+        if (!fp64_only) {
+            k_proj_gemm_df<<<grid, dim3(16, 16), 0, st>>>(Pb, Pf, Q, Bw.p, E.p, o, o2);
+            HFMM_CUDA(cudaMemsetAsync(bad.p, 0, sizeof(int), st));
+            const int64_t n = (int64_t)nb * Pb * Pf;
+            k_any_nonfinite<<<(unsigned)std::min<int64_t>((n + 255) / 256, 4096), 256, 0, st>>>(o, n, bad.p);
+            HFMM_CUDA(cudaGetLastError());
+            int h_bad = 0;
+            HFMM_CUDA(cudaMemcpyAsync(&h_bad, bad.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+            HFMM_CUDA(cudaStreamSynchronize(st));
+            redo = h_bad != 0;
+        }
+        if (redo) k_proj_gemm<<<grid, dim3(16, 16), 0, st>>>(Pb, Pf, Q, Bw.p, E.p, o, o2);
         HFMM_CUDA(cudaGetLastError());
     }
     HFMM_CUDA(cudaStreamSynchronize(st));  // scratch buffers are freed on return

@@ -6,13 +6,16 @@ its plan (octree, translation operators, near-field correction) and Krylov
 basis are built on the device when the request is admitted, stay resident
 until its solve has finished, and are then released.
 
-  * Admission: a request is started only while the device memory reserved by
+  * Admission: a request is started as soon as the device memory reserved by
     the requests in flight, plus its own estimate, stays within the budget
-    (by default 80 % of the device's memory); requests wait in arrival order.
-    A request whose estimate alone exceeds the budget is rejected.
-  * Concurrency: `workers` host threads, each with its own CUDA stream, so the
-    plan building of one request (host octree and lists, device operator and
-    correction kernels) overlaps the solves of others.
+    (by default 80 % of the device's memory) and a slot is free; requests are
+    admitted in arrival order.  A request whose estimate alone exceeds the
+    budget is rejected.
+  * Concurrency: every admitted request runs at once on its own host thread and
+    CUDA stream (up to `max_inflight` slots, 64 by default, so that the memory
+    budget is what bounds it), so the plan building of some requests (host
+    octree and lists, device operator and correction kernels) overlaps the
+    solves of others and their kernels share the device.
   * Multi-RHS requests use the library's lockstep solver (one batched,
     graph-captured matvec per GMRES iteration for all directions).
 
@@ -23,22 +26,42 @@ second of wall time from the first arrival to the last completion).
 """
 from __future__ import annotations
 
-import queue
 import threading
 import time
 
 import numpy as np
 
 
-def estimate_bytes(n_points: int, nrhs: int, restart: int) -> int:
-    """Device memory of one request: plan (about 1.2 KB per point: sorted points,
-    the near-field correction, expansions, operators) plus the Krylov basis and
-    work vectors ((restart + 1) + 4 double-float vectors per right-hand side, 16 B per
-    point each) plus, for several right-hand sides, the batched matvec buffers."""
+def _order(k: float, a: float, p_min: int = 7) -> int:
+    """The plan's per-level expansion order p = ceil(k a + 6 log10(k a + pi)), at least p_min."""
+    import math
+
+    return max(p_min, int(math.ceil(k * a + 6.0 * math.log10(k * a + math.pi))))
+
+
+def estimate_bytes(n_points: int, nrhs: int, restart: int, k: float = 0.0, extent: float = 0.0,
+                   leaf_max: int = 64) -> int:
+    """Device memory of one request: plan (about 1.2 KB per point: sorted points, the
+    near-field correction, expansions) plus its translation operators (per level from 2 to
+    the leaf level: 316 M2L matrices of (p+1)^2 x (p+1)^2 complex64 and 16 M2M / L2L ones,
+    p from the plan's order formula on a box of side extent / 2^l), plus the Krylov basis and
+    work vectors ((restart + 1) + 4 double-float vectors per right-hand side, 16 B per point
+    each) plus, for several right-hand sides, the batched matvec buffers; 128 MB of slack."""
+    import math
+
     per_point = 1200 + 16 * nrhs * (restart + 5)
     if nrhs > 1:
         per_point += 200 * nrhs
-    return int(n_points * per_point + (64 << 20))
+    ops = 0
+    if k > 0.0 and extent > 0.0:
+        depth = max(2, int(math.ceil(math.log(max(n_points / leaf_max, 1.0)) / math.log(4.0))) + 1)
+        prev = None
+        for lev in range(2, depth + 1):
+            a = 0.5 * math.sqrt(3.0) * extent / 2 ** lev
+            P = (_order(k, a) + 1) ** 2
+            ops += 316 * P * P * 8 + (16 * P * prev * 8 if prev else 0)
+            prev = P
+    return int(n_points * per_point + ops + (128 << 20))
 
 
 class Admission:
@@ -81,7 +104,7 @@ class Admission:
             self._cv.notify_all()
 
 
-def gpu_executor(restart: int = 30, tol: float = 1e-4, keep_solution: bool = False):
+def gpu_executor(restart: int = 30, tol: float = 1e-4, keep_solution: bool = False, max_iter: int = 1000):
     """Executor that solves a request with the library on the calling thread's stream.
     Returns a function(request, stream) -> dict of timings and results (with the
     solutions, [nrhs][N] complex64 on the host, under "x" when keep_solution)."""
@@ -92,7 +115,7 @@ def gpu_executor(restart: int = 30, tol: float = 1e-4, keep_solution: bool = Fal
     def run(req, stream):
         t0 = time.perf_counter()
         with torch.cuda.stream(stream):
-            plan = Plan(req["V"], req["F"], req["k"], stream=stream, restart=restart, tol=tol)
+            plan = Plan(req["V"], req["F"], req["k"], stream=stream, restart=restart, tol=tol, max_iter=max_iter)
             try:
                 torch.cuda.synchronize()  # plan ready (its build is part of the request's time)
                 t1 = time.perf_counter()
@@ -117,16 +140,17 @@ def gpu_executor(restart: int = 30, tol: float = 1e-4, keep_solution: bool = Fal
 
 
 class ServingEngine:
-    def __init__(self, executor=None, workers: int = 2, budget_bytes: int | None = None,
-                 budget_frac: float = 0.8, restart: int = 30, tol: float = 1e-4, stream_factory=None):
+    def __init__(self, executor=None, max_inflight: int = 64, budget_bytes: int | None = None,
+                 budget_frac: float = 0.8, restart: int = 30, tol: float = 1e-4, stream_factory=None,
+                 workers: int | None = None, max_iter: int = 1000):
         if budget_bytes is None:
             import torch
 
             budget_bytes = int(budget_frac * torch.cuda.mem_get_info()[1])
         self.admission = Admission(budget_bytes)
-        self.workers = int(workers)
+        self.max_inflight = int(workers if workers is not None else max_inflight)  # slots
         self.restart = int(restart)
-        self.executor = executor if executor is not None else gpu_executor(restart, tol)
+        self.executor = executor if executor is not None else gpu_executor(restart, tol, max_iter=max_iter)
         if stream_factory is None:
             def stream_factory():
                 import torch
@@ -138,52 +162,53 @@ class ServingEngine:
         """requests: dicts with arrival_s, V, F, k, nrhs, dirs (and anything else, passed
         through). Blocks until all are served; returns (records, summary)."""
         reqs = sorted(requests, key=lambda r: r["arrival_s"])
-        ready: queue.Queue = queue.Queue()
         records = []
         rec_lock = threading.Lock()
+        slots = threading.Semaphore(self.max_inflight)
         t0 = time.perf_counter()
+        running = []
 
-        def client():
-            for r in reqs:
-                delay = t0 + r["arrival_s"] - time.perf_counter()
-                if delay > 0:
-                    time.sleep(delay)
-                ready.put((self.admission.ticket(), time.perf_counter(), r))
-            for _ in range(self.workers):
-                ready.put(None)
+        def serve(r, t_arrive, est, stream):
+            rec = {"id": r.get("id"), "arrival_s": t_arrive - t0, "nrhs": r["nrhs"], "estimate_bytes": est}
+            t_start = time.perf_counter()
+            try:
+                out = self.executor(r, stream)
+                rec.update(out)
+                rec["status"] = "ok" if out.get("status", 0) == 0 else "not converged"
+            except Exception as e:  # the request fails; the server goes on
+                rec.update(status="error", error=str(e))
+            finally:
+                self.admission.release(est)
+                slots.release()
+            t_done = time.perf_counter()
+            rec.update(start_s=t_start - t0, done_s=t_done - t0, wait_s=t_start - t_arrive, latency_s=t_done - t_arrive)
+            with rec_lock:
+                records.append(rec)
 
-        def worker():
-            stream = self.stream_factory()
-            while True:
-                item = ready.get()
-                if item is None:
-                    return
-                ticket, t_arrive, r = item
-                est = estimate_bytes(len(r["F"]) * 3, r["nrhs"], self.restart)
-                rec = {"id": r.get("id"), "arrival_s": t_arrive - t0, "nrhs": r["nrhs"], "estimate_bytes": est}
-                if not self.admission.acquire(ticket, est):
-                    rec.update(status="rejected", done_s=time.perf_counter() - t0)
-                else:
-                    t_start = time.perf_counter()
-                    try:
-                        out = self.executor(r, stream)
-                        rec.update(out)
-                        rec["status"] = "ok" if out.get("status", 0) == 0 else "not converged"
-                    except Exception as e:  # the request fails; the server goes on
-                        rec.update(status="error", error=str(e))
-                    finally:
-                        self.admission.release(est)
-                    t_done = time.perf_counter()
-                    rec.update(start_s=t_start - t0, done_s=t_done - t0, wait_s=t_start - t_arrive,
-                               latency_s=t_done - t_arrive)
+        # the dispatcher: requests in arrival order; each starts as soon as a slot and its
+        # memory are free (admission in order, so a large request is not overtaken)
+        for r in reqs:
+            delay = t0 + r["arrival_s"] - time.perf_counter()
+            if delay > 0:
+                time.sleep(delay)
+            t_arrive = t0 + r["arrival_s"]  # the request exists from its arrival, even while the dispatcher waits
+            V = np.asarray(r["V"], dtype=np.float64)
+            extent = float((V.max(axis=0) - V.min(axis=0)).max()) if V.size else 0.0
+            est = estimate_bytes(len(r["F"]) * 3, r["nrhs"], self.restart, float(r["k"]), extent)
+            ticket = self.admission.ticket()
+            slots.acquire()
+            if not self.admission.acquire(ticket, est):
+                slots.release()
                 with rec_lock:
-                    records.append(rec)
-
-        threads = [threading.Thread(target=client)] + [threading.Thread(target=worker) for _ in range(self.workers)]
-        for t in threads:
-            t.start()
-        for t in threads:
-            t.join()
+                    records.append({"id": r.get("id"), "arrival_s": t_arrive - t0, "nrhs": r["nrhs"],
+                                    "estimate_bytes": est, "status": "rejected",
+                                    "done_s": time.perf_counter() - t0})
+                continue
+            th = threading.Thread(target=serve, args=(r, t_arrive, est, self.stream_factory()))
+            th.start()
+            running.append(th)
+        for th in running:
+            th.join()
         return records, summarize(records, self.admission)
 
 

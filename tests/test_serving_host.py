@@ -30,7 +30,7 @@ def _req(i, t, n_tri, nrhs=1):
 def test_budget_limits_concurrency_and_keeps_arrival_order():
     log, lock = [], threading.Lock()
     one = serving.estimate_bytes(3 * 1000, 1, 30)
-    eng = serving.ServingEngine(executor=_fake_executor(log, lock), workers=4, budget_bytes=2 * one + 1,
+    eng = serving.ServingEngine(executor=_fake_executor(log, lock), max_inflight=4, budget_bytes=2 * one + 1,
                                 restart=30, stream_factory=lambda: None)
     reqs = [_req(i, 0.001 * i, 1000) for i in range(8)]
     recs, summ = eng.run(reqs)
@@ -47,9 +47,25 @@ def test_budget_limits_concurrency_and_keeps_arrival_order():
         assert r["latency_s"] >= r["solve_s"] - 1e-3 and r["wait_s"] >= 0
 
 
+def test_memory_not_a_worker_count_bounds_concurrency():
+    """64 slots, a budget of six requests: six run at once, then each finished request lets the
+    next one in (admission follows memory, not a fixed pool of workers)."""
+    log, lock = [], threading.Lock()
+    one = serving.estimate_bytes(3 * 1000, 1, 30)
+    eng = serving.ServingEngine(executor=_fake_executor(log, lock, 0.1), max_inflight=64, budget_bytes=6 * one,
+                                restart=30, stream_factory=lambda: None)
+    recs, summ = eng.run([_req(i, 0.0, 1000) for i in range(12)])
+    live, peak = 0, 0
+    for kind, _, _ in sorted(log, key=lambda e: e[2]):
+        live += 1 if kind == "start" else -1
+        peak = max(peak, live)
+    assert summ["ok"] == 12 and peak == 6
+    assert summ["makespan_s"] < 0.35  # two waves of 0.1 s, not twelve
+
+
 def test_oversized_request_is_rejected_and_others_served():
     log, lock = [], threading.Lock()
-    eng = serving.ServingEngine(executor=_fake_executor(log, lock, 0.01), workers=2,
+    eng = serving.ServingEngine(executor=_fake_executor(log, lock, 0.01), max_inflight=2,
                                 budget_bytes=serving.estimate_bytes(3 * 2000, 1, 30), restart=30,
                                 stream_factory=lambda: None)
     reqs = [_req(0, 0.0, 1000), _req(1, 0.001, 10 ** 6, nrhs=16), _req(2, 0.002, 1000)]
@@ -61,7 +77,7 @@ def test_oversized_request_is_rejected_and_others_served():
 def test_latency_includes_waiting_for_the_budget():
     log, lock = [], threading.Lock()
     one = serving.estimate_bytes(3 * 1000, 1, 30)
-    eng = serving.ServingEngine(executor=_fake_executor(log, lock, 0.1), workers=2, budget_bytes=one,
+    eng = serving.ServingEngine(executor=_fake_executor(log, lock, 0.1), max_inflight=2, budget_bytes=one,
                                 restart=30, stream_factory=lambda: None)
     recs, summ = eng.run([_req(0, 0.0, 1000), _req(1, 0.0, 1000)])
     second = max(recs, key=lambda r: r["done_s"])
