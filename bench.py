@@ -381,6 +381,9 @@ def run_batched(args):
         cfg["adaptive"] = 1
     if args.leaf_max > 0:
         cfg["leaf_max"] = args.leaf_max
+    for key in ("p2p_kernel", "m2l_kernel", "overlap", "tc_group", "autotune"):
+        if getattr(args, key) is not None:
+            cfg[key] = getattr(args, key)
     V, F = synthetic.workload_mesh(mesh)
     N, R = 3 * F.shape[0], args.nrhs
     stream = torch.cuda.current_stream()
@@ -490,6 +493,7 @@ def run_batched(args):
             "config": {"workload": f"{args.workload}: {synthetic.WORKLOADS[mesh][0]}, {R} plane-wave right-hand "
                                    "sides (seeded Fibonacci directions) per batched matvec",
                        "N": N, "k": k, "nrhs": R, "orders": info["orders"], "graph": "one captured CUDA graph per step",
+                       "kernels": plan.tuning(), "autotune": plan.cfg.autotune,
                        "m2l": "FP32 SIMT" if args.simt else "tcgen05 BF16x3 (levels with (p+1)^2 <= 64), FP32 SIMT above",
                        "l2": "inputs larger than L2 (batched expansions alone exceed it)"},
             "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99)),
@@ -665,6 +669,11 @@ def main():
                  "p50_ms": 1e3 * float(np.percentile(lat, 50)), "p99_ms": 1e3 * float(np.percentile(lat, 99)),
                  "iterations": its[-1], "true_relres": rrs[-1], "restart": restart, "tol": 1e-4,
                  "status": "converged" if stt == 0 else "not converged", "rhs": "plane wave along +z"}
+        # everything but the matvecs (one per iteration and one true residual per restart cycle),
+        # per Arnoldi step: orthogonalisation, norms, Hessenberg bookkeeping, launches, the
+        # per-iteration 16-byte read of the residual estimate
+        n_mv = its[-1] + -(-its[-1] // restart)
+        solve["arnoldi_ms_per_step"] = (solve["ms_per_solve"] - n_mv * total_ms / args.steps) / max(its[-1], 1)
 
     # ------------------------------------------------------------ the plain single-RHS FP32 form
     # (M2L on FP32 SIMT at every level), same workload, same CUDA-event timing on the same stream

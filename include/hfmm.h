@@ -96,10 +96,9 @@ typedef struct {
                            applies the 56 canonical operators of the offsets' reflection classes,
                            writing each local once); -1 default/tuned (-1) */
     int tc_group;       /* work items per tensor-core block: 8, 16 or 32; 0 default/tuned (0) */
-    int overlap;        /* single right-hand-side matvec on a uniform tree: 1 near field and
-                           correction on a second branch beside the far field, the whole matvec
-                           captured once as a CUDA graph and replayed; 0 one stage after another;
-                           -1 default/tuned (-1) */
+    int overlap;        /* single right-hand-side matvec on a uniform tree, captured once as a
+                           CUDA graph and replayed: 1 near field and correction on a second branch
+                           beside the far field; 0 one stage after another; -1 default/tuned (-1) */
     int precision;      /* 1: the plan also keeps an FP64 near field and correction: FP64 positions
                            and weights, correction integrals with FP64 quadrature nodes kept in
                            FP64, used by hfmm_matvec_df and by the outer residual of
@@ -121,7 +120,10 @@ int hfmm_plan_create(const hfmm_config* cfg, const double* vertices, int64_t n_v
                      const int32_t* tris, int64_t n_tri, double k_re, double k_im,
                      void* stream, hfmm_plan** out);
 
-void hfmm_plan_destroy(hfmm_plan* plan); /* NULL is a no-op */
+/* Releases the plan's device memory.  The caller must have completed (or synchronised) the work
+ * it issued with this plan on its own streams; the plan's internal streams are synchronised
+ * here, not the whole device.  NULL is a no-op. */
+void hfmm_plan_destroy(hfmm_plan* plan);
 
 int64_t hfmm_num_points(const hfmm_plan* plan); /* N = 3 * n_tri, or -1 for NULL */
 

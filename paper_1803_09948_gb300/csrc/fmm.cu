@@ -12,6 +12,8 @@
 #include <cmath>
 #include <type_traits>
 
+#include <mutex>
+
 #include "hfmm_internal.cuh"
 #include "kernel_poly.h"
 
@@ -1517,41 +1519,72 @@ static void matvec_branches(hfmm_plan* P, cudaStream_t st, cudaStream_t side) {
     l2p_stage(P, 7, st);
 }
 
+// Captures fn's launches on `cap` (thread-local mode) into an instantiated graph.  Another
+// thread of the process can invalidate a capture in progress (a device-wide synchronisation,
+// as a memory release performs, while this thread is capturing); the capture is then
+// abandoned, the error cleared, and false returned so the caller runs the work directly.
+// Errors that are not about the capture propagate as usual.
+template <typename Fn>
+static bool capture_graph(cudaStream_t cap, Fn fn, cudaGraphExec_t* out) {
+    cudaGraph_t g = nullptr;
+    HFMM_CUDA(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
+    bool ok = true;
+    try {
+        fn();
+    } catch (const HfmmError&) {
+        ok = false;
+    }
+    const cudaError_t ee = cudaStreamEndCapture(cap, &g);
+    if (!ok || ee != cudaSuccess || !g) {
+        if (g) cudaGraphDestroy(g);
+        const cudaError_t last = cudaGetLastError();  // clears a non-sticky capture error
+        const bool capture_err = ee == cudaErrorStreamCaptureInvalidated || last == cudaErrorStreamCaptureInvalidated ||
+                                 ee == cudaErrorStreamCaptureUnsupported || last == cudaErrorStreamCaptureUnsupported;
+        if (!capture_err && last != cudaSuccess) HFMM_CUDA(last);
+        if (!capture_err && ee != cudaSuccess) HFMM_CUDA(ee);
+        return false;
+    }
+    const cudaError_t e = cudaGraphInstantiate(out, g, 0);
+    cudaGraphDestroy(g);
+    HFMM_CUDA(e);
+    return true;
+}
+
 // sig (sorted, pre-scaled densities) -> phi (sorted potentials) for the whole operator.
-// With mv_mode 1 (uniform trees) the two-branch form is captured once per plan into a CUDA
-// graph on a plan-owned stream and replayed on `st`: it reads and writes only plan-owned
-// buffers, so one capture serves every later matvec, including the solver's.
+// On uniform trees the matvec (the two-branch form for mv_mode 1, the chain of stages for
+// mv_mode 0) is captured once per plan into a CUDA graph on a plan-owned stream and replayed
+// on `st`: it reads and writes only plan-owned buffers, so one capture serves every later
+// matvec, including the solver's.
 void run_matvec_sorted(hfmm_plan* P, int parts, cudaStream_t st) {
-    if (parts != 7 || P->stage_ev || P->mv_mode == 0 || P->adaptive) {
+    if (parts != 7 || P->stage_ev || P->adaptive) {
         matvec_sequential(P, parts, st);
         return;
     }
+    // the whole matvec as one graph launch (two branches, or one chain): GMRES waits on the host
+    // once per iteration, after which a chain of separate launches would leave the device idle
+    // between the short tree-pass kernels while the host catches up
     MatvecGraph& G = P->mvg;
-    if (!G.graph) {
+    const bool br = P->mv_mode == 1;
+    cudaGraphExec_t& gx = br ? G.graph : G.seq;
+    int64_t& gl = br ? G.launches : G.seq_launches;
+    if (!gx) {
         if (!G.cap) HFMM_CUDA(cudaStreamCreateWithFlags(&G.cap, cudaStreamNonBlocking));
         if (!G.side) HFMM_CUDA(cudaStreamCreateWithFlags(&G.side, cudaStreamNonBlocking));
         if (!G.fork) HFMM_CUDA(cudaEventCreateWithFlags(&G.fork, cudaEventDisableTiming));
         if (!G.join) HFMM_CUDA(cudaEventCreateWithFlags(&G.join, cudaEventDisableTiming));
         const int64_t l0 = P->launches;
-        cudaGraph_t g = nullptr;
-        HFMM_CUDA(cudaStreamBeginCapture(G.cap, cudaStreamCaptureModeThreadLocal));
-        try {
-            matvec_branches(P, G.cap, G.side);
-        } catch (...) {
-            cudaStreamEndCapture(G.cap, &g);
-            if (g) cudaGraphDestroy(g);
-            P->launches = l0;
-            throw;
+        const bool ok = br ? capture_graph(G.cap, [&] { matvec_branches(P, G.cap, G.side); }, &gx)
+                           : capture_graph(G.cap, [&] { matvec_sequential(P, 7, G.cap); }, &gx);
+        if (!ok) {
+            P->launches = l0;  // the capture was invalidated (see capture_graph): run the stages directly
+            matvec_sequential(P, parts, st);
+            return;
         }
-        HFMM_CUDA(cudaStreamEndCapture(G.cap, &g));
-        const cudaError_t e = cudaGraphInstantiate(&G.graph, g, 0);
-        cudaGraphDestroy(g);
-        HFMM_CUDA(e);
-        G.launches = P->launches - l0;
+        gl = P->launches - l0;
         P->launches = l0;
     }
-    HFMM_CUDA(cudaGraphLaunch(G.graph, st));
-    P->launches += G.launches;
+    HFMM_CUDA(cudaGraphLaunch(gx, st));
+    P->launches += gl;
 }
 
 void run_direct_sorted(hfmm_plan* P, cudaStream_t st) {
@@ -1939,6 +1972,35 @@ bool batch_supported(const hfmm_plan* P, int R) {
     return P->p2p_cap > 0 && p2p_b_smem(P->p2p_cap) <= 200 * 1024;
 }
 
+// Once per device: the batched kernels may take up to the device's opt-in shared memory per
+// block (each launch asks for what its plan needs).  A function's limit is process-wide, so a
+// per-plan value would let a plan with a smaller neighbourhood lower it under another plan's
+// launch on another thread.
+static void batch_kernels_init() {
+    static std::mutex mu;
+    static bool done[64] = {};
+    int dev = 0;
+    HFMM_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lock(mu);
+    if (dev >= 0 && dev < 64 && done[dev]) return;
+    int optin = 0;
+    HFMM_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    auto allow = [&](const void* fn) {
+        cudaFuncAttributes fa{};
+        HFMM_CUDA(cudaFuncGetAttributes(&fa, fn));
+        HFMM_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes));
+    };
+    allow((const void*)k_p2p_b<true>);
+    allow((const void*)k_p2p_b<false>);
+    allow((const void*)k_p2m_b<-1>);
+    for (int p = 0; p <= 9; ++p)
+        with_leaf_order(p, [&](auto pp) {
+            constexpr int PP = decltype(pp)::value;
+            allow((const void*)k_l2p_b<PP>);
+        });
+    if (dev >= 0 && dev < 64) done[dev] = true;
+}
+
 void batch_setup(hfmm_plan* P, int R, cudaStream_t st) {
     BatchState& B = P->batch;
     if (B.R == R && B.sig.p) return;
@@ -2058,18 +2120,7 @@ void batch_setup(hfmm_plan* P, int R, cudaStream_t st) {
     P->dev_bytes += cnt;
     // shared-memory limits above 48 KiB, set before any capture
     m2l_tc_init();
-    const size_t sp2p = p2p_b_smem(P->p2p_cap);
-    HFMM_CUDA(cudaFuncSetAttribute(k_p2p_b<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sp2p));
-    HFMM_CUDA(cudaFuncSetAttribute(k_p2p_b<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sp2p));
-    if (L >= 2) {
-        const int Pl = P->lev[L].P;
-        // P2M keeps the any-order basis: with the unrolled one its registers halve the blocks per SM
-        HFMM_CUDA(cudaFuncSetAttribute(k_p2m_b<-1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p2m_b_smem(Pl)));
-        with_leaf_order(P->lev[L].p, [&](auto pp) {
-            constexpr int PP = decltype(pp)::value;
-            HFMM_CUDA(cudaFuncSetAttribute(k_l2p_b<PP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)l2p_b_smem(Pl)));
-        });
-    }
+    batch_kernels_init();
 }
 
 void run_matvec_batched(hfmm_plan* P, const float2* density, float2* potential, cudaStream_t st) {
@@ -2151,20 +2202,11 @@ void batched_matvec(hfmm_plan* P, const float2* d, float2* o, int R, cudaStream_
             B.graph = nullptr;
         }
         const int64_t l0 = P->launches;
-        cudaGraph_t g = nullptr;
-        HFMM_CUDA(cudaStreamBeginCapture(B.cap_stream, cudaStreamCaptureModeThreadLocal));
-        try {
-            run_matvec_batched(P, d, o, B.cap_stream);
-        } catch (...) {
-            cudaStreamEndCapture(B.cap_stream, &g);
-            if (g) cudaGraphDestroy(g);
-            P->launches = l0;
-            throw;
+        if (!capture_graph(B.cap_stream, [&] { run_matvec_batched(P, d, o, B.cap_stream); }, &B.graph)) {
+            P->launches = l0;  // the capture was invalidated (see capture_graph): run the matvec directly
+            run_matvec_batched(P, d, o, st);
+            return;
         }
-        HFMM_CUDA(cudaStreamEndCapture(B.cap_stream, &g));
-        const cudaError_t e = cudaGraphInstantiate(&B.graph, g, 0);
-        cudaGraphDestroy(g);
-        HFMM_CUDA(e);
         B.g_launches = P->launches - l0;
         P->launches = l0;
         B.g_in = d;

@@ -133,15 +133,24 @@ __device__ __forceinline__ double2 block_sum2(double2 v, double2* sh) {
 }
 
 // partial[i * RG + blk] = sum over the block's rows of conj(V_i) w, for the kDotVecs vectors
-// i = blockIdx.y * kDotVecs + c (< nvec); grid RG x ceil(nvec / kDotVecs)
+// i = blockIdx.y * kDotVecs + c (< nvec); grid RG x ceil(nvec / kDotVecs).  with_norm: the
+// blocks of y = 0 also leave |w|^2 in partial[nvec * RG + blk].  skip (may be NULL): when *skip
+// is set the pass is not needed and the kernel returns at once.
 __global__ void __launch_bounds__(RB) k_dots_df(int64_t N, const float4* __restrict__ V, int nvec,
-                                                const float4* __restrict__ w, double2* __restrict__ partial) {
+                                                const float4* __restrict__ w, double2* __restrict__ partial,
+                                                const int* __restrict__ skip, int with_norm) {
+    if (skip && *skip) return;
     __shared__ double2 sh[RB / 32];
     const int i0 = blockIdx.y * kDotVecs;
     const int nv = min(kDotVecs, nvec - i0);
-    Acc re[kDotVecs], im[kDotVecs];
+    const bool nrm = with_norm && blockIdx.y == 0;
+    Acc re[kDotVecs], im[kDotVecs], wn;
     for (int64_t r = (int64_t)blockIdx.x * RB + threadIdx.x; r < N; r += (int64_t)RG * RB) {
         const float4 b = w[r];
+        if (nrm) {
+            wn.add_prod(b.x, b.z, b.x, b.z);
+            wn.add_prod(b.y, b.w, b.y, b.w);
+        }
 #pragma unroll
         for (int c = 0; c < kDotVecs; ++c) {
             if (c >= nv) break;
@@ -158,6 +167,10 @@ __global__ void __launch_bounds__(RB) k_dots_df(int64_t N, const float4* __restr
         if (c >= nv) break;  // uniform over the block
         const double2 s = block_sum2(make_double2(re[c].value(), im[c].value()), sh);
         if (threadIdx.x == 0) partial[(int64_t)(i0 + c) * RG + blockIdx.x] = s;
+    }
+    if (nrm) {  // uniform over the block
+        const double2 s = block_sum2(make_double2(wn.value(), 0.0), sh);
+        if (threadIdx.x == 0) partial[(int64_t)nvec * RG + blockIdx.x] = s;
     }
 }
 
@@ -190,7 +203,8 @@ __global__ void __launch_bounds__(RB) k_reduce(const double2* __restrict__ parti
 
 // x += sign * sum_i h_i V_i, with h given as double-float pairs hdf[i] = (re_hi, im_hi, re_lo, im_lo)
 __global__ void k_axpy_df(int64_t N, const float4* __restrict__ V, int nvec, const float4* __restrict__ hdf,
-                          float sign, float4* __restrict__ x) {
+                          float sign, float4* __restrict__ x, const int* __restrict__ skip = nullptr) {
+    if (skip && *skip) return;
     extern __shared__ float4 hs[];
     for (int q = threadIdx.x; q < nvec; q += blockDim.x) hs[q] = hdf[q];
     __syncthreads();
@@ -227,7 +241,8 @@ __device__ __forceinline__ float4 to_df4(double2 v) {
 // block i: h_i = sum of its RG partials; coeff[i] = h_i as double-float (the update
 // w -= V h); hsum[i] += h_i (the Hessenberg column, summed over the two passes)
 __global__ void __launch_bounds__(RB) k_reduce_h(const double2* __restrict__ partial, float4* __restrict__ coeff,
-                                                 double2* __restrict__ hsum) {
+                                                 double2* __restrict__ hsum, const int* __restrict__ skip) {
+    if (skip && *skip) return;
     __shared__ double2 sh[RB / 32];
     double2 acc = make_double2(0, 0);
     for (int b = threadIdx.x; b < RG; b += RB) {
@@ -241,6 +256,20 @@ __global__ void __launch_bounds__(RB) k_reduce_h(const double2* __restrict__ par
         hsum[blockIdx.x].x += s.x;
         hsum[blockIdx.x].y += s.y;
     }
+}
+
+// Whether the second Gram-Schmidt pass is needed (the criterion of Daniel, Gragg, Kaufman and
+// Stewart): after the first pass |w'|^2 = |w|^2 - sum |h_i|^2 (Pythagoras, FP64); if it kept at
+// least half of |w|^2 (|w'| >= |w| / sqrt 2) the first pass lost no significant digits and
+// *skip = 1, else the pass runs.  wpart: the RG partials of |w|^2 before the pass.
+__global__ void __launch_bounds__(RB) k_reorth_decide(const double2* __restrict__ wpart, const double2* __restrict__ h,
+                                                      int nvec, int* __restrict__ skip) {
+    __shared__ double2 sh[RB / 32];
+    double2 acc = make_double2(0, 0);
+    for (int b = threadIdx.x; b < RG; b += RB) acc.x += wpart[b].x;
+    for (int i = threadIdx.x; i < nvec; i += RB) acc.y += h[i].x * h[i].x + h[i].y * h[i].y;
+    const double2 s = block_sum2(acc, sh);
+    if (threadIdx.x == 0) *skip = (s.x - s.y >= 0.5 * s.x) ? 1 : 0;
 }
 
 // one block: nrm = sqrt(sum of the RG partials of |w|^2); hsum[j1] = nrm (when j1 >= 0);
@@ -386,7 +415,7 @@ int run_gmres(hfmm_plan* P, const void* rhs, void* x_out, int* iters, double* re
     // norm, scale
     const size_t n_part = 2 * (size_t)RG * (m + 2), n_hsum = 2 * (size_t)(m + 2), n_H = 2 * (size_t)(m + 1) * m,
                  n_cs = 2 * (size_t)m, n_g = 2 * (size_t)(m + 1), n_y = 2 * (size_t)m, n_coef = 2 * (size_t)(m + 2);
-    const size_t n_ws = n_part + n_hsum + n_H + 2 * n_cs + n_g + n_y + n_coef + 4;
+    const size_t n_ws = n_part + n_hsum + n_H + 2 * n_cs + n_g + n_y + n_coef + 6;
     if (P->kry_m != m) {
         P->kry.alloc((size_t)(m + 1) * N, nullptr);
         P->gw.alloc(N, nullptr);
@@ -409,6 +438,7 @@ int run_gmres(hfmm_plan* P, const void* rhs, void* x_out, int* iters, double* re
     A.res = tail;             // 2 doubles
     double* nrm = tail + 2;   // 1 double
     float2* scale = (float2*)(tail + 3);
+    int* skip2 = (int*)(tail + 4);  // second Gram-Schmidt pass not needed
     Ctx c{P, st, N, (unsigned)((N + 255) / 256), partial, hsum, coeff};
     float4* V = P->kry.p;
     auto launch_norm = [&](const float4* w, int j1) {  // nrm, scale = 1 / nrm, hsum[j1] = nrm
@@ -416,10 +446,17 @@ int run_gmres(hfmm_plan* P, const void* rhs, void* x_out, int* iters, double* re
         k_norm_finish<<<1, RB, 0, st>>>(partial, j1, hsum, scale, nrm);
         c.count(2);
     };
-    auto cgs_pass = [&](int nvec, float4* w) {  // h = V^H w; w -= V h; hsum += h
-        k_dots_df<<<dim3(RG, (nvec + kDotVecs - 1) / kDotVecs), RB, 0, st>>>(N, V, nvec, w, partial);
-        k_reduce_h<<<nvec, RB, 0, st>>>(partial, coeff, hsum);
-        k_axpy_df<<<c.nb, 256, sizeof(float4) * nvec, st>>>(N, V, nvec, coeff, -1.f, w);
+    // h = V^H w; w -= V h; hsum += h.  The first pass also takes |w|^2 and decides whether the
+    // second pass runs (its kernels return at once when it does not).
+    auto cgs_pass = [&](int nvec, float4* w, bool first) {
+        k_dots_df<<<dim3(RG, (nvec + kDotVecs - 1) / kDotVecs), RB, 0, st>>>(N, V, nvec, w, partial,
+                                                                              first ? nullptr : skip2, first);
+        k_reduce_h<<<nvec, RB, 0, st>>>(partial, coeff, hsum, first ? nullptr : skip2);
+        if (first) {
+            k_reorth_decide<<<1, RB, 0, st>>>(partial + (size_t)nvec * RG, hsum, nvec, skip2);
+            c.count();
+        }
+        k_axpy_df<<<c.nb, 256, sizeof(float4) * nvec, st>>>(N, V, nvec, coeff, -1.f, w, first ? nullptr : skip2);
         c.count(3);
     };
     k_c64_to_df<<<c.nb, 256, 0, st>>>(N, (const float2*)rhs, P->gb.p);
@@ -450,8 +487,8 @@ int run_gmres(hfmm_plan* P, const void* rhs, void* x_out, int* iters, double* re
             float4* w = P->gw.p;
             c.matvec(V + (int64_t)j * N, w);
             HFMM_CUDA(cudaMemsetAsync(hsum, 0, sizeof(double2) * (j + 2), st));
-            cgs_pass(j + 1, w);  // classical Gram-Schmidt, twice
-            cgs_pass(j + 1, w);
+            cgs_pass(j + 1, w, true);  // classical Gram-Schmidt, repeated when the first pass cancelled
+            cgs_pass(j + 1, w, false);
             launch_norm(w, j + 1);
             k_scale_df_dev<<<c.nb, 256, 0, st>>>(N, w, scale, V + (int64_t)(j + 1) * N);
             k_givens<<<1, 32, 0, st>>>(j, m, hsum, A, bnorm);

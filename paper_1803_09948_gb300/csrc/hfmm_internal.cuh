@@ -166,15 +166,19 @@ struct BatchState {
 };
 
 // The single right-hand-side matvec (sorted densities -> sorted potentials) captured as a
-// CUDA graph with the near field on a side branch (see run_matvec_sorted).
+// CUDA graph: with the near field on a side branch (overlap = 1), or its stages one after
+// another (overlap = 0); see run_matvec_sorted.
 struct MatvecGraph {
     cudaStream_t cap = nullptr, side = nullptr;  // capture stream and the near-field branch
     cudaEvent_t fork = nullptr, join = nullptr;
-    cudaGraphExec_t graph = nullptr;
-    int64_t launches = 0;  // kernels in one replay
+    cudaGraphExec_t graph = nullptr;      // two branches
+    cudaGraphExec_t seq = nullptr;        // one chain
+    int64_t launches = 0, seq_launches = 0;  // kernels in one replay
     void reset() {
         if (graph) cudaGraphExecDestroy(graph);
+        if (seq) cudaGraphExecDestroy(seq);
         graph = nullptr;
+        seq = nullptr;
     }
     ~MatvecGraph() {
         reset();

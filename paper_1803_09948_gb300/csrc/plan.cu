@@ -1205,7 +1205,12 @@ int hfmm_plan_create(const hfmm_config* cfg, const double* vertices, int64_t n_v
 
 void hfmm_plan_destroy(hfmm_plan* P) {
     if (!P) return;
-    cudaDeviceSynchronize();
+    // the plan's own streams (graph replays launch on the caller's streams, which the caller has
+    // finished with before releasing the plan); no device-wide wait, so that other plans'
+    // work in flight, or a graph capture on another thread, is not held up or invalidated
+    if (P->mvg.cap) cudaStreamSynchronize(P->mvg.cap);
+    if (P->mvg.side) cudaStreamSynchronize(P->mvg.side);
+    if (P->batch.cap_stream) cudaStreamSynchronize(P->batch.cap_stream);
     delete P;
 }
 

@@ -117,7 +117,8 @@ def gpu_executor(restart: int = 30, tol: float = 1e-4, keep_solution: bool = Fal
         with torch.cuda.stream(stream):
             plan = Plan(req["V"], req["F"], req["k"], stream=stream, restart=restart, tol=tol, max_iter=max_iter)
             try:
-                torch.cuda.synchronize()  # plan ready (its build is part of the request's time)
+                stream.synchronize()  # plan ready (its build is part of the request's time); only this
+                # request's stream: a device-wide wait would stall every other request in flight
                 t1 = time.perf_counter()
                 R, N = req["nrhs"], plan.n
                 b = torch.empty(R * N, dtype=torch.complex64, device="cuda")
