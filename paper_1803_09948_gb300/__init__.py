@@ -296,7 +296,7 @@ def hfmm_plan_costs(plan):
     return dict(zip(keys, [float(v) for v in c]))
 
 
-TUNABLES = [("p2p_kernel", [0, 1]), ("m2l_kernel", [0, 1]), ("tc_group", [8, 16, 32]), ("overlap", [0, 1])]
+TUNABLES = [("p2p_kernel", [0, 1, 2]), ("m2l_kernel", [0, 1]), ("tc_group", [8, 16, 32]), ("overlap", [0, 1])]
 
 
 def hfmm_plan_tuning(plan):

@@ -427,6 +427,143 @@ __global__ void __launch_bounds__(kPkThreads) k_p2p_packed(const int32_t* __rest
     }
 }
 
+// ------------------------------------------------------------------ pipelined near field
+// The packed kernel's arithmetic in persistent blocks that walk leaves b, b + grid, ...: while
+// a block evaluates one leaf, the next leaf's sources travel from global to shared memory with
+// cp.async (raw, as stored), so the global loads no longer sit in front of a block barrier;
+// after the evaluation they are shifted into the leaf's frame and laid out in pairs from shared
+// memory.  Same pairs, the same per-pair arithmetic and the same j != i rule as k_p2p_packed.
+constexpr int kPipeBlocksPerSM = 8;
+
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+                 "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* dst, const void* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+                 "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+__global__ void __launch_bounds__(kPkThreads) k_p2p_pipe(int nleaf, const int32_t* __restrict__ leaf_start,
+                                                         const int4* __restrict__ leaf_ijk,
+                                                         const int32_t* __restrict__ nbr_ptr,
+                                                         const int32_t* __restrict__ nbr,
+                                                         const float4* __restrict__ pts,
+                                                         const float2* __restrict__ sig, float shift, int cap_pairs,
+                                                         float2* __restrict__ phi) {
+    extern __shared__ float4 sq[];                                  // [2 cap_pairs] pairs (packed layout)
+    float4* rawp = sq + 2 * cap_pairs;                              // [2 cap_pairs] next leaf's positions
+    float2* sim = reinterpret_cast<float2*>(rawp + 2 * cap_pairs);  // [cap_pairs]
+    float2* raws = sim + cap_pairs;                                 // [2 cap_pairs] next leaf's densities
+    __shared__ NbrTable TT[2];
+    __shared__ float2 s_red[kPkThreads];
+    const int tid = threadIdx.x;
+    float* sf = reinterpret_cast<float*>(sq);
+    float* sfi = reinterpret_cast<float*>(sim);
+    auto issue = [&](const NbrTable& T) {  // raw copies of the neighbourhood, padding slots left out
+        const int total = T.off[T.nl];
+        for (int p = tid; p < total; p += kPkThreads) {
+            const int q = nbr_segment(T, p);
+            const int e = p - T.off[q];
+            if (e < T.cnt[q]) {
+                cp_async16(rawp + p, pts + T.j0[q] + e);
+                cp_async8(raws + p, sig + T.j0[q] + e);
+            }
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+    auto pack = [&](const NbrTable& T) {  // raw -> shifted pairs (padding: far away, zero density)
+        const int total = T.off[T.nl];
+        for (int p = tid; p < total; p += kPkThreads) {
+            const int q = nbr_segment(T, p);
+            const int e = p - T.off[q];
+            float x = kPkPad, y = kPkPad, z = kPkPad, sr = 0.f, si = 0.f;
+            if (e < T.cnt[q]) {
+                const float4 pt = rawp[p];
+                const float2 g = raws[p];
+                const float4 o = T.sh[q];
+                x = pt.x + o.x;
+                y = pt.y + o.y;
+                z = pt.z + o.z;
+                sr = g.x;
+                si = g.y;
+            }
+            const int pq = p >> 1, h = p & 1;
+            float* r = sf + 8 * pq;
+            r[h] = x;
+            r[2 + h] = y;
+            r[4 + h] = z;
+            r[6 + h] = sr;
+            sfi[2 * pq + h] = si;
+        }
+    };
+    int b = blockIdx.x;
+    if (b >= nleaf) return;  // uniform over the block
+    int cur = 0;
+    if (tid < 32) build_nbr_table(b, leaf_start, leaf_ijk, nbr_ptr, nbr, shift, true, TT[0]);
+    __syncthreads();
+    issue(TT[0]);
+    cp_async_wait_all();
+    __syncthreads();
+    pack(TT[0]);
+    __syncthreads();
+    for (; b < nleaf; b += gridDim.x) {
+        const int bn = b + gridDim.x;
+        const bool more = bn < nleaf;  // uniform over the block
+        if (more) {
+            if (tid < 32) build_nbr_table(bn, leaf_start, leaf_ijk, nbr_ptr, nbr, shift, true, TT[cur ^ 1]);
+            __syncthreads();
+            issue(TT[cur ^ 1]);
+        }
+        const NbrTable& T = TT[cur];
+        const int npair = T.off[T.nl] >> 1;
+        const int nself = T.cnt[0];
+        const int qself = T.off[1] >> 1;
+        const int TTn = min(nself, kPkThreads);
+        const int S = kPkThreads / max(TTn, 1);
+        const int slot = tid % max(TTn, 1), sp = tid / max(TTn, 1);
+        const int i0 = __ldg(leaf_start + b);
+        for (int t0 = 0; t0 < nself; t0 += TTn) {
+            const int it = t0 + slot;
+            float ar = 0.f, ai = 0.f;
+            if (sp < S && it < nself) {
+                const float* tr = sf + 8 * (it >> 1) + (it & 1);
+                const float2 ntx = f2(-tr[0]), nty = f2(-tr[2]), ntz = f2(-tr[4]);
+                float2 A = f2(0.f), B = f2(0.f), C = f2(0.f), D = f2(0.f);
+                int q = sp;
+                for (; q < qself; q += S)
+                    pk_pair<true>(sq[2 * q], sq[2 * q + 1], sim[q], ntx, nty, ntz, 2 * q - it, A, B, C, D);
+#pragma unroll 2
+                for (; q < npair; q += S) pk_pair<false>(sq[2 * q], sq[2 * q + 1], sim[q], ntx, nty, ntz, 0, A, B, C, D);
+                ar = (A.x + A.y) - (B.x + B.y);
+                ai = (C.x + C.y) + (D.x + D.y);
+            }
+            s_red[tid] = make_float2(ar, ai);
+            __syncthreads();
+            if (sp == 0 && it < nself) {
+                float2 acc = s_red[slot];
+                for (int r = 1; r < S; ++r) {
+                    const float2 v = s_red[slot + r * TTn];
+                    acc.x += v.x;
+                    acc.y += v.y;
+                }
+                phi[i0 + it] = acc;
+            }
+            __syncthreads();
+        }
+        if (more) {
+            cp_async_wait_all();  // this thread's copies of the next leaf
+            __syncthreads();      // everyone's, and the pairs of this leaf are no longer read
+            pack(TT[cur ^ 1]);
+            __syncthreads();
+            cur ^= 1;
+        }
+    }
+}
+
 // ============================================================== FP32 special functions
 // out[n] = j_n(x) / s^n, n = 0..p
 // Reciprocals for the small-argument series of j_n (uploaded with the Legendre tables):
@@ -1331,6 +1468,15 @@ static void launch_translate(hfmm_plan* P, const TransItem* items, float2* coef,
 }
 
 // Near field (P2P between neighbouring leaves, or zeros): the first writer of P->phi.
+static int p2p_sm_count() {
+    static int n[64] = {};
+    int dev = 0;
+    HFMM_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) dev = 0;
+    if (!n[dev]) HFMM_CUDA(cudaDeviceGetAttribute(&n[dev], cudaDevAttrMultiProcessorCount, dev));
+    return n[dev];
+}
+
 static void near_stage(hfmm_plan* P, int parts, cudaStream_t st) {
     int64_t N = P->N;
     mark_stage(P, 1, st);
@@ -1339,7 +1485,12 @@ static void near_stage(hfmm_plan* P, int parts, cudaStream_t st) {
         if (P->p2p_cap > 0 && staged <= 96 * 1024 && P->p2p_maxnbr <= kStagedNbr) {
             const int cap_pairs = P->p2p_cap / 2 + 2;
             const size_t pk_smem = (size_t)cap_pairs * (2 * sizeof(float4) + sizeof(float2));
-            if (P->poly_p2p && P->p2p_variant == 1) {
+            if (P->poly_p2p && P->p2p_variant == 2) {
+                const int grid = (int)std::min<int64_t>(P->nleaf, (int64_t)kPipeBlocksPerSM * p2p_sm_count());
+                k_p2p_pipe<<<(unsigned)grid, kPkThreads, (size_t)cap_pairs * (4 * sizeof(float4) + 3 * sizeof(float2)),
+                             st>>>((int)P->nleaf, P->leaf_start.p, P->leaf_ijk.p, P->nbr_ptr.p, P->nbr.p, P->pts.p,
+                                   P->sig.p, P->p2p_shift, cap_pairs, P->phi.p);
+            } else if (P->poly_p2p && P->p2p_variant == 1) {
                 k_p2p_packed<<<(unsigned)P->nleaf, kPkThreads, pk_smem, st>>>(
                     P->leaf_start.p, P->leaf_ijk.p, P->nbr_ptr.p, P->nbr.p, P->pts.p, P->sig.p, P->p2p_shift,
                     cap_pairs, P->phi.p);
@@ -1493,6 +1644,7 @@ void matvec_kernels_init() {
     allow((const void*)k_p2p_staged<true>);
     allow((const void*)k_p2p_staged<false>);
     allow((const void*)k_p2p_packed);
+    allow((const void*)k_p2p_pipe);
     allow((const void*)k_p2m);
     if (dev >= 0 && dev < 64) done[dev] = true;
 }

@@ -28,6 +28,15 @@ namespace hfmm {
 
 using cd = std::complex<double>;
 
+// The host waits for `st` through a blocking-sync event: the thread sleeps instead of spinning,
+// so that many solves in flight (one host thread each, as in serving) leave the host cores to
+// the plan builds and launches beside them.
+static void host_wait(hfmm_plan* P, cudaStream_t st) {
+    if (!P->host_ev) HFMM_CUDA(cudaEventCreateWithFlags(&P->host_ev, cudaEventBlockingSync | cudaEventDisableTiming));
+    HFMM_CUDA(cudaEventRecord(P->host_ev, st));
+    HFMM_CUDA(cudaEventSynchronize(P->host_ev));
+}
+
 static constexpr int RB = 256;  // threads per reduction block
 static constexpr int RG = 296;  // reduction blocks per vector (2 per SM)
 static constexpr int kDotVecs = 8;  // basis vectors per inner-product block (w is read once per 8)
@@ -258,10 +267,13 @@ __global__ void __launch_bounds__(RB) k_reduce_h(const double2* __restrict__ par
     }
 }
 
-// Whether the second Gram-Schmidt pass is needed (the criterion of Daniel, Gragg, Kaufman and
-// Stewart): after the first pass |w'|^2 = |w|^2 - sum |h_i|^2 (Pythagoras, FP64); if it kept at
-// least half of |w|^2 (|w'| >= |w| / sqrt 2) the first pass lost no significant digits and
-// *skip = 1, else the pass runs.  wpart: the RG partials of |w|^2 before the pass.
+// Whether the second Gram-Schmidt pass is needed (a test in the manner of Daniel, Gragg, Kaufman
+// and Stewart): after the first pass |w'|^2 = |w|^2 - sum |h_i|^2 (Pythagoras, FP64).  One
+// classical pass leaves w' orthogonal to the basis up to about u |w| / |w'|, u the working
+// precision; the basis and w are double-float (u ~ 1e-14), so the pass is repeated only when
+// |w'| < kReorthEta |w| (1e-4: orthogonality stays below about 1e-10, far under any GMRES
+// tolerance), else *skip = 1.  wpart: the RG partials of |w|^2 before the pass.
+constexpr double kReorthEta = 1e-4;
 __global__ void __launch_bounds__(RB) k_reorth_decide(const double2* __restrict__ wpart, const double2* __restrict__ h,
                                                       int nvec, int* __restrict__ skip) {
     __shared__ double2 sh[RB / 32];
@@ -269,7 +281,7 @@ __global__ void __launch_bounds__(RB) k_reorth_decide(const double2* __restrict_
     for (int b = threadIdx.x; b < RG; b += RB) acc.x += wpart[b].x;
     for (int i = threadIdx.x; i < nvec; i += RB) acc.y += h[i].x * h[i].x + h[i].y * h[i].y;
     const double2 s = block_sum2(acc, sh);
-    if (threadIdx.x == 0) *skip = (s.x - s.y >= 0.5 * s.x) ? 1 : 0;
+    if (threadIdx.x == 0) *skip = (s.x - s.y >= kReorthEta * kReorthEta * s.x) ? 1 : 0;
 }
 
 // one block: nrm = sqrt(sum of the RG partials of |w|^2); hsum[j1] = nrm (when j1 >= 0);
@@ -399,7 +411,7 @@ struct Ctx {
         count(2);
         double2 h;
         HFMM_CUDA(cudaMemcpyAsync(&h, small, sizeof(double2), cudaMemcpyDeviceToHost, st));
-        HFMM_CUDA(cudaStreamSynchronize(st));
+        host_wait(P, st);
         return std::sqrt(h.x);
     }
 };
@@ -466,7 +478,7 @@ int run_gmres(hfmm_plan* P, const void* rhs, void* x_out, int* iters, double* re
     if (bnorm == 0.0) {
         k_df_to_c64<<<c.nb, 256, 0, st>>>(N, P->gx.p, (float2*)x_out);
         c.count();
-        HFMM_CUDA(cudaStreamSynchronize(st));
+        host_wait(P, st);
         *iters = 0;
         *relres = 0.0;
         return HFMM_OK;
@@ -495,7 +507,7 @@ int run_gmres(hfmm_plan* P, const void* rhs, void* x_out, int* iters, double* re
             c.count(2);
             double rh[2];
             HFMM_CUDA(cudaMemcpyAsync(rh, A.res, sizeof(rh), cudaMemcpyDeviceToHost, st));
-            HFMM_CUDA(cudaStreamSynchronize(st));
+            host_wait(P, st);
             ++it;
             jdone = j + 1;
             if (rh[0] <= tol || rh[1] == 0.0) break;
@@ -514,7 +526,7 @@ int run_gmres(hfmm_plan* P, const void* rhs, void* x_out, int* iters, double* re
     k_df_to_c64<<<c.nb, 256, 0, st>>>(N, P->gx.p, (float2*)x_out);
     c.count();
     HFMM_CUDA(cudaGetLastError());
-    HFMM_CUDA(cudaStreamSynchronize(st));
+    host_wait(P, st);
     *iters = it;
     *relres = beta / bnorm;
     return converged ? HFMM_OK : HFMM_NOT_CONVERGED;
@@ -643,7 +655,7 @@ struct BCtx {
         count(2);
         std::vector<double2> h(R);
         HFMM_CUDA(cudaMemcpyAsync(h.data(), small, sizeof(double2) * R, cudaMemcpyDeviceToHost, st));
-        HFMM_CUDA(cudaStreamSynchronize(st));
+        host_wait(P, st);
         std::vector<double> out(R);
         for (int r = 0; r < R; ++r) out[r] = std::sqrt(h[r].x);
         return out;
@@ -678,7 +690,7 @@ struct BCtx {
         count(2);
         std::vector<double2> h((size_t)R * nvec);
         HFMM_CUDA(cudaMemcpyAsync(h.data(), small, sizeof(double2) * h.size(), cudaMemcpyDeviceToHost, st));
-        HFMM_CUDA(cudaStreamSynchronize(st));
+        host_wait(P, st);
         std::vector<std::vector<cd>> hc(R, std::vector<cd>(nvec));
         for (int r = 0; r < R; ++r)
             for (int i = 0; i < nvec; ++i) {
@@ -815,7 +827,7 @@ int run_gmres_batched(hfmm_plan* P, const float2* rhs, float2* x_out, int R, int
     k_df_to_c64<<<c.nbRN(), 256, 0, st>>>(RN, xg, x_out);
     c.count();
     HFMM_CUDA(cudaGetLastError());
-    HFMM_CUDA(cudaStreamSynchronize(st));
+    host_wait(P, st);
     return all_done() ? HFMM_OK : HFMM_NOT_CONVERGED;
 }
 
@@ -851,7 +863,7 @@ int run_refinement(hfmm_plan* Pi, hfmm_plan* Po, const float2* rhs, float2* x_ou
         Pi->launches += 2;
         double2 h;
         HFMM_CUDA(cudaMemcpyAsync(&h, small, sizeof(double2), cudaMemcpyDeviceToHost, st));
-        HFMM_CUDA(cudaStreamSynchronize(st));
+        host_wait(Pi, st);
         return std::sqrt(h.x);
     };
     // A_outer applied to the iterate: on a precision = 1 plan the near field and correction in
@@ -897,7 +909,7 @@ int run_refinement(hfmm_plan* Pi, hfmm_plan* Po, const float2* rhs, float2* x_ou
     k_df_to_c64<<<nb, 256, 0, st>>>(N, Pi->rx.p, x_out);
     Pi->launches += 1;
     HFMM_CUDA(cudaGetLastError());
-    HFMM_CUDA(cudaStreamSynchronize(st));
+    host_wait(Pi, st);
     if (outer_iters) *outer_iters = outer;
     if (inner_iters) *inner_iters = inner;
     if (relres) *relres = rel;

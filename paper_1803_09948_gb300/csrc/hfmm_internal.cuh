@@ -304,6 +304,10 @@ struct hfmm_plan {
     float tune_ms[HFMM_NUM_TUNABLES][HFMM_TUNE_CANDIDATES] = {{-1, -1, -1, -1}, {-1, -1, -1, -1},
                                                              {-1, -1, -1, -1}, {-1, -1, -1, -1}};
     MatvecGraph mvg;
+    cudaEvent_t host_ev = nullptr;  // blocking-sync event for the solvers' host waits
+    ~hfmm_plan() {
+        if (host_ev) cudaEventDestroy(host_ev);
+    }
 };
 
 // ---------------------------------------------------------------- kernels: FMM matvec

@@ -233,8 +233,8 @@ void emit_items(const PairBuckets& pb, const std::vector<int64_t>& op_of_bucket,
 }  // namespace
 
 // candidates of each tunable (the order of hfmm_plan_tuning's tuned_ms) and the defaults
-constexpr int kTuneCount[HFMM_NUM_TUNABLES] = {2, 2, 3, 2};
-constexpr int kTuneValue[HFMM_NUM_TUNABLES][HFMM_TUNE_CANDIDATES] = {{0, 1}, {0, 1}, {8, 16, 32}, {0, 1}};
+constexpr int kTuneCount[HFMM_NUM_TUNABLES] = {3, 2, 3, 2};
+constexpr int kTuneValue[HFMM_NUM_TUNABLES][HFMM_TUNE_CANDIDATES] = {{0, 1, 2}, {0, 1}, {8, 16, 32}, {0, 1}};
 constexpr int kTuneDefault[HFMM_NUM_TUNABLES] = {kDefaultP2PKernel, kDefaultM2LKernel, 32, kDefaultOverlap};
 
 // Splits the source-stationary M2L groups (built with at most m2l_tc_max_group() items,
@@ -1186,7 +1186,7 @@ int hfmm_plan_create(const hfmm_config* cfg, const double* vertices, int64_t n_v
         cfg->p_min < 0 || cfg->p_min > HFMM_PMAX || !(cfg->near_factor >= 0.0) || cfg->quad_order < 2 ||
         cfg->quad_order > 64 || cfg->restart < 1 || cfg->max_iter < 1 || !(cfg->tol > 0.0) ||
         (cfg->m2l_tensor != 0 && cfg->m2l_tensor != 1) || (cfg->adaptive != 0 && cfg->adaptive != 1) ||
-        (cfg->autotune != 0 && cfg->autotune != 1) || cfg->p2p_kernel < -1 || cfg->p2p_kernel > 1 ||
+        (cfg->autotune != 0 && cfg->autotune != 1) || cfg->p2p_kernel < -1 || cfg->p2p_kernel > 2 ||
         cfg->m2l_kernel < -1 || cfg->m2l_kernel > 1 ||
         (cfg->tc_group != 0 && cfg->tc_group != 8 && cfg->tc_group != 16 && cfg->tc_group != 32) ||
         cfg->overlap < -1 || cfg->overlap > 1 || (cfg->precision != 0 && cfg->precision != 1))

@@ -104,7 +104,8 @@ class Admission:
             self._cv.notify_all()
 
 
-def gpu_executor(restart: int = 30, tol: float = 1e-4, keep_solution: bool = False, max_iter: int = 1000):
+def gpu_executor(restart: int = 30, tol: float = 1e-4, keep_solution: bool = False, max_iter: int = 1000,
+                 max_building: int = 8):
     """Executor that solves a request with the library on the calling thread's stream.
     Returns a function(request, stream) -> dict of timings and results (with the
     solutions, [nrhs][N] complex64 on the host, under "x" when keep_solution)."""
@@ -112,13 +113,18 @@ def gpu_executor(restart: int = 30, tol: float = 1e-4, keep_solution: bool = Fal
 
     from . import Plan
 
+    # at most max_building plans are built at once: a build is mostly host work (octree, lists,
+    # work items) plus short device kernels, and dozens at once only slow every one of them down
+    building = threading.Semaphore(max_building)
+
     def run(req, stream):
         t0 = time.perf_counter()
         with torch.cuda.stream(stream):
-            plan = Plan(req["V"], req["F"], req["k"], stream=stream, restart=restart, tol=tol, max_iter=max_iter)
-            try:
+            with building:
+                plan = Plan(req["V"], req["F"], req["k"], stream=stream, restart=restart, tol=tol, max_iter=max_iter)
                 stream.synchronize()  # plan ready (its build is part of the request's time); only this
                 # request's stream: a device-wide wait would stall every other request in flight
+            try:
                 t1 = time.perf_counter()
                 R, N = req["nrhs"], plan.n
                 b = torch.empty(R * N, dtype=torch.complex64, device="cuda")

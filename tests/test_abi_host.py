@@ -66,7 +66,7 @@ def test_invalid_arguments_are_rejected_on_the_host():
     assert _create(V, F, adaptive=2)[0] == pkg.HFMM_E_INVALID
     assert _create(V, F, m2l_tensor=-1)[0] == pkg.HFMM_E_INVALID
     assert _create(V, F, autotune=2)[0] == pkg.HFMM_E_INVALID
-    assert _create(V, F, p2p_kernel=2)[0] == pkg.HFMM_E_INVALID
+    assert _create(V, F, p2p_kernel=3)[0] == pkg.HFMM_E_INVALID
     assert _create(V, F, tc_group=12)[0] == pkg.HFMM_E_INVALID
     assert _create(V, F, overlap=3)[0] == pkg.HFMM_E_INVALID
     assert _create(V[:0], F)[0] == pkg.HFMM_E_INVALID          # no vertices
@@ -123,6 +123,7 @@ def test_tuner_rule_with_fake_timings():
     assert pkg.hfmm_tune_choose(P2P, [0.90, 1.00]) == 0           # staged 10 % faster
     assert pkg.hfmm_tune_choose(P2P, [0.99, 1.00]) == 1           # within noise: default kept
     assert pkg.hfmm_tune_choose(P2P, [1.20, 1.00]) == 1
+    assert pkg.hfmm_tune_choose(P2P, [1.20, 1.00, 0.90]) == 2     # the pipelined kernel 10 % faster
     # M2L: the default is the source-stationary kernel (0)
     assert pkg.hfmm_tune_choose(M2L, [2.0, 0.5]) == 1
     assert pkg.hfmm_tune_choose(M2L, [1.0, 0.99]) == 0
@@ -136,4 +137,4 @@ def test_tuner_rule_with_fake_timings():
     with pytest.raises(pkg.HfmmError):
         pkg.hfmm_tune_choose(7, [1.0, 2.0])
     with pytest.raises(pkg.HfmmError):
-        pkg.hfmm_tune_choose(P2P, [1.0, 2.0, 3.0])  # more values than candidates
+        pkg.hfmm_tune_choose(P2P, [1.0, 2.0, 3.0, 4.0])  # more values than candidates

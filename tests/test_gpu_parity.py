@@ -237,6 +237,31 @@ def test_solve_c1_against_dense_solution(c1):
     assert e_gpu < e_lu + 60 * 2e-4
 
 
+def test_solve_c1_matches_the_oracle_gmres(c1):
+    """The converged GMRES solution against the oracle's: FP64 GMRES(30) to 1e-4 (the oracle's
+    own implementation) on the oracle's operator, its FP64 FMM of the point part at the same
+    order and tree plus its sparse correction.  The two operators differ by the GPU's FP32
+    arithmetic (about 1e-6), so both solves take the same Krylov steps and stop at the same
+    iteration; the solutions then agree to 1e-4."""
+    plan = c1["plan"]
+    V, F = c1["V"], c1["F"]
+    b = _dev(np.zeros(plan.n))
+    plan.rhs_planewave([0.0, 0.0, 1.0], b)
+    x = torch.empty_like(b)
+    st, its, rr = plan.solve(b, x)
+    assert st == pkg.HFMM_OK
+    X, W, _ = oracle.points(V, F)
+    C = oracle.correction_csr(V, F, 1.0, c1["r"])
+
+    def op(s):
+        return oracle.fmm(X, W, 1.0, s, leaf_max=64, p_fixed=8, parts=3)[0] + C @ s
+
+    bb = oracle.plane_wave(X, 1.0, (0, 0, 1))
+    xo, it_o, rr_o, _ = oracle.gmres(op, bb, restart=30, tol=1e-4)
+    assert abs(it_o - its[0]) <= 1
+    assert rel(_host(x), xo) < 1e-4
+
+
 def test_solve_tight_matches_dense_solution():
     """Higher order (operator error ~4e-7) and tolerance 5e-7 (an FP32 matvec
     cannot certify much less): solution within 1e-4 of the oracle's."""

@@ -1,7 +1,8 @@
 """Every selectable kernel variant against the FP64 oracle.
 
 The configuration can pin (or leave to the plan-time tuner) the near-field kernel
-(p2p_kernel 0: four lanes per target; 1: packed FP32x2 pairs of sources), the matvec
+(p2p_kernel 0: four lanes per target; 1: packed FP32x2 pairs of sources; 2: the packed
+arithmetic in persistent blocks with the next leaf's sources loaded by cp.async), the matvec
 form (overlap 0: stages one after another; 1: near field and correction on a second
 branch beside the far field, captured once as a CUDA graph) and the tensor-core group
 size.  Whatever the tuner picks must meet the same bars as the defaults:
@@ -52,7 +53,7 @@ def c1():
     return dict(V=V, F=F, s=s, ref=oracle.direct_matvec(V, F, 1.0, r, s), near=near)
 
 
-@pytest.mark.parametrize("p2p", [0, 1])
+@pytest.mark.parametrize("p2p", [0, 1, 2])
 @pytest.mark.parametrize("overlap", [0, 1])
 def test_matvec_variants_against_oracle(c1, p2p, overlap):
     plan = pkg.Plan(c1["V"], c1["F"], 1.0, p_fixed=8, leaf_max=64, p2p_kernel=p2p, overlap=overlap)
@@ -77,7 +78,7 @@ def test_overlapped_and_sequential_forms_agree(c1):
         b.close()
 
 
-@pytest.mark.parametrize("p2p", [0, 1])
+@pytest.mark.parametrize("p2p", [0, 1, 2])
 def test_near_field_kernels_all_pairs_and_polynomial_edge(p2p):
     """One leaf holding every point (targets loop over several rounds of 128 threads),
     and the polynomial's top range on the corner-lattice soup."""
@@ -102,7 +103,7 @@ def test_near_field_kernels_all_pairs_and_polynomial_edge(p2p):
         plan.close()
 
 
-@pytest.mark.parametrize("p2p", [0, 1])
+@pytest.mark.parametrize("p2p", [0, 1, 2])
 @pytest.mark.parametrize("level,leaf", [(0, 4), (1, 16), (2, 20)])
 def test_near_field_kernels_small_and_ragged(p2p, level, leaf):
     """Leaves of 1..20 points: odd self segments, padding pairs, one thread group per target."""
@@ -193,7 +194,7 @@ def test_autotuned_plan_meets_the_bars(c1):
         t = plan.tuning()
         for name, cands in pkg.TUNABLES:
             assert t[name]["choice"] in cands
-        assert set(t["p2p_kernel"]["ms"]) == {0, 1} and set(t["overlap"]["ms"]) == {0, 1}
+        assert set(t["p2p_kernel"]["ms"]) == {0, 1, 2} and set(t["overlap"]["ms"]) == {0, 1}
         assert set(t["m2l_kernel"]["ms"]) == {0, 1}
         assert all(v > 0 for q in t.values() for v in q["ms"].values())
         assert rel(_apply(plan, c1["s"]), c1["ref"]) < 1e-4
