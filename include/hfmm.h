@@ -219,7 +219,9 @@ int hfmm_field(hfmm_plan* plan, const void* density, const double* targets, int6
 /*
  * Mixed-precision iterative refinement for one right-hand side (the paper's
  * GMRES solve taken to a tighter residual; configuration "refinement to
- * 1e-6"): x_0 = 0; repeat  r = b - A_outer x  (formed in double-float, FP64-class),
+ * 1e-6"): x_0 = 0; repeat  r = b - A_outer x  (formed in double-float, FP64-class;
+ * on an outer plan created with precision = 1 its near field and correction are evaluated
+ * in FP64 on the whole double-float iterate, as in hfmm_matvec_df),
  * stop when |r| <= tol_outer |b|, solve A_inner d = r by GMRES on the inner plan
  * (its own restart and tolerance), x += d (double-float).  `inner` and `outer`
  * are plans of the same mesh and wavenumber (same N, user point order); the
