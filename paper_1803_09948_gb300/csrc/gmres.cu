@@ -145,7 +145,7 @@ __device__ __forceinline__ double2 block_sum2(double2 v, double2* sh) {
 // i = blockIdx.y * kDotVecs + c (< nvec); grid RG x ceil(nvec / kDotVecs).  with_norm: the
 // blocks of y = 0 also leave |w|^2 in partial[nvec * RG + blk].  skip (may be NULL): when *skip
 // is set the pass is not needed and the kernel returns at once.
-__global__ void __launch_bounds__(RB) k_dots_df(int64_t N, const float4* __restrict__ V, int nvec,
+__global__ void __launch_bounds__(RB, 2) k_dots_df(int64_t N, const float4* __restrict__ V, int nvec,
                                                 const float4* __restrict__ w, double2* __restrict__ partial,
                                                 const int* __restrict__ skip, int with_norm) {
     if (skip && *skip) return;
@@ -160,10 +160,15 @@ __global__ void __launch_bounds__(RB) k_dots_df(int64_t N, const float4* __restr
             wn.add_prod(b.x, b.z, b.x, b.z);
             wn.add_prod(b.y, b.w, b.y, b.w);
         }
+        // all the row's loads in flight before the arithmetic (absent vectors read as zero,
+        // which adds nothing)
+        float4 av[kDotVecs];
+#pragma unroll
+        for (int c = 0; c < kDotVecs; ++c)
+            av[c] = c < nv ? V[(int64_t)(i0 + c) * N + r] : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
         for (int c = 0; c < kDotVecs; ++c) {
-            if (c >= nv) break;
-            const float4 a = V[(int64_t)(i0 + c) * N + r];
+            const float4 a = av[c];
             // conj(a) b = (ar br + ai bi) + i (ar bi - ai br)
             re[c].add_prod(a.x, a.z, b.x, b.z);
             re[c].add_prod(a.y, a.w, b.y, b.w);
@@ -546,10 +551,13 @@ __global__ void __launch_bounds__(RB) k_dots_bdf(int64_t N, int R, const float4*
     Acc re[kDotVecs], im[kDotVecs];
     for (int64_t n = (int64_t)blockIdx.x * RB + threadIdx.x; n < N; n += (int64_t)RG * RB) {
         const float4 b = wr[n];
+        float4 av[kDotVecs];  // all the row's loads in flight first (absent vectors: zero)
+#pragma unroll
+        for (int c = 0; c < kDotVecs; ++c)
+            av[c] = c < nv ? V[((int64_t)(i0 + c) * R + r) * N + n] : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
         for (int c = 0; c < kDotVecs; ++c) {
-            if (c >= nv) break;
-            const float4 a = V[((int64_t)(i0 + c) * R + r) * N + n];
+            const float4 a = av[c];
             re[c].add_prod(a.x, a.z, b.x, b.z);
             re[c].add_prod(a.y, a.w, b.y, b.w);
             im[c].add_prod(a.x, a.z, b.y, b.w);
