@@ -203,6 +203,15 @@ int hfmm_solve(hfmm_plan* plan, const void* rhs, void* x_out, int nrhs, int* ite
                double* relres_out, void* stream);
 
 /*
+ * Whether the plan's last single right-hand-side solve ran each GMRES cycle as one graph
+ * launch: a CUDA graph whose while node repeats one Arnoldi step (matvec, Gram-Schmidt,
+ * rotations, residual estimate) until a kernel of the step sets its condition to zero, with no
+ * host round trip per iteration (*cycle_graph = 1), or with the host driving the same steps
+ * (0: adaptive trees, or a graph that could not be built).  HOST output.
+ */
+int hfmm_solver_info(const hfmm_plan* plan, int* cycle_graph);
+
+/*
  * Off-surface evaluation (the paper's scattered field at observation points,
  * Sec. 6.4): field[t] = sum_j w_j exp(i k |t - x_j|) / (4 pi |t - x_j|) density_j,
  * the single-layer potential of the density at n_targets points t away from the

@@ -30,7 +30,7 @@ EXPORTED = [
     "hfmm_plan_info", "hfmm_matvec", "hfmm_matvec_parts", "hfmm_direct", "hfmm_rhs_planewave",
     "hfmm_solve", "hfmm_solve_refined", "hfmm_status_string", "hfmm_last_error", "hfmm_matvec_timed",
     "hfmm_launch_count", "hfmm_plan_costs", "hfmm_point_sum_noalloc", "hfmm_device_status", "hfmm_field",
-    "hfmm_matvec_host", "hfmm_plan_tuning", "hfmm_tune_choose", "hfmm_matvec_df",
+    "hfmm_matvec_host", "hfmm_plan_tuning", "hfmm_tune_choose", "hfmm_matvec_df", "hfmm_solver_info",
 ]
 HFMM_NOALLOC_MAX_POINTS = 262144
 STAGES = ["prep", "p2p", "p2m", "m2m", "m2l_simt", "m2l", "l2l", "l2p", "corr", "output"]
@@ -90,6 +90,7 @@ def lib():
         L.hfmm_matvec_parts.argtypes = [vp, vp, vp, ctypes.c_int, ctypes.c_int, vp]
         L.hfmm_matvec_host.argtypes = [vp, vp, vp, ctypes.c_int, vp]
         L.hfmm_matvec_df.argtypes = [vp, vp, vp, ctypes.c_int, vp]
+        L.hfmm_solver_info.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
         L.hfmm_plan_tuning.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_float)]
         L.hfmm_tune_choose.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_float), ctypes.c_int,
                                        ctypes.POINTER(ctypes.c_int)]
@@ -429,6 +430,12 @@ class Plan:
 
     def matvec_host(self, density, potential, nrhs=1, stream=None):
         hfmm_matvec_host(self.handle, density, potential, nrhs, stream)
+
+    def solver_info(self):
+        """{'cycle_graph': 1 if the last single-RHS solve ran its GMRES cycles as graph launches}."""
+        v = ctypes.c_int()
+        _check(lib().hfmm_solver_info(self.handle, ctypes.byref(v)), "hfmm_solver_info")
+        return {"cycle_graph": v.value}
 
     def matvec_df(self, density_df, potential_df, parts=7, stream=None):
         hfmm_matvec_df(self.handle, density_df, potential_df, parts, stream)

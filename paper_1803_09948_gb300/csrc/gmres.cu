@@ -147,10 +147,13 @@ __device__ __forceinline__ double2 block_sum2(double2 v, double2* sh) {
 // is set the pass is not needed and the kernel returns at once.
 __global__ void __launch_bounds__(RB, 2) k_dots_df(int64_t N, const float4* __restrict__ V, int nvec,
                                                 const float4* __restrict__ w, double2* __restrict__ partial,
-                                                const int* __restrict__ skip, int with_norm) {
+                                                const int* __restrict__ skip, int with_norm,
+                                                const int* __restrict__ jd = nullptr) {
     if (skip && *skip) return;
+    if (jd) nvec = *jd + 1;  // the iteration index held on the device (graph-replayed steps)
     __shared__ double2 sh[RB / 32];
     const int i0 = blockIdx.y * kDotVecs;
+    if (i0 >= nvec) return;  // uniform over the block (grids sized for the longest step)
     const int nv = min(kDotVecs, nvec - i0);
     const bool nrm = with_norm && blockIdx.y == 0;
     Acc re[kDotVecs], im[kDotVecs], wn;
@@ -217,8 +220,10 @@ __global__ void __launch_bounds__(RB) k_reduce(const double2* __restrict__ parti
 
 // x += sign * sum_i h_i V_i, with h given as double-float pairs hdf[i] = (re_hi, im_hi, re_lo, im_lo)
 __global__ void k_axpy_df(int64_t N, const float4* __restrict__ V, int nvec, const float4* __restrict__ hdf,
-                          float sign, float4* __restrict__ x, const int* __restrict__ skip = nullptr) {
+                          float sign, float4* __restrict__ x, const int* __restrict__ skip = nullptr,
+                          const int* __restrict__ jd = nullptr) {
     if (skip && *skip) return;
+    if (jd) nvec = *jd + 1;
     extern __shared__ float4 hs[];
     for (int q = threadIdx.x; q < nvec; q += blockDim.x) hs[q] = hdf[q];
     __syncthreads();
@@ -255,8 +260,10 @@ __device__ __forceinline__ float4 to_df4(double2 v) {
 // block i: h_i = sum of its RG partials; coeff[i] = h_i as double-float (the update
 // w -= V h); hsum[i] += h_i (the Hessenberg column, summed over the two passes)
 __global__ void __launch_bounds__(RB) k_reduce_h(const double2* __restrict__ partial, float4* __restrict__ coeff,
-                                                 double2* __restrict__ hsum, const int* __restrict__ skip) {
+                                                 double2* __restrict__ hsum, const int* __restrict__ skip,
+                                                 const int* __restrict__ jd = nullptr) {
     if (skip && *skip) return;
+    if (jd && (int)blockIdx.x > *jd) return;  // blocks beyond this step's vectors
     __shared__ double2 sh[RB / 32];
     double2 acc = make_double2(0, 0);
     for (int b = threadIdx.x; b < RG; b += RB) {
@@ -279,8 +286,11 @@ __global__ void __launch_bounds__(RB) k_reduce_h(const double2* __restrict__ par
 // |w'| < kReorthEta |w| (1e-4: orthogonality stays below about 1e-10, far under any GMRES
 // tolerance), else *skip = 1.  wpart: the RG partials of |w|^2 before the pass.
 constexpr double kReorthEta = 1e-4;
-__global__ void __launch_bounds__(RB) k_reorth_decide(const double2* __restrict__ wpart, const double2* __restrict__ h,
-                                                      int nvec, int* __restrict__ skip) {
+__global__ void __launch_bounds__(RB) k_reorth_decide(const double2* __restrict__ partial, const double2* __restrict__ h,
+                                                      int nvec, int* __restrict__ skip,
+                                                      const int* __restrict__ jd = nullptr) {
+    if (jd) nvec = *jd + 1;
+    const double2* wpart = partial + (size_t)nvec * RG;
     __shared__ double2 sh[RB / 32];
     double2 acc = make_double2(0, 0);
     for (int b = threadIdx.x; b < RG; b += RB) acc.x += wpart[b].x;
@@ -293,7 +303,8 @@ __global__ void __launch_bounds__(RB) k_reorth_decide(const double2* __restrict_
 // scale = 1 / nrm as (hi, lo) (0 when nrm = 0); out[0] = nrm
 __global__ void __launch_bounds__(RB) k_norm_finish(const double2* __restrict__ partial, int j1,
                                                     double2* __restrict__ hsum, float2* __restrict__ scale,
-                                                    double* __restrict__ out) {
+                                                    double* __restrict__ out, const int* __restrict__ jd = nullptr) {
+    if (jd) j1 = *jd + 1;
     __shared__ double2 sh[RB / 32];
     double2 acc = make_double2(0, 0);
     for (int b = threadIdx.x; b < RG; b += RB) acc.x += partial[b].x;
@@ -308,11 +319,12 @@ __global__ void __launch_bounds__(RB) k_norm_finish(const double2* __restrict__ 
     }
 }
 
-// b = s a with s = (hi, lo) read from device memory
+// b = s a with s = (hi, lo) read from device memory; with jd, b is basis vector *jd + 1 of b
 __global__ void k_scale_df_dev(int64_t N, const float4* __restrict__ a, const float2* __restrict__ s,
-                               float4* __restrict__ b) {
+                               float4* __restrict__ b, const int* __restrict__ jd = nullptr) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
+    if (jd) b += (int64_t)(*jd + 1) * N;
     const float sh = s->x, sl = s->y;
     const float4 v = a[i];
     float4 o;
@@ -344,8 +356,11 @@ struct Arnoldi {     // device state of one GMRES cycle (FP64)
 };
 
 // Column j: previous rotations, a new rotation for rows (j, j+1), g, the residual estimate.
-__global__ void k_givens(int j, int m, const double2* __restrict__ hsum, Arnoldi A, double bnorm) {
+__global__ void k_givens(int j, int m, const double2* __restrict__ hsum, Arnoldi A, double bnorm,
+                         const int* __restrict__ jd = nullptr, const double* __restrict__ bnorm_d = nullptr) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    if (jd) j = *jd;
+    if (bnorm_d) bnorm = *bnorm_d;
     double2 h[2];  // rows i, i + 1 as the rotations sweep down
     h[0] = hsum[0];
     for (int i = 0; i < j; ++i) {
@@ -394,6 +409,31 @@ __global__ void k_backsolve(int n, int m, Arnoldi A, double2* __restrict__ y, fl
     }
 }
 
+// sig[i] = wscale[i] (high part of basis vector *jd at user point perm[i]): the density of the
+// step's matvec, read from the basis without a host-side pointer
+__global__ void k_prep_basis(int64_t N, const int32_t* __restrict__ perm, const float* __restrict__ wscale,
+                             const float4* __restrict__ V, const int* __restrict__ jd, float2* __restrict__ sig) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const float4 v = V[(int64_t)(*jd) * N + perm[i]];
+    const float w = wscale[i];
+    sig[i] = make_float2(w * v.x, w * v.y);
+}
+
+// End of an Arnoldi step: one more iteration and one more basis vector; the cycle goes on while
+// the residual estimate is above tol, the new column is non-zero, the cycle has room and the
+// iteration budget is not spent.  With a graph, the decision is the while node's condition.
+__global__ void k_step_end(const double* __restrict__ res, int* __restrict__ jd, int* __restrict__ itd, int m,
+                           int maxit, double tol, int* __restrict__ cont, cudaGraphConditionalHandle h, int use_h) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const int j = *jd + 1, it = *itd + 1;
+    *jd = j;
+    *itd = it;
+    const int go = (res[0] > tol && res[1] != 0.0 && j < m && it < maxit) ? 1 : 0;
+    *cont = go;
+    if (use_h) cudaGraphSetConditional(h, (unsigned)go);
+}
+
 namespace {
 struct Ctx {
     hfmm_plan* P;
@@ -432,8 +472,12 @@ int run_gmres(hfmm_plan* P, const void* rhs, void* x_out, int* iters, double* re
     // norm, scale
     const size_t n_part = 2 * (size_t)RG * (m + 2), n_hsum = 2 * (size_t)(m + 2), n_H = 2 * (size_t)(m + 1) * m,
                  n_cs = 2 * (size_t)m, n_g = 2 * (size_t)(m + 1), n_y = 2 * (size_t)m, n_coef = 2 * (size_t)(m + 2);
-    const size_t n_ws = n_part + n_hsum + n_H + 2 * n_cs + n_g + n_y + n_coef + 6;
+    const size_t n_ws = n_part + n_hsum + n_H + 2 * n_cs + n_g + n_y + n_coef + 8;
     if (P->kry_m != m) {
+        if (P->gm_exec) {  // the captured step refers to the old workspace
+            cudaGraphExecDestroy(P->gm_exec);
+            P->gm_exec = nullptr;
+        }
         P->kry.alloc((size_t)(m + 1) * N, nullptr);
         P->gw.alloc(N, nullptr);
         P->gx.alloc(N, nullptr);
@@ -456,6 +500,10 @@ int run_gmres(hfmm_plan* P, const void* rhs, void* x_out, int* iters, double* re
     double* nrm = tail + 2;   // 1 double
     float2* scale = (float2*)(tail + 3);
     int* skip2 = (int*)(tail + 4);  // second Gram-Schmidt pass not needed
+    int* jd = (int*)(tail + 5);     // step of the cycle, held on the device
+    int* itd = jd + 1;              // iterations of the solve
+    int* contd = (int*)(tail + 6);  // the step's decision (host-driven steps)
+    double* bnd = tail + 7;         // ||b||
     Ctx c{P, st, N, (unsigned)((N + 255) / 256), partial, hsum, coeff};
     float4* V = P->kry.p;
     auto launch_norm = [&](const float4* w, int j1) {  // nrm, scale = 1 / nrm, hsum[j1] = nrm
@@ -470,11 +518,89 @@ int run_gmres(hfmm_plan* P, const void* rhs, void* x_out, int* iters, double* re
                                                                               first ? nullptr : skip2, first);
         k_reduce_h<<<nvec, RB, 0, st>>>(partial, coeff, hsum, first ? nullptr : skip2);
         if (first) {
-            k_reorth_decide<<<1, RB, 0, st>>>(partial + (size_t)nvec * RG, hsum, nvec, skip2);
+            k_reorth_decide<<<1, RB, 0, st>>>(partial, hsum, nvec, skip2);
             c.count();
         }
         k_axpy_df<<<c.nb, 256, sizeof(float4) * nvec, st>>>(N, V, nvec, coeff, -1.f, w, first ? nullptr : skip2);
         c.count(3);
+    };
+    // One Arnoldi step with the step index j held on the device (stream s): the matvec of basis
+    // vector j, Gram-Schmidt against the j + 1 vectors (the second pass only when the first
+    // cancelled), the new basis vector, the rotations and the residual estimate, then the
+    // decision to go on (the while node's condition h when use_h).  Grids are sized for the
+    // cycle's longest step, so the same launches serve every j.
+    auto step = [&](cudaStream_t s, cudaGraphConditionalHandle h, int use_h) {
+        float4* w = P->gw.p;
+        const unsigned gy = (unsigned)((m + kDotVecs - 1) / kDotVecs);
+        k_prep_basis<<<c.nb, 256, 0, s>>>(N, P->perm.p, P->wscale.p, V, jd, P->sig.p);
+        run_matvec_sorted(P, 15, s);  // every stage launched directly (a replay cannot sit in this capture)
+        launch_output(P, P->phi.p, w, VecKind::DoubleFloat, s);
+        HFMM_CUDA(cudaMemsetAsync(hsum, 0, sizeof(double2) * (m + 1), s));
+        for (int pass = 0; pass < 2; ++pass) {
+            const bool first = pass == 0;
+            k_dots_df<<<dim3(RG, gy), RB, 0, s>>>(N, V, 0, w, partial, first ? nullptr : skip2, first, jd);
+            k_reduce_h<<<m, RB, 0, s>>>(partial, coeff, hsum, first ? nullptr : skip2, jd);
+            if (first) k_reorth_decide<<<1, RB, 0, s>>>(partial, hsum, 0, skip2, jd);
+            k_axpy_df<<<c.nb, 256, sizeof(float4) * m, s>>>(N, V, 0, coeff, -1.f, w, first ? nullptr : skip2, jd);
+        }
+        k_norm2_df<<<RG, RB, 0, s>>>(N, w, partial);
+        k_norm_finish<<<1, RB, 0, s>>>(partial, 0, hsum, scale, nrm, jd);
+        k_scale_df_dev<<<c.nb, 256, 0, s>>>(N, w, scale, V, jd);
+        k_givens<<<1, 32, 0, s>>>(0, m, hsum, A, 0.0, jd, bnd);
+        k_step_end<<<1, 32, 0, s>>>(A.res, jd, itd, m, maxit, tol, contd, h, use_h);
+        c.count(13);  // prep, 7 Gram-Schmidt kernels, norm, norm finish, scale, rotations, step end
+        HFMM_CUDA(cudaGetLastError());
+    };
+    // The whole cycle as one graph launch: a while node whose body is one step, looping on the
+    // device until k_step_end says stop (no host round trip per iteration).  Built once per
+    // plan and restart length; on an adaptive tree, or if building fails (a capture that another
+    // thread invalidated), the host drives the same steps.
+    auto cycle_graph = [&]() -> bool {
+        if (P->adaptive) return false;
+        if (P->gm_exec) return true;
+        MatvecGraph& MG = P->mvg;
+        if (!MG.cap) HFMM_CUDA(cudaStreamCreateWithFlags(&MG.cap, cudaStreamNonBlocking));
+        cudaGraph_t g = nullptr;
+        HFMM_CUDA(cudaGraphCreate(&g, 0));
+        cudaGraphConditionalHandle h;
+        cudaGraphNodeParams cp = {};
+        cudaGraphNode_t node;
+        if (cudaGraphConditionalHandleCreate(&h, g, 1u, cudaGraphCondAssignDefault) != cudaSuccess) {
+            cudaGraphDestroy(g);
+            cudaGetLastError();
+            return false;
+        }
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = h;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        if (cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &cp) != cudaSuccess) {
+            cudaGraphDestroy(g);
+            cudaGetLastError();
+            return false;
+        }
+        cudaGraph_t body = cp.conditional.phGraph_out[0];
+        const int64_t l0 = P->launches;
+        bool ok = cudaStreamBeginCaptureToGraph(MG.cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) ==
+                  cudaSuccess;
+        if (ok) {
+            try {
+                step(MG.cap, h, 1);
+            } catch (const HfmmError&) {
+                ok = false;
+            }
+            cudaGraph_t out = nullptr;
+            ok = (cudaStreamEndCapture(MG.cap, &out) == cudaSuccess) && ok;
+        }
+        P->gm_launches = P->launches - l0;
+        P->launches = l0;
+        if (ok) ok = cudaGraphInstantiate(&P->gm_exec, g, 0) == cudaSuccess;
+        cudaGraphDestroy(g);
+        if (!ok) {
+            P->gm_exec = nullptr;
+            cudaGetLastError();  // clears a capture or instantiation error; the host drives the steps
+        }
+        return ok;
     };
     k_c64_to_df<<<c.nb, 256, 0, st>>>(N, (const float2*)rhs, P->gb.p);
     c.count();
@@ -488,35 +614,39 @@ int run_gmres(hfmm_plan* P, const void* rhs, void* x_out, int* iters, double* re
         *relres = 0.0;
         return HFMM_OK;
     }
+    HFMM_CUDA(cudaMemcpyAsync(bnd, &bnorm, sizeof(double), cudaMemcpyHostToDevice, st));
+    HFMM_CUDA(cudaMemsetAsync(itd, 0, sizeof(int), st));
     // r0 = b (x0 = 0)
     HFMM_CUDA(cudaMemcpyAsync(P->gw.p, P->gb.p, sizeof(float4) * N, cudaMemcpyDeviceToDevice, st));
+    const bool use_graph = cycle_graph();
+    P->gm_used = use_graph ? 1 : 0;
     double beta = bnorm;
     int it = 0;
     bool converged = false;
     while (it < maxit && !converged) {
-        // V_0 = r / beta, g = (beta, 0, ...)
+        // V_0 = r / beta, g = (beta, 0, ...), j = 0
         launch_norm(P->gw.p, -1);
         k_scale_df_dev<<<c.nb, 256, 0, st>>>(N, P->gw.p, scale, V);
         k_cycle_start<<<1, 64, 0, st>>>(m, A, nrm);
         c.count(2);
-        int jdone = 0;
-        for (int j = 0; j < m && it < maxit; ++j) {
-            float4* w = P->gw.p;
-            c.matvec(V + (int64_t)j * N, w);
-            HFMM_CUDA(cudaMemsetAsync(hsum, 0, sizeof(double2) * (j + 2), st));
-            cgs_pass(j + 1, w, true);  // classical Gram-Schmidt, repeated when the first pass cancelled
-            cgs_pass(j + 1, w, false);
-            launch_norm(w, j + 1);
-            k_scale_df_dev<<<c.nb, 256, 0, st>>>(N, w, scale, V + (int64_t)(j + 1) * N);
-            k_givens<<<1, 32, 0, st>>>(j, m, hsum, A, bnorm);
-            c.count(2);
-            double rh[2];
-            HFMM_CUDA(cudaMemcpyAsync(rh, A.res, sizeof(rh), cudaMemcpyDeviceToHost, st));
-            host_wait(P, st);
-            ++it;
-            jdone = j + 1;
-            if (rh[0] <= tol || rh[1] == 0.0) break;
+        HFMM_CUDA(cudaMemsetAsync(jd, 0, sizeof(int), st));
+        if (use_graph) {
+            HFMM_CUDA(cudaGraphLaunch(P->gm_exec, st));
+        } else {
+            for (;;) {
+                step(st, cudaGraphConditionalHandle{}, 0);
+                int go = 0;
+                HFMM_CUDA(cudaMemcpyAsync(&go, contd, sizeof(int), cudaMemcpyDeviceToHost, st));
+                host_wait(P, st);
+                if (!go) break;
+            }
         }
+        int ji[2];
+        HFMM_CUDA(cudaMemcpyAsync(ji, jd, sizeof(ji), cudaMemcpyDeviceToHost, st));
+        host_wait(P, st);
+        const int jdone = ji[0];
+        if (use_graph) P->launches += (int64_t)jdone * P->gm_launches;
+        it = ji[1];
         // y = H^{-1} g (upper triangular, FP64, on the device), x += V y
         k_backsolve<<<1, 32, 0, st>>>(jdone, m, A, y, coeff);
         k_axpy_df<<<c.nb, 256, sizeof(float4) * jdone, st>>>(N, V, jdone, coeff, 1.f, P->gx.p);

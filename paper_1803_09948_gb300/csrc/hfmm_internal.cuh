@@ -305,7 +305,11 @@ struct hfmm_plan {
                                                              {-1, -1, -1, -1}, {-1, -1, -1, -1}};
     MatvecGraph mvg;
     cudaEvent_t host_ev = nullptr;  // blocking-sync event for the solvers' host waits
+    cudaGraphExec_t gm_exec = nullptr;  // a GMRES cycle as one launch (while node over one step)
+    int64_t gm_launches = 0;            // kernels in one step
+    int gm_used = 0;                    // the last single-RHS solve ran its cycles as graph launches
     ~hfmm_plan() {
+        if (gm_exec) cudaGraphExecDestroy(gm_exec);
         if (host_ev) cudaEventDestroy(host_ev);
     }
 };

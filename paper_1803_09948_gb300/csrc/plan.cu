@@ -1260,6 +1260,12 @@ int hfmm_matvec_parts(hfmm_plan* P, const void* density, void* potential, int nr
     HFMM_GUARD_END
 }
 
+int hfmm_solver_info(const hfmm_plan* P, int* cycle_graph) {
+    if (!P || !cycle_graph) return HFMM_E_INVALID;
+    *cycle_graph = P->gm_used;
+    return HFMM_OK;
+}
+
 int hfmm_matvec_df(hfmm_plan* P, const void* density_df, void* potential_df, int parts, void* stream) {
     if (!P || !density_df || !potential_df || parts < 0 || parts > 7) return HFMM_E_INVALID;
     if (P->cfg.precision != 1) {

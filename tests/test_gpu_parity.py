@@ -219,6 +219,7 @@ def test_solve_c1_against_dense_solution(c1):
     x = torch.empty_like(b)
     st, its, rr = plan.solve(b, x)
     assert st == pkg.HFMM_OK and rr[0] <= 1e-4 and its[0] < 100
+    assert plan.solver_info()["cycle_graph"] == 1  # each cycle one graph launch (while node)
     X, _, _ = oracle.points(c1["V"], c1["F"])
     Z = oracle.dense_Z(c1["V"], c1["F"], 1.0, c1["r"])
     bb = oracle.plane_wave(X, 1.0, (0, 0, 1))
