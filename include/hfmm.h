@@ -212,6 +212,23 @@ int hfmm_solve(hfmm_plan* plan, const void* rhs, void* x_out, int nrhs, int* ite
 int hfmm_solver_info(const hfmm_plan* plan, int* cycle_graph);
 
 /*
+ * Solves G independent problems Z_g x_g = rhs_g together (the paper's GMRES solve, Sec. 5.1 and
+ * 6.4, for several scattering requests at once): one right-hand side per plan, G distinct plans
+ * of possibly different meshes and wavenumbers, each with its own restart, tolerance and
+ * iteration limit.  The solves advance in lockstep over restart cycles; each cycle of every
+ * unfinished solve runs inside ONE shared graph launch (one while node per solve, a finished
+ * solve's loop closed by a gate), so the requests' steps share the launch and run side by side
+ * on the device; the cycle ends (update, true residual) run per solve.  Results equal
+ * hfmm_solve's on each plan.  plans, rhs, x_out: HOST arrays of G entries (rhs / x_out are
+ * device complex64 [N_g]); iters_out / relres_out: HOST arrays of G (may be NULL).  Returns
+ * after completion; HFMM_NOT_CONVERGED if any solve hit its iteration limit; HFMM_E_INVALID for
+ * G outside 1..HFMM_GROUP_MAX, NULL entries or a plan given twice.
+ */
+#define HFMM_GROUP_MAX 64
+int hfmm_solve_group(hfmm_plan* const* plans, int G, const void* const* rhs, void* const* x_out, int* iters_out,
+                     double* relres_out, void* stream);
+
+/*
  * Off-surface evaluation (the paper's scattered field at observation points,
  * Sec. 6.4): field[t] = sum_j w_j exp(i k |t - x_j|) / (4 pi |t - x_j|) density_j,
  * the single-layer potential of the density at n_targets points t away from the

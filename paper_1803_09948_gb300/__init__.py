@@ -31,6 +31,7 @@ EXPORTED = [
     "hfmm_solve", "hfmm_solve_refined", "hfmm_status_string", "hfmm_last_error", "hfmm_matvec_timed",
     "hfmm_launch_count", "hfmm_plan_costs", "hfmm_point_sum_noalloc", "hfmm_device_status", "hfmm_field",
     "hfmm_matvec_host", "hfmm_plan_tuning", "hfmm_tune_choose", "hfmm_matvec_df", "hfmm_solver_info",
+    "hfmm_solve_group",
 ]
 HFMM_NOALLOC_MAX_POINTS = 262144
 STAGES = ["prep", "p2p", "p2m", "m2m", "m2l_simt", "m2l", "l2l", "l2p", "corr", "output"]
@@ -91,6 +92,8 @@ def lib():
         L.hfmm_matvec_host.argtypes = [vp, vp, vp, ctypes.c_int, vp]
         L.hfmm_matvec_df.argtypes = [vp, vp, vp, ctypes.c_int, vp]
         L.hfmm_solver_info.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
+        L.hfmm_solve_group.argtypes = [ctypes.POINTER(vp), ctypes.c_int, ctypes.POINTER(vp), ctypes.POINTER(vp),
+                                       ctypes.POINTER(ctypes.c_int), dp, vp]
         L.hfmm_plan_tuning.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_float)]
         L.hfmm_tune_choose.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_float), ctypes.c_int,
                                        ctypes.POINTER(ctypes.c_int)]
@@ -378,6 +381,28 @@ def hfmm_field(plan, density, targets, field_out, stream=None):
     _vec(field_out, T.shape[0], 1, "field_out")
     _check(lib().hfmm_field(plan, _ptr(density), T.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), T.shape[0],
                             _ptr(field_out), _stream(stream)), "hfmm_field")
+
+
+def hfmm_solve_group(plans, rhs, x_out, stream=None):
+    """G single right-hand-side solves on distinct plans, each restart cycle of all of them in one
+    shared graph launch.  plans: Plan objects or handles; rhs / x_out: complex64 CUDA tensors of
+    each plan's N.  Returns (status, iterations[G], true relative residuals[G])."""
+    hs = [p.handle if isinstance(p, Plan) else p for p in plans]
+    G = len(hs)
+    if not (len(rhs) == len(x_out) == G):
+        raise ValueError("plans, rhs and x_out must have the same length")
+    for h, b, x in zip(hs, rhs, x_out):
+        n = hfmm_num_points(h)
+        _vec(b, n, 1, "rhs")
+        _vec(x, n, 1, "x_out")
+    vp = ctypes.c_void_p
+    pa = (vp * G)(*[h.value if isinstance(h, vp) else h for h in hs])
+    ra = (vp * G)(*[b.data_ptr() for b in rhs])
+    xa = (vp * G)(*[x.data_ptr() for x in x_out])
+    its = (ctypes.c_int * G)()
+    rr = (ctypes.c_double * G)()
+    st = _check(lib().hfmm_solve_group(pa, G, ra, xa, its, rr, _stream(stream)), "hfmm_solve_group")
+    return st, list(its), list(rr)
 
 
 def hfmm_solve_refined(inner, outer, rhs, x_out, tol=1e-6, max_outer=10, stream=None):

@@ -434,105 +434,111 @@ __global__ void k_step_end(const double* __restrict__ res, int* __restrict__ jd,
     if (use_h) cudaGraphSetConditional(h, (unsigned)go);
 }
 
+// cudaGraphSetConditional(h, *act): opens (1) or closes (0) a group member's while loop
+__global__ void k_cond_init(cudaGraphConditionalHandle h, const int* __restrict__ act) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) cudaGraphSetConditional(h, *act ? 1u : 0u);
+}
+
 namespace {
-struct Ctx {
-    hfmm_plan* P;
-    cudaStream_t st;
-    int64_t N;
-    unsigned nb;
-    double2* partial;  // RG * (m + 2)
-    double2* small;    // at least one value
-    float4* coeff;     // m + 2 double-float complex coefficients
+
+// One single right-hand-side GMRES(m) solve on a plan (Sec. 5.1's solver): its workspace, the
+// pieces of a restart cycle, and what the host keeps between cycles.
+struct Solver {
+    hfmm_plan* P = nullptr;
+    int64_t N = 0;
+    int m = 0, maxit = 0;
+    double tol = 0.0;
+    unsigned nb = 0;
+    float4* V = nullptr;
+    double2 *partial = nullptr, *hsum = nullptr, *y = nullptr;
+    float4* coeff = nullptr;
+    Arnoldi A{};
+    double* nrm = nullptr;
+    float2* scale = nullptr;
+    int *skip2 = nullptr, *jd = nullptr, *itd = nullptr, *contd = nullptr, *actd = nullptr;
+    double* bnd = nullptr;
+    double bnorm = 0.0, beta = 0.0;
+    int it = 0;
+    bool converged = false, done = false;
+    int64_t step_launches = 0;  // kernels of one captured step
 
     void count(int n = 1) { P->launches += n; }
-    void matvec(const float4* in, float4* out) {
+
+    // workspace (doubles): partials RG (m + 2) complex, hsum m + 2, H (m + 1) m, cs m, sn m,
+    // g m + 1, y m (complex each), coefficients m + 2 (double-float complex), then 8 scalars:
+    // residual pair, norm, scale, second-pass flag, step and iteration counters, step
+    // decision and group gate, ||b||
+    void init(hfmm_plan* plan) {
+        P = plan;
+        N = P->N;
+        m = P->cfg.restart;
+        tol = P->cfg.tol;
+        maxit = P->cfg.max_iter;
+        nb = (unsigned)((N + 255) / 256);
+        const size_t n_part = 2 * (size_t)RG * (m + 2), n_hsum = 2 * (size_t)(m + 2), n_H = 2 * (size_t)(m + 1) * m,
+                     n_cs = 2 * (size_t)m, n_g = 2 * (size_t)(m + 1), n_y = 2 * (size_t)m, n_coef = 2 * (size_t)(m + 2);
+        const size_t n_ws = n_part + n_hsum + n_H + 2 * n_cs + n_g + n_y + n_coef + 8;
+        if (P->kry_m != m) {
+            if (P->gm_exec) {  // the captured step refers to the old workspace
+                cudaGraphExecDestroy(P->gm_exec);
+                P->gm_exec = nullptr;
+            }
+            P->kry.alloc((size_t)(m + 1) * N, nullptr);
+            P->gw.alloc(N, nullptr);
+            P->gx.alloc(N, nullptr);
+            P->gb.alloc(N, nullptr);
+            P->gred.alloc(n_ws, nullptr);
+            P->kry_m = m;
+        }
+        double* ws = P->gred.p;
+        partial = (double2*)ws;
+        hsum = (double2*)(ws + n_part);
+        A.H = (double2*)(ws + n_part + n_hsum);
+        A.cs = (double2*)(ws + n_part + n_hsum + n_H);
+        A.sn = A.cs + m;
+        A.g = (double2*)(ws + n_part + n_hsum + n_H + 2 * n_cs);
+        y = (double2*)(ws + n_part + n_hsum + n_H + 2 * n_cs + n_g);
+        coeff = (float4*)(ws + n_part + n_hsum + n_H + 2 * n_cs + n_g + n_y);
+        double* tail = ws + n_part + n_hsum + n_H + 2 * n_cs + n_g + n_y + n_coef;
+        A.res = tail;  // 2 doubles
+        nrm = tail + 2;
+        scale = (float2*)(tail + 3);
+        skip2 = (int*)(tail + 4);  // second Gram-Schmidt pass not needed
+        jd = (int*)(tail + 5);     // step of the cycle, held on the device
+        itd = jd + 1;              // iterations of the solve
+        contd = (int*)(tail + 6);  // the step's decision (host-driven steps)
+        actd = contd + 1;          // the solve still runs (group launches)
+        bnd = tail + 7;            // ||b||
+        V = P->kry.p;
+    }
+    void matvec(const float4* in, float4* out, cudaStream_t st) {
         launch_density_prep(P, in, VecKind::DoubleFloat, P->sig.p, st);
         run_matvec_sorted(P, 7, st);
         launch_output(P, P->phi.p, out, VecKind::DoubleFloat, st);
     }
-    double norm(const float4* w) {
+    double norm(const float4* w, cudaStream_t st) {
         k_norm2_df<<<RG, RB, 0, st>>>(N, w, partial);
-        k_reduce<<<1, RB, 0, st>>>(partial, small);
+        k_reduce<<<1, RB, 0, st>>>(partial, hsum + m + 1);
         count(2);
         double2 h;
-        HFMM_CUDA(cudaMemcpyAsync(&h, small, sizeof(double2), cudaMemcpyDeviceToHost, st));
+        HFMM_CUDA(cudaMemcpyAsync(&h, hsum + m + 1, sizeof(double2), cudaMemcpyDeviceToHost, st));
         host_wait(P, st);
         return std::sqrt(h.x);
     }
-};
-}  // namespace
-
-int run_gmres(hfmm_plan* P, const void* rhs, void* x_out, int* iters, double* relres, cudaStream_t st) {
-    const int64_t N = P->N;
-    const int m = P->cfg.restart;
-    const double tol = P->cfg.tol;
-    const int maxit = P->cfg.max_iter;
-    // workspace (doubles): partials RG (m + 2) complex, hsum m + 2, H (m + 1) m, cs m, sn m,
-    // g m + 1, y m (complex each), coefficients m + 2 (double-float complex), residual pair,
-    // norm, scale
-    const size_t n_part = 2 * (size_t)RG * (m + 2), n_hsum = 2 * (size_t)(m + 2), n_H = 2 * (size_t)(m + 1) * m,
-                 n_cs = 2 * (size_t)m, n_g = 2 * (size_t)(m + 1), n_y = 2 * (size_t)m, n_coef = 2 * (size_t)(m + 2);
-    const size_t n_ws = n_part + n_hsum + n_H + 2 * n_cs + n_g + n_y + n_coef + 8;
-    if (P->kry_m != m) {
-        if (P->gm_exec) {  // the captured step refers to the old workspace
-            cudaGraphExecDestroy(P->gm_exec);
-            P->gm_exec = nullptr;
-        }
-        P->kry.alloc((size_t)(m + 1) * N, nullptr);
-        P->gw.alloc(N, nullptr);
-        P->gx.alloc(N, nullptr);
-        P->gb.alloc(N, nullptr);
-        P->gred.alloc(n_ws, nullptr);
-        P->kry_m = m;
-    }
-    double* ws = P->gred.p;
-    double2* partial = (double2*)ws;
-    double2* hsum = (double2*)(ws + n_part);
-    Arnoldi A;
-    A.H = (double2*)(ws + n_part + n_hsum);
-    A.cs = (double2*)(ws + n_part + n_hsum + n_H);
-    A.sn = A.cs + m;
-    A.g = (double2*)(ws + n_part + n_hsum + n_H + 2 * n_cs);
-    double2* y = (double2*)(ws + n_part + n_hsum + n_H + 2 * n_cs + n_g);
-    float4* coeff = (float4*)(ws + n_part + n_hsum + n_H + 2 * n_cs + n_g + n_y);
-    double* tail = ws + n_part + n_hsum + n_H + 2 * n_cs + n_g + n_y + n_coef;
-    A.res = tail;             // 2 doubles
-    double* nrm = tail + 2;   // 1 double
-    float2* scale = (float2*)(tail + 3);
-    int* skip2 = (int*)(tail + 4);  // second Gram-Schmidt pass not needed
-    int* jd = (int*)(tail + 5);     // step of the cycle, held on the device
-    int* itd = jd + 1;              // iterations of the solve
-    int* contd = (int*)(tail + 6);  // the step's decision (host-driven steps)
-    double* bnd = tail + 7;         // ||b||
-    Ctx c{P, st, N, (unsigned)((N + 255) / 256), partial, hsum, coeff};
-    float4* V = P->kry.p;
-    auto launch_norm = [&](const float4* w, int j1) {  // nrm, scale = 1 / nrm, hsum[j1] = nrm
+    void launch_norm(const float4* w, int j1, cudaStream_t st) {  // nrm, scale = 1 / nrm, hsum[j1] = nrm
         k_norm2_df<<<RG, RB, 0, st>>>(N, w, partial);
         k_norm_finish<<<1, RB, 0, st>>>(partial, j1, hsum, scale, nrm);
-        c.count(2);
-    };
-    // h = V^H w; w -= V h; hsum += h.  The first pass also takes |w|^2 and decides whether the
-    // second pass runs (its kernels return at once when it does not).
-    auto cgs_pass = [&](int nvec, float4* w, bool first) {
-        k_dots_df<<<dim3(RG, (nvec + kDotVecs - 1) / kDotVecs), RB, 0, st>>>(N, V, nvec, w, partial,
-                                                                              first ? nullptr : skip2, first);
-        k_reduce_h<<<nvec, RB, 0, st>>>(partial, coeff, hsum, first ? nullptr : skip2);
-        if (first) {
-            k_reorth_decide<<<1, RB, 0, st>>>(partial, hsum, nvec, skip2);
-            c.count();
-        }
-        k_axpy_df<<<c.nb, 256, sizeof(float4) * nvec, st>>>(N, V, nvec, coeff, -1.f, w, first ? nullptr : skip2);
-        c.count(3);
-    };
+        count(2);
+    }
     // One Arnoldi step with the step index j held on the device (stream s): the matvec of basis
     // vector j, Gram-Schmidt against the j + 1 vectors (the second pass only when the first
     // cancelled), the new basis vector, the rotations and the residual estimate, then the
     // decision to go on (the while node's condition h when use_h).  Grids are sized for the
     // cycle's longest step, so the same launches serve every j.
-    auto step = [&](cudaStream_t s, cudaGraphConditionalHandle h, int use_h) {
+    void step(cudaStream_t s, cudaGraphConditionalHandle h, int use_h) {
         float4* w = P->gw.p;
         const unsigned gy = (unsigned)((m + kDotVecs - 1) / kDotVecs);
-        k_prep_basis<<<c.nb, 256, 0, s>>>(N, P->perm.p, P->wscale.p, V, jd, P->sig.p);
+        k_prep_basis<<<nb, 256, 0, s>>>(N, P->perm.p, P->wscale.p, V, jd, P->sig.p);
         run_matvec_sorted(P, 15, s);  // every stage launched directly (a replay cannot sit in this capture)
         launch_output(P, P->phi.p, w, VecKind::DoubleFloat, s);
         HFMM_CUDA(cudaMemsetAsync(hsum, 0, sizeof(double2) * (m + 1), s));
@@ -541,130 +547,228 @@ int run_gmres(hfmm_plan* P, const void* rhs, void* x_out, int* iters, double* re
             k_dots_df<<<dim3(RG, gy), RB, 0, s>>>(N, V, 0, w, partial, first ? nullptr : skip2, first, jd);
             k_reduce_h<<<m, RB, 0, s>>>(partial, coeff, hsum, first ? nullptr : skip2, jd);
             if (first) k_reorth_decide<<<1, RB, 0, s>>>(partial, hsum, 0, skip2, jd);
-            k_axpy_df<<<c.nb, 256, sizeof(float4) * m, s>>>(N, V, 0, coeff, -1.f, w, first ? nullptr : skip2, jd);
+            k_axpy_df<<<nb, 256, sizeof(float4) * m, s>>>(N, V, 0, coeff, -1.f, w, first ? nullptr : skip2, jd);
         }
         k_norm2_df<<<RG, RB, 0, s>>>(N, w, partial);
         k_norm_finish<<<1, RB, 0, s>>>(partial, 0, hsum, scale, nrm, jd);
-        k_scale_df_dev<<<c.nb, 256, 0, s>>>(N, w, scale, V, jd);
+        k_scale_df_dev<<<nb, 256, 0, s>>>(N, w, scale, V, jd);
         k_givens<<<1, 32, 0, s>>>(0, m, hsum, A, 0.0, jd, bnd);
         k_step_end<<<1, 32, 0, s>>>(A.res, jd, itd, m, maxit, tol, contd, h, use_h);
-        c.count(13);  // prep, 7 Gram-Schmidt kernels, norm, norm finish, scale, rotations, step end
+        count(13);  // prep, 7 Gram-Schmidt kernels, norm, norm finish, scale, rotations, step end
         HFMM_CUDA(cudaGetLastError());
-    };
-    // The whole cycle as one graph launch: a while node whose body is one step, looping on the
-    // device until k_step_end says stop (no host round trip per iteration).  Built once per
-    // plan and restart length; on an adaptive tree, or if building fails (a capture that another
-    // thread invalidated), the host drives the same steps.
-    auto cycle_graph = [&]() -> bool {
-        if (P->adaptive) return false;
-        if (P->gm_exec) return true;
-        MatvecGraph& MG = P->mvg;
-        if (!MG.cap) HFMM_CUDA(cudaStreamCreateWithFlags(&MG.cap, cudaStreamNonBlocking));
-        cudaGraph_t g = nullptr;
-        HFMM_CUDA(cudaGraphCreate(&g, 0));
-        cudaGraphConditionalHandle h;
-        cudaGraphNodeParams cp = {};
-        cudaGraphNode_t node;
-        if (cudaGraphConditionalHandleCreate(&h, g, 1u, cudaGraphCondAssignDefault) != cudaSuccess) {
-            cudaGraphDestroy(g);
-            cudaGetLastError();
-            return false;
-        }
-        cp.type = cudaGraphNodeTypeConditional;
-        cp.conditional.handle = h;
-        cp.conditional.type = cudaGraphCondTypeWhile;
-        cp.conditional.size = 1;
-        if (cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &cp) != cudaSuccess) {
-            cudaGraphDestroy(g);
-            cudaGetLastError();
-            return false;
-        }
-        cudaGraph_t body = cp.conditional.phGraph_out[0];
-        const int64_t l0 = P->launches;
-        bool ok = cudaStreamBeginCaptureToGraph(MG.cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) ==
-                  cudaSuccess;
-        if (ok) {
-            try {
-                step(MG.cap, h, 1);
-            } catch (const HfmmError&) {
-                ok = false;
-            }
-            cudaGraph_t out = nullptr;
-            ok = (cudaStreamEndCapture(MG.cap, &out) == cudaSuccess) && ok;
-        }
-        P->gm_launches = P->launches - l0;
-        P->launches = l0;
-        if (ok) ok = cudaGraphInstantiate(&P->gm_exec, g, 0) == cudaSuccess;
-        cudaGraphDestroy(g);
-        if (!ok) {
-            P->gm_exec = nullptr;
-            cudaGetLastError();  // clears a capture or instantiation error; the host drives the steps
-        }
-        return ok;
-    };
-    k_c64_to_df<<<c.nb, 256, 0, st>>>(N, (const float2*)rhs, P->gb.p);
-    c.count();
-    HFMM_CUDA(cudaMemsetAsync(P->gx.p, 0, sizeof(float4) * N, st));
-    double bnorm = c.norm(P->gb.p);
-    if (bnorm == 0.0) {
-        k_df_to_c64<<<c.nb, 256, 0, st>>>(N, P->gx.p, (float2*)x_out);
-        c.count();
-        host_wait(P, st);
-        *iters = 0;
-        *relres = 0.0;
-        return HFMM_OK;
     }
-    HFMM_CUDA(cudaMemcpyAsync(bnd, &bnorm, sizeof(double), cudaMemcpyHostToDevice, st));
-    HFMM_CUDA(cudaMemsetAsync(itd, 0, sizeof(int), st));
-    // r0 = b (x0 = 0)
-    HFMM_CUDA(cudaMemcpyAsync(P->gw.p, P->gb.p, sizeof(float4) * N, cudaMemcpyDeviceToDevice, st));
-    const bool use_graph = cycle_graph();
-    P->gm_used = use_graph ? 1 : 0;
-    double beta = bnorm;
-    int it = 0;
-    bool converged = false;
-    while (it < maxit && !converged) {
-        // V_0 = r / beta, g = (beta, 0, ...), j = 0
-        launch_norm(P->gw.p, -1);
-        k_scale_df_dev<<<c.nb, 256, 0, st>>>(N, P->gw.p, scale, V);
-        k_cycle_start<<<1, 64, 0, st>>>(m, A, nrm);
-        c.count(2);
-        HFMM_CUDA(cudaMemsetAsync(jd, 0, sizeof(int), st));
-        if (use_graph) {
-            HFMM_CUDA(cudaGraphLaunch(P->gm_exec, st));
-        } else {
-            for (;;) {
-                step(st, cudaGraphConditionalHandle{}, 0);
-                int go = 0;
-                HFMM_CUDA(cudaMemcpyAsync(&go, contd, sizeof(int), cudaMemcpyDeviceToHost, st));
-                host_wait(P, st);
-                if (!go) break;
-            }
+    // b, x = 0, ||b||, r0 = b; false (and done) when b = 0
+    bool start(const void* rhs, cudaStream_t st) {
+        k_c64_to_df<<<nb, 256, 0, st>>>(N, (const float2*)rhs, P->gb.p);
+        count();
+        HFMM_CUDA(cudaMemsetAsync(P->gx.p, 0, sizeof(float4) * N, st));
+        bnorm = norm(P->gb.p, st);
+        it = 0;
+        beta = bnorm;
+        if (bnorm == 0.0) {
+            converged = done = true;
+            return false;
         }
+        HFMM_CUDA(cudaMemcpyAsync(bnd, &bnorm, sizeof(double), cudaMemcpyHostToDevice, st));
+        HFMM_CUDA(cudaMemsetAsync(itd, 0, sizeof(int), st));
+        HFMM_CUDA(cudaMemcpyAsync(P->gw.p, P->gb.p, sizeof(float4) * N, cudaMemcpyDeviceToDevice, st));
+        converged = done = false;
+        return true;
+    }
+    // V_0 = r / beta, g = (beta, 0, ...), j = 0
+    void cycle_begin(cudaStream_t st) {
+        launch_norm(P->gw.p, -1, st);
+        k_scale_df_dev<<<nb, 256, 0, st>>>(N, P->gw.p, scale, V);
+        k_cycle_start<<<1, 64, 0, st>>>(m, A, nrm);
+        count(2);
+        HFMM_CUDA(cudaMemsetAsync(jd, 0, sizeof(int), st));
+    }
+    void host_steps(cudaStream_t st) {
+        for (;;) {
+            step(st, cudaGraphConditionalHandle{}, 0);
+            int go = 0;
+            HFMM_CUDA(cudaMemcpyAsync(&go, contd, sizeof(int), cudaMemcpyDeviceToHost, st));
+            host_wait(P, st);
+            if (!go) break;
+        }
+    }
+    // after the cycle's steps: y = H^{-1} g, x += V y, the true residual and its norm
+    void cycle_end(cudaStream_t st, bool graph) {
         int ji[2];
         HFMM_CUDA(cudaMemcpyAsync(ji, jd, sizeof(ji), cudaMemcpyDeviceToHost, st));
         host_wait(P, st);
         const int jdone = ji[0];
-        if (use_graph) P->launches += (int64_t)jdone * P->gm_launches;
+        if (graph) P->launches += (int64_t)jdone * step_launches;
         it = ji[1];
-        // y = H^{-1} g (upper triangular, FP64, on the device), x += V y
         k_backsolve<<<1, 32, 0, st>>>(jdone, m, A, y, coeff);
-        k_axpy_df<<<c.nb, 256, sizeof(float4) * jdone, st>>>(N, V, jdone, coeff, 1.f, P->gx.p);
-        c.count(2);
-        // true residual r = b - A x
-        c.matvec(P->gx.p, P->gw.p);
-        k_sub_df<<<c.nb, 256, 0, st>>>(N, P->gb.p, P->gw.p, P->gw.p);
-        c.count();
-        beta = c.norm(P->gw.p);
+        k_axpy_df<<<nb, 256, sizeof(float4) * jdone, st>>>(N, V, jdone, coeff, 1.f, P->gx.p);
+        count(2);
+        matvec(P->gx.p, P->gw.p, st);
+        k_sub_df<<<nb, 256, 0, st>>>(N, P->gb.p, P->gw.p, P->gw.p);
+        count();
+        beta = norm(P->gw.p, st);
         converged = beta / bnorm <= tol;
+        done = converged || it >= maxit;
     }
-    k_df_to_c64<<<c.nb, 256, 0, st>>>(N, P->gx.p, (float2*)x_out);
-    c.count();
-    HFMM_CUDA(cudaGetLastError());
-    host_wait(P, st);
-    *iters = it;
-    *relres = beta / bnorm;
-    return converged ? HFMM_OK : HFMM_NOT_CONVERGED;
+    void finish(void* x_out, cudaStream_t st) {
+        k_df_to_c64<<<nb, 256, 0, st>>>(N, P->gx.p, (float2*)x_out);
+        count();
+        HFMM_CUDA(cudaGetLastError());
+        host_wait(P, st);
+    }
+};
+
+// Adds to graph g, for each solver, a while node whose body is one step of that solver
+// (captured on the solver plan's own capture stream).  gated: the loop is opened or closed at
+// each launch by a kernel node before it that copies the solver's device flag into the
+// condition; else the condition starts at 1 at every launch.  False if any part fails.
+bool add_step_loops(cudaGraph_t g, Solver* const* S, int n, bool gated) {
+    for (int i = 0; i < n; ++i) {
+        Solver& s = *S[i];
+        MatvecGraph& MG = s.P->mvg;
+        if (!MG.cap && cudaStreamCreateWithFlags(&MG.cap, cudaStreamNonBlocking) != cudaSuccess) return false;
+        cudaGraphConditionalHandle h;
+        if (cudaGraphConditionalHandleCreate(&h, g, gated ? 0u : 1u, gated ? 0u : cudaGraphCondAssignDefault) !=
+            cudaSuccess)
+            return false;
+        cudaGraphNode_t gate = nullptr;
+        if (gated) {
+            int* act = s.actd;
+            void* args[] = {&h, &act};
+            cudaKernelNodeParams kp = {};
+            kp.func = (void*)k_cond_init;
+            kp.gridDim = dim3(1);
+            kp.blockDim = dim3(1);
+            kp.kernelParams = args;
+            if (cudaGraphAddKernelNode(&gate, g, nullptr, 0, &kp) != cudaSuccess) return false;
+        }
+        cudaGraphNodeParams cp = {};
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = h;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        cudaGraphNode_t node;
+        if (cudaGraphAddNode(&node, g, gate ? &gate : nullptr, nullptr, gate ? 1 : 0, &cp) != cudaSuccess) return false;
+        cudaGraph_t body = cp.conditional.phGraph_out[0];
+        const int64_t l0 = s.P->launches;
+        if (cudaStreamBeginCaptureToGraph(MG.cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) !=
+            cudaSuccess)
+            return false;
+        bool ok = true;
+        try {
+            s.step(MG.cap, h, 1);
+        } catch (const HfmmError&) {
+            ok = false;
+        }
+        cudaGraph_t out = nullptr;
+        ok = (cudaStreamEndCapture(MG.cap, &out) == cudaSuccess) && ok;
+        s.step_launches = s.P->launches - l0;
+        s.P->launches = l0;
+        if (!ok) return false;
+    }
+    return true;
+}
+
+// a graph over the solvers' step loops, instantiated; nullptr (errors cleared) if it cannot be built
+cudaGraphExec_t build_loops(Solver* const* S, int n, bool gated) {
+    cudaGraph_t g = nullptr;
+    if (cudaGraphCreate(&g, 0) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    cudaGraphExec_t ex = nullptr;
+    if (!add_step_loops(g, S, n, gated) || cudaGraphInstantiate(&ex, g, 0) != cudaSuccess) ex = nullptr;
+    cudaGraphDestroy(g);
+    cudaGetLastError();  // a capture another thread invalidated, or an unsupported node: steps from the host
+    return ex;
+}
+
+}  // namespace
+
+int run_gmres(hfmm_plan* P, const void* rhs, void* x_out, int* iters, double* relres, cudaStream_t st) {
+    Solver S;
+    S.init(P);
+    if (!S.start(rhs, st)) {
+        S.finish(x_out, st);
+        *iters = 0;
+        *relres = 0.0;
+        return HFMM_OK;
+    }
+    // The whole cycle as one graph launch: a while node whose body is one step, looping on the
+    // device until the step's last kernel clears its condition (no host round trip per
+    // iteration).  Built once per plan and restart length; on an adaptive tree, or if building
+    // fails, the host drives the same steps.
+    if (!P->adaptive && !P->gm_exec) {
+        Solver* one = &S;
+        P->gm_exec = build_loops(&one, 1, false);
+        P->gm_launches = S.step_launches;
+    }
+    S.step_launches = P->gm_launches;
+    const bool graph = P->gm_exec != nullptr;
+    P->gm_used = graph ? 1 : 0;
+    while (!S.done) {
+        S.cycle_begin(st);
+        if (graph) HFMM_CUDA(cudaGraphLaunch(P->gm_exec, st));
+        else S.host_steps(st);
+        S.cycle_end(st, graph);
+    }
+    S.finish(x_out, st);
+    *iters = S.it;
+    *relres = S.beta / S.bnorm;
+    return S.converged ? HFMM_OK : HFMM_NOT_CONVERGED;
+}
+
+// G independent solves (different plans, one right-hand side each) in lockstep over restart
+// cycles: each cycle of every unfinished solve runs inside one shared graph launch, one gated
+// while node per solve (a finished solve's loop is closed by its gate), so the requests' steps
+// share a launch and proceed side by side on the device; the cycle ends run per solve.
+int run_gmres_group(hfmm_plan* const* plans, int G, const void* const* rhs, void* const* x_out, int* iters,
+                    double* relres, cudaStream_t st) {
+    std::vector<Solver> S((size_t)G);
+    std::vector<Solver*> ptr((size_t)G);
+    bool adaptive = false;
+    for (int g = 0; g < G; ++g) {
+        S[(size_t)g].init(plans[g]);
+        ptr[(size_t)g] = &S[(size_t)g];
+        adaptive |= plans[g]->adaptive;
+        S[(size_t)g].start(rhs[g], st);
+    }
+    cudaGraphExec_t ex = adaptive ? nullptr : build_loops(ptr.data(), G, true);
+    struct Guard {
+        cudaGraphExec_t e;
+        ~Guard() {
+            if (e) cudaGraphExecDestroy(e);
+        }
+    } guard{ex};
+    for (;;) {
+        bool any = false;
+        for (int g = 0; g < G; ++g) any |= !S[(size_t)g].done;
+        if (!any) break;
+        for (int g = 0; g < G; ++g) {
+            Solver& s = S[(size_t)g];
+            const int act = s.done ? 0 : 1;
+            HFMM_CUDA(cudaMemcpyAsync(s.actd, &act, sizeof(int), cudaMemcpyHostToDevice, st));
+            if (!s.done) s.cycle_begin(st);
+        }
+        if (ex) {
+            HFMM_CUDA(cudaGraphLaunch(ex, st));
+        } else {
+            for (int g = 0; g < G; ++g)
+                if (!S[(size_t)g].done) S[(size_t)g].host_steps(st);
+        }
+        for (int g = 0; g < G; ++g)
+            if (!S[(size_t)g].done) S[(size_t)g].cycle_end(st, ex != nullptr);
+    }
+    bool all = true;
+    for (int g = 0; g < G; ++g) {
+        Solver& s = S[(size_t)g];
+        s.finish(x_out[g], st);
+        if (iters) iters[g] = s.it;
+        if (relres) relres[g] = s.bnorm > 0.0 ? s.beta / s.bnorm : 0.0;
+        all &= s.converged;
+        s.P->gm_used = ex ? 1 : 0;
+    }
+    return all ? HFMM_OK : HFMM_NOT_CONVERGED;
 }
 
 // ============================================================== R systems in lockstep

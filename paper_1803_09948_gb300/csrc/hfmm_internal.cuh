@@ -444,6 +444,9 @@ void m2l_ts_launch(const TsTile* tiles, int64_t ntiles, int max_chunks, const Ts
 
 // ---------------------------------------------------------------- GMRES
 int run_gmres(hfmm_plan* P, const void* rhs, void* x, int* iters, double* relres, cudaStream_t st);
+// G single right-hand-side solves on distinct plans, cycles of all of them in one graph launch
+int run_gmres_group(hfmm_plan* const* plans, int G, const void* const* rhs, void* const* x_out, int* iters,
+                    double* relres, cudaStream_t st);
 // R (2..64) systems with the same operator in lockstep: one batched matvec per iteration,
 // an independent Arnoldi process per right-hand side. rhs, x: device complex64 [R][N].
 int run_gmres_batched(hfmm_plan* P, const float2* rhs, float2* x, int R, int* iters, double* relres,

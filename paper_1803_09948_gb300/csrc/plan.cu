@@ -1260,6 +1260,22 @@ int hfmm_matvec_parts(hfmm_plan* P, const void* density, void* potential, int nr
     HFMM_GUARD_END
 }
 
+int hfmm_solve_group(hfmm_plan* const* plans, int G, const void* const* rhs, void* const* x_out, int* iters_out,
+                     double* relres_out, void* stream) {
+    if (!plans || !rhs || !x_out || G < 1 || G > HFMM_GROUP_MAX) return HFMM_E_INVALID;
+    for (int g = 0; g < G; ++g) {
+        if (!plans[g] || !rhs[g] || !x_out[g]) return HFMM_E_INVALID;
+        for (int q = 0; q < g; ++q)
+            if (plans[q] == plans[g]) {
+                g_last_error = "hfmm_solve_group: a plan appears twice (each solve needs its own plan)";
+                return HFMM_E_INVALID;
+            }
+    }
+    HFMM_GUARD_BEGIN
+    return run_gmres_group(plans, G, rhs, x_out, iters_out, relres_out, (cudaStream_t)stream);
+    HFMM_GUARD_END
+}
+
 int hfmm_solver_info(const hfmm_plan* P, int* cycle_graph) {
     if (!P || !cycle_graph) return HFMM_E_INVALID;
     *cycle_graph = P->gm_used;

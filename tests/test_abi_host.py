@@ -76,6 +76,9 @@ def test_invalid_arguments_are_rejected_on_the_host():
     lib = pkg.lib()
     assert lib.hfmm_matvec(None, None, None, 1, None) == pkg.HFMM_E_INVALID
     assert lib.hfmm_matvec_host(None, None, None, 1, None) == pkg.HFMM_E_INVALID
+    assert lib.hfmm_solve_group(None, 0, None, None, None, None, None) == pkg.HFMM_E_INVALID
+    assert lib.hfmm_solve_group(None, 2, None, None, None, None, None) == pkg.HFMM_E_INVALID
+    assert lib.hfmm_solver_info(None, None) == pkg.HFMM_E_INVALID
     assert lib.hfmm_solve(None, None, None, 1, None, None, None) == pkg.HFMM_E_INVALID
     assert lib.hfmm_num_points(None) == -1
     lib.hfmm_plan_destroy(None)  # no-op

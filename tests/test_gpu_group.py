@@ -1,0 +1,96 @@
+"""Several requests' solves in one shared launch: hfmm_solve_group runs G single right-hand-side
+GMRES solves on distinct plans (different meshes and wavenumbers) in lockstep over restart
+cycles, each cycle of all unfinished solves inside one graph launch with a gated while node
+per solve.  Each solve must equal the same plan's solve alone (same kernels in the same order
+on its own data: identical iteration counts, solutions equal to 1e-6), a solve that stops
+early must not be stepped again, and a zero right-hand side returns zero."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_1803_09948_gb300 as pkg
+import synthetic
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import __graft_entry__
+
+    __graft_entry__.build()
+
+
+def _rhs(plan, d):
+    b = torch.empty(plan.n, dtype=torch.complex64, device="cuda")
+    plan.rhs_planewave(d, b)
+    return b
+
+
+def test_group_equals_solves_alone():
+    specs = [("sphere", 8, 2.0, {}), ("ellipsoid", 7, 3.0, {}), ("star", 8, 1.5, {"max_iter": 6}),
+             ("sphere", 6, 4.0, {"restart": 10})]
+    plans, rhs = [], []
+    try:
+        for q, (shape, nu, k, cfg) in enumerate(specs):
+            V, F = synthetic.serving_shape(shape, nu, seed=30 + q)
+            plans.append(pkg.Plan(V, F, k, **cfg))
+            rhs.append(_rhs(plans[-1], [0.0, 0.6, 0.8]))
+        rhs.append(torch.zeros_like(rhs[0]))  # a zero right-hand side on a fifth plan
+        V, F = synthetic.serving_shape("sphere", 8, seed=30)
+        plans.append(pkg.Plan(V, F, 2.0))
+        alone = []
+        for p, b in zip(plans, rhs):
+            x = torch.empty_like(b)
+            st, it, rr = p.solve(b, x)
+            alone.append((st, it[0], rr[0], x.cpu().numpy()))
+        xs = [torch.empty_like(b) for b in rhs]
+        st, its, rrs = pkg.hfmm_solve_group(plans, rhs, xs)
+        torch.cuda.synchronize()
+        assert st == pkg.HFMM_NOT_CONVERGED  # the star solve stops at its 6-iteration limit
+        for g, (sa, ia, ra, xa) in enumerate(alone):
+            assert its[g] == ia, (g, its[g], ia)
+            xg = xs[g].cpu().numpy()
+            if g == len(plans) - 1:
+                assert ia == 0 and not np.any(xg)
+                continue
+            assert np.linalg.norm(xg - xa) <= 1e-6 * np.linalg.norm(xa), g
+            assert abs(rrs[g] - ra) <= 1e-6 * max(ra, 1e-12) + 1e-12
+        assert its[2] == 6 and alone[2][0] == pkg.HFMM_NOT_CONVERGED
+        assert all(p.solver_info()["cycle_graph"] == 1 for p in plans[:-1])
+    finally:
+        for p in plans:
+            p.close()
+
+
+def test_group_solution_against_the_oracle():
+    """One member of a group against the oracle's dense operator (residual <= 2e-4)."""
+    V, F = synthetic.serving_shape("ellipsoid", 6, seed=40)
+    a = pkg.Plan(V, F, 2.5, tol=1e-5)
+    V2, F2 = synthetic.serving_shape("star", 6, seed=41)
+    b2 = pkg.Plan(V2, F2, 1.5, tol=1e-5)
+    try:
+        r1, r2 = _rhs(a, [0.0, 0.0, 1.0]), _rhs(b2, [1.0, 0.0, 0.0])
+        x1, x2 = torch.empty_like(r1), torch.empty_like(r2)
+        st, its, rrs = pkg.hfmm_solve_group([a, b2], [r1, r2], [x1, x2])
+        assert st == pkg.HFMM_OK
+        X, _, _ = oracle.points(V, F)
+        Z = oracle.dense_Z(V, F, 2.5, oracle.near_radius(V, F, 1.0))
+        bb = oracle.plane_wave(X, 2.5, (0, 0, 1))
+        xg = x1.cpu().numpy().astype(np.complex128)
+        assert np.linalg.norm(Z @ xg - bb) <= 2e-4 * np.linalg.norm(bb)
+    finally:
+        a.close()
+        b2.close()
+
+
+def test_group_refuses_a_repeated_plan():
+    V, F = synthetic.sphere_mesh(2)
+    p = pkg.Plan(V, F, 1.0)
+    try:
+        b = _rhs(p, [0.0, 0.0, 1.0])
+        with pytest.raises(pkg.HfmmError):
+            pkg.hfmm_solve_group([p, p], [b, b], [torch.empty_like(b), torch.empty_like(b)])
+    finally:
+        p.close()
