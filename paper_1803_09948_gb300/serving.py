@@ -16,6 +16,13 @@ until its solve has finished, and are then released.
     budget is what bounds it), so the plan building of some requests (host
     octree and lists, device operator and correction kernels) overlaps the
     solves of others and their kernels share the device.
+  * Shared launches: single right-hand-side requests of at most `group_n_max`
+    points (200k) that arrive within `group_wait_s` (50 ms) of the first of them
+    are served as one group (up to `group_max`, 8): their plans are built side
+    by side, then hfmm_solve_group advances all their GMRES solves together,
+    every restart cycle of all unfinished solves inside one graph launch (a
+    gated while node per solve).  Requests keep their own admission (memory,
+    slot) and records.
   * Multi-RHS requests use the library's lockstep solver (one batched,
     graph-captured matvec per GMRES iteration for all directions).
 
@@ -146,10 +153,69 @@ def gpu_executor(restart: int = 30, tol: float = 1e-4, keep_solution: bool = Fal
     return run
 
 
+def gpu_group_executor(restart: int = 30, tol: float = 1e-4, keep_solution: bool = False, max_iter: int = 1000,
+                       max_building: int = 8):
+    """Executor for a group of single right-hand-side requests: their plans are built (at most
+    max_building at once), then hfmm_solve_group advances all their GMRES solves together, each
+    restart cycle of every unfinished solve inside one shared graph launch.  Returns a function
+    (requests, stream) -> list of per-request dicts (as gpu_executor's)."""
+    import concurrent.futures as cf
+
+    import torch
+
+    from . import Plan, hfmm_solve_group
+
+    def run(reqs, stream):
+        t0 = time.perf_counter()
+        plans = [None] * len(reqs)
+        build_s = [0.0] * len(reqs)
+
+        def build(q):
+            t = time.perf_counter()
+            with torch.cuda.stream(stream):
+                plans[q] = Plan(reqs[q]["V"], reqs[q]["F"], reqs[q]["k"], stream=stream, restart=restart, tol=tol,
+                                max_iter=max_iter)
+            build_s[q] = time.perf_counter() - t
+
+        try:
+            with cf.ThreadPoolExecutor(max_workers=max(1, min(max_building, len(reqs)))) as ex:
+                list(ex.map(build, range(len(reqs))))
+            stream.synchronize()
+            t1 = time.perf_counter()
+            with torch.cuda.stream(stream):
+                bs, xs = [], []
+                for p, r in zip(plans, reqs):
+                    b = torch.empty(p.n, dtype=torch.complex64, device="cuda")
+                    p.rhs_planewave(np.asarray(r["dirs"]).reshape(1, 3), b, stream=stream)
+                    bs.append(b)
+                    xs.append(torch.empty_like(b))
+                status, its, rrs = hfmm_solve_group(plans, bs, xs, stream=stream)
+                hosts = [x.to("cpu", non_blocking=False) for x in xs]
+            t2 = time.perf_counter()
+            outs = []
+            for q, (p, r) in enumerate(zip(plans, reqs)):
+                ok = rrs[q] <= tol
+                o = {"status": 0 if ok else 1, "iterations": [int(its[q])], "relres": [float(rrs[q])],
+                     "n_points": p.n, "build_s": build_s[q], "group_build_s": t1 - t0, "solve_s": t2 - t1,
+                     "device_bytes": p.info()["device_bytes"], "response_bytes": hosts[q].numel() * 8,
+                     "group_size": len(reqs)}
+                if keep_solution:
+                    o["x"] = hosts[q].numpy().reshape(1, p.n)
+                outs.append(o)
+            return outs
+        finally:
+            for p in plans:
+                if p is not None:
+                    p.close()
+
+    return run
+
+
 class ServingEngine:
     def __init__(self, executor=None, max_inflight: int = 64, budget_bytes: int | None = None,
                  budget_frac: float = 0.8, restart: int = 30, tol: float = 1e-4, stream_factory=None,
-                 workers: int | None = None, max_iter: int = 1000):
+                 workers: int | None = None, max_iter: int = 1000, group_executor=None, group_max: int = 8,
+                 group_n_max: int = 200_000, group_wait_s: float = 0.05):
         if budget_bytes is None:
             import torch
 
@@ -158,6 +224,15 @@ class ServingEngine:
         self.max_inflight = int(workers if workers is not None else max_inflight)  # slots
         self.restart = int(restart)
         self.executor = executor if executor is not None else gpu_executor(restart, tol, max_iter=max_iter)
+        # single right-hand-side requests of at most group_n_max points that arrive within
+        # group_wait_s of each other are solved together (up to group_max): one shared launch per
+        # restart cycle for all of them; group_max = 1 turns grouping off
+        if group_executor is None and executor is None and group_max > 1:
+            group_executor = gpu_group_executor(restart, tol, max_iter=max_iter)
+        self.group_executor = group_executor
+        self.group_max = int(group_max)
+        self.group_n_max = int(group_n_max)
+        self.group_wait_s = float(group_wait_s)
         if stream_factory is None:
             def stream_factory():
                 import torch
@@ -192,6 +267,43 @@ class ServingEngine:
             with rec_lock:
                 records.append(rec)
 
+        class Group:  # single right-hand-side requests collected for one group solve
+            def __init__(self):
+                self.members = []  # (request, arrival time, estimate)
+                self.open = True
+                self.full = threading.Event()
+
+        group_lock = threading.Lock()
+        current = [None]
+
+        def serve_group(g, stream):
+            g.full.wait(self.group_wait_s)  # the collection window (or until the group is full)
+            with group_lock:
+                g.open = False
+            t_start = time.perf_counter()
+            reqs_g = [m[0] for m in g.members]
+            try:
+                outs = self.group_executor(reqs_g, stream)
+                err = None
+            except Exception as e:  # the group fails; the server goes on
+                outs, err = [{} for _ in reqs_g], str(e)
+            finally:
+                for m in g.members:
+                    self.admission.release(m[2])
+                    slots.release()
+            t_done = time.perf_counter()
+            for (r, t_arrive, est), out in zip(g.members, outs):
+                rec = {"id": r.get("id"), "arrival_s": t_arrive - t0, "nrhs": r["nrhs"], "estimate_bytes": est}
+                rec.update(out)
+                if err is not None:
+                    rec.update(status="error", error=err)
+                else:
+                    rec["status"] = "ok" if out.get("status", 0) == 0 else "not converged"
+                rec.update(start_s=t_start - t0, done_s=t_done - t0, wait_s=t_start - t_arrive,
+                           latency_s=t_done - t_arrive)
+                with rec_lock:
+                    records.append(rec)
+
         # the dispatcher: requests in arrival order; each starts as soon as a slot and its
         # memory are free (admission in order, so a large request is not overtaken)
         for r in reqs:
@@ -211,7 +323,21 @@ class ServingEngine:
                                     "estimate_bytes": est, "status": "rejected",
                                     "done_s": time.perf_counter() - t0})
                 continue
-            th = threading.Thread(target=serve, args=(r, t_arrive, est, self.stream_factory()))
+            if (self.group_executor is not None and self.group_max > 1 and r["nrhs"] == 1 and
+                    len(r["F"]) * 3 <= self.group_n_max):
+                with group_lock:
+                    g = current[0]
+                    fresh = g is None or not g.open or len(g.members) >= self.group_max
+                    if fresh:
+                        g = current[0] = Group()
+                    g.members.append((r, t_arrive, est))
+                    if len(g.members) >= self.group_max:
+                        g.full.set()
+                if not fresh:
+                    continue
+                th = threading.Thread(target=serve_group, args=(g, self.stream_factory()))
+            else:
+                th = threading.Thread(target=serve, args=(r, t_arrive, est, self.stream_factory()))
             th.start()
             running.append(th)
         for th in running:

@@ -88,3 +88,27 @@ def test_served_solutions_match_the_oracle():
             assert np.linalg.norm(Z @ x - b) <= 2e-4 * np.linalg.norm(b), (r["id"], q)
             x_lu = np.linalg.solve(Z, b)
             assert np.linalg.norm(x - x_lu) <= 2e-2 * np.linalg.norm(x_lu), (r["id"], q)
+
+
+def test_grouped_requests_equal_requests_alone():
+    """Single right-hand-side requests arriving together are served as one group solve (every
+    restart cycle of all of them in one graph launch); each one's solution equals the same
+    request served alone, within 2 cond(Z) x 1e-5 (cond(Z) <= 100 here)."""
+    specs = [("sphere", 8, 2.0), ("ellipsoid", 7, 3.0), ("star", 8, 1.5), ("sphere", 6, 1.0)]
+    reqs = []
+    for q, (shape, nu, k) in enumerate(specs):
+        V, F = synthetic.serving_shape(shape, nu, seed=50 + q)
+        dirs = np.asarray(synthetic.fibonacci_directions(1, seed=q)).reshape(1, 3)
+        reqs.append({"id": q, "arrival_s": 0.001 * q, "V": V, "F": F, "k": k, "nrhs": 1, "dirs": dirs})
+    ex = serving.gpu_executor(restart=30, tol=1e-5, keep_solution=True)
+    gx = serving.gpu_group_executor(restart=30, tol=1e-5, keep_solution=True)
+    recs, summ = serving.ServingEngine(executor=ex, group_executor=gx, group_max=8, group_wait_s=0.2,
+                                       restart=30).run(reqs)
+    assert summ["ok"] == len(specs)
+    got = {r["id"]: r for r in recs}
+    assert all(got[r["id"]]["group_size"] == len(specs) for r in reqs)
+    for r in reqs:
+        alone, s1 = serving.ServingEngine(executor=ex, max_inflight=1, group_max=1, restart=30).run([dict(r)])
+        assert s1["ok"] == 1
+        xa, xg = alone[0]["x"].astype(np.complex128), got[r["id"]]["x"].astype(np.complex128)
+        assert np.linalg.norm(xg[0] - xa[0]) <= 2e-3 * np.linalg.norm(xa[0]), r["id"]

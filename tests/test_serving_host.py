@@ -63,6 +63,32 @@ def test_memory_not_a_worker_count_bounds_concurrency():
     assert summ["makespan_s"] < 0.35  # two waves of 0.1 s, not twelve
 
 
+def test_single_rhs_requests_are_grouped():
+    """Small single right-hand-side requests arriving together are served as groups of at most
+    group_max (one group solve each); a multi-RHS request runs on its own; every request keeps
+    its own record, and its latency includes the collection window."""
+    log, lock = [], threading.Lock()
+    groups = []
+
+    def group_exec(reqs, stream):
+        with lock:
+            groups.append([r["id"] for r in reqs])
+        time.sleep(0.05)
+        return [{"status": 0, "iterations": [3], "relres": [1e-5], "build_s": 0.0, "solve_s": 0.05,
+                 "group_size": len(reqs)} for _ in reqs]
+
+    eng = serving.ServingEngine(executor=_fake_executor(log, lock, 0.05), group_executor=group_exec, group_max=4,
+                                group_wait_s=0.05, budget_bytes=10 ** 12, restart=30, stream_factory=lambda: None)
+    reqs = [_req(i, 0.002 * i, 1000) for i in range(6)] + [_req(6, 0.003, 1000, nrhs=3)]
+    recs, summ = eng.run(reqs)
+    assert summ["ok"] == 7
+    assert sorted(len(g) for g in groups) == [2, 4] and sorted(sum(groups, [])) == list(range(6))
+    by = {r["id"]: r for r in recs}
+    assert [e[1] for e in log if e[0] == "start"] == [6]  # the multi-RHS request alone
+    for i in range(6):
+        assert by[i]["group_size"] in (2, 4) and by[i]["latency_s"] >= 0.05
+
+
 def test_oversized_request_is_rejected_and_others_served():
     log, lock = [], threading.Lock()
     eng = serving.ServingEngine(executor=_fake_executor(log, lock, 0.01), max_inflight=2,
