@@ -333,7 +333,8 @@ def run_serving(args):
         V, F = synthetic.serving_shape(sp["shape"], sp["nu"], sp["seed"])
         dirs = np.asarray(synthetic.fibonacci_directions(sp["nrhs"], seed=sp["seed"] % 100000)).reshape(-1, 3)
         reqs.append(dict(sp, V=V, F=F, dirs=dirs))
-    eng = serving.ServingEngine(max_inflight=args.serve_slots, restart=30, tol=1e-4, max_iter=args.serve_maxiter)
+    eng = serving.ServingEngine(max_inflight=args.serve_slots, restart=30, tol=1e-4, max_iter=args.serve_maxiter,
+                                group_max=args.serve_group)
     clocks = ClockSampler(0)
     clocks.start()
     records, summ = eng.run(reqs)
@@ -346,12 +347,14 @@ def run_serving(args):
                                f"star geodesic meshes, N log-uniform in [10k, {args.serve_nmax}], k uniform in "
                                f"[1, {args.serve_kmax}], 1-16 plane-wave right-hand sides, GMRES(30) to 1e-4 "
                                f"(at most {args.serve_maxiter} iterations)",
-                   "slots": args.serve_slots, "budget": "80% of device memory (admission by memory, in arrival order)"},
+                   "slots": args.serve_slots, "budget": "80% of device memory (admission by memory, in arrival order)",
+                   "groups": "single-RHS requests of <= 200k points arriving within 50 ms: up to 8 per group solve, "
+                             "one shared graph launch per restart cycle" if args.serve_group > 1 else "off"},
         "latency_s": {"p50": summ["latency_p50_s"], "p99": summ["latency_p99_s"], "mean": summ["latency_mean_s"]},
         "serving": summ,
         "requests": [dict({k_: r.get(k_) for k_ in ("id", "n_points", "nrhs", "status", "latency_s", "wait_s",
                                                     "build_s", "solve_s", "iterations", "error",
-                                                    "estimate_bytes", "device_bytes")},
+                                                    "estimate_bytes", "device_bytes", "group_size")},
                           k=next(q["k"] for q in reqs if q["id"] == r["id"]), shape=next(q["shape"] for q in reqs if q["id"] == r["id"]))
                      for r in sorted(records, key=lambda r: r["id"])],
         "clocks": clk,
@@ -545,6 +548,7 @@ def main():
     ap.add_argument("--serve-kmax", type=float, default=30.0)
     ap.add_argument("--serve-slots", type=int, default=64, help="most requests in flight (memory admits first)")
     ap.add_argument("--serve-maxiter", type=int, default=300, help="GMRES iteration cap per request")
+    ap.add_argument("--serve-group", type=int, default=8, help="most single-RHS requests per group solve (1: off)")
     ap.add_argument("--nrhs", type=int, default=1,
                     help="> 1: batched plane-wave right-hand sides in one graph-captured matvec per step")
     args = ap.parse_args()

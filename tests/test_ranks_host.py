@@ -67,6 +67,6 @@ def test_single_gpu_arms_return_on_other_ranks(arm, monkeypatch, capsys):
     monkeypatch.setenv("RANK", "1")
     monkeypatch.setenv("LOCAL_RANK", "1")
     args = SimpleNamespace(workload="sphere_655360", steps=2, warmup=1, serve=4, serve_nmax=20000, serve_kmax=2.0,
-                           serve_slots=1, refine_pmin=12, restart=0)
+                           serve_slots=1, serve_group=1, refine_pmin=12, restart=0)
     assert getattr(bench, arm)(args) is None
     assert capsys.readouterr().out == ""
