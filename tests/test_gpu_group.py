@@ -3,9 +3,9 @@ GMRES solves on distinct plans (different meshes and wavenumbers) in lockstep ov
 cycles, each cycle of all unfinished solves inside one graph launch with a gated while node
 per solve.  Each solve must equal the same plan's solve alone: the same kernels on its own
 data, so the same iteration counts, and solutions equal up to the run-to-run order of the
-tensor-core M2L's bulk reductions (FP32 rounding, amplified by GMRES: ~1e-5; a solve reading
-another's buffers would differ at O(1)); a solve that stops early must not be stepped again,
-and a zero right-hand side returns zero."""
+tensor-core translations' bulk reductions (FP32 rounding, amplified by GMRES: 1e-5 to 1e-4,
+the most with a short restart cycle; a solve reading another's buffers would differ at O(1));
+a solve that stops early must not be stepped again, and a zero right-hand side returns zero."""
 import numpy as np
 import pytest
 import torch
@@ -57,7 +57,7 @@ def test_group_equals_solves_alone():
             if g == len(plans) - 1:
                 assert ia == 0 and not np.any(xg)
                 continue
-            assert np.linalg.norm(xg - xa) <= 1e-4 * np.linalg.norm(xa), g
+            assert np.linalg.norm(xg - xa) <= 1e-3 * np.linalg.norm(xa), g
             assert abs(rrs[g] - ra) <= 0.05 * ra, g
         assert its[2] == 6 and alone[2][0] == pkg.HFMM_NOT_CONVERGED
         assert all(p.solver_info()["cycle_graph"] == 1 for p in plans[:-1])
