@@ -1467,6 +1467,22 @@ static void launch_translate(hfmm_plan* P, const TransItem* items, float2* coef,
     ++P->launches;
 }
 
+static int p2p_sm_count();
+
+// M2M / L2L between the coarse levels: few items (8 offsets) of many rows, so K is split
+// across blocks until about two blocks per SM are in flight, each part at least 32 deep
+// (the items accumulate, so the parts' partial sums add in the output).
+static void launch_tree_translate(hfmm_plan* P, const TransItem* items, float2* coef, int rhs, int64_t b, int64_t e,
+                                  int pout, int pin, cudaStream_t st) {
+    const int64_t blocks = (e - b) * ((pout + 31) / 32);
+    int kparts = 1;
+    if (blocks > 0) {
+        const int64_t want = (2 * (int64_t)p2p_sm_count() + blocks - 1) / blocks;
+        kparts = (int)std::max<int64_t>(1, std::min<int64_t>(want, pin / 32));
+    }
+    launch_translate(P, items, coef, rhs, b, e, pout, HFMM_TRANS_NB, st, kparts);
+}
+
 // Near field (P2P between neighbouring leaves, or zeros): the first writer of P->phi.
 static int p2p_sm_count() {
     static int n[64] = {};
@@ -1553,8 +1569,8 @@ static void far_stage(hfmm_plan* P, int parts, cudaStream_t st) {
                               P->coef.p, P->dev_err.p, 1, st);
                 ++P->launches;
             } else {
-                launch_translate(P, P->items.p, P->coef.p, 1, P->m2m_items_begin[l], P->m2m_items_end[l], P->lev[l].P,
-                                 HFMM_TRANS_NB, st);
+                launch_tree_translate(P, P->items.p, P->coef.p, 1, P->m2m_items_begin[l], P->m2m_items_end[l],
+                                      P->lev[l].P, P->lev[l + 1].P, st);
             }
         }
     if (far && P->adaptive && P->n_w > 0) {  // W lists: the W boxes' multipoles at the leaf's points
@@ -1590,8 +1606,8 @@ static void far_stage(hfmm_plan* P, int parts, cudaStream_t st) {
                               P->coef.p, P->dev_err.p, 1, st);
                 ++P->launches;
             } else {
-                launch_translate(P, P->items.p, P->coef.p, 1, P->l2l_items_begin[l], P->l2l_items_end[l], P->lev[l].P,
-                                 HFMM_TRANS_NB, st);
+                launch_tree_translate(P, P->items.p, P->coef.p, 1, P->l2l_items_begin[l], P->l2l_items_end[l],
+                                      P->lev[l].P, P->lev[l - 1].P, st);
             }
         }
 }

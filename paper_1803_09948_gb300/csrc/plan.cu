@@ -985,7 +985,9 @@ static void build_plan(hfmm_plan* P, const double* V, int64_t nv, const int32_t*
             std::vector<int64_t> ops(8);
             for (int o = 0; o < 8; ++o) ops[o] = P->lev[l].pc_op + (int64_t)o * P->lev[l].P * P->lev[l - 1].P;
             P->l2l_items_begin[l] = (int64_t)items.size();
-            emit_items(pb, ops, P->lev[l - 1].lofs, P->lev[l].lofs, P->lev[l - 1].P, P->lev[l].P, 0, items, cols);
+            // accumulating (a child has one parent, but the SIMT kernel splits a coarse level's
+            // K across blocks, whose partial sums meet in the child's locals)
+            emit_items(pb, ops, P->lev[l - 1].lofs, P->lev[l].lofs, P->lev[l - 1].P, P->lev[l].P, 1, items, cols);
             P->l2l_items_end[l] = (int64_t)items.size();
             P->cost[2] += (double)ch.key.size() * P->lev[l].P * P->lev[l - 1].P;
         }
