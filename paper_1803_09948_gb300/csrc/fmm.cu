@@ -304,13 +304,14 @@ __global__ void __launch_bounds__(128) k_p2p_staged(const int32_t* __restrict__ 
 //   sq[2q]   = {x_2q, x_2q+1, y_2q, y_2q+1},  sq[2q+1] = {z_2q, z_2q+1, Re s_2q, Re s_2q+1},
 //   sim[q]   = {Im s_2q, Im s_2q+1}
 // (self leaf first, each of the two segments padded to an even length with a zero-density
-// source far away).  A thread holds one target and evaluates both sources of a pair at once
-// with packed FP32x2 arithmetic (fma.rn.f32x2 and friends), walking every S-th pair; the S
-// threads that share a target meet in shared memory.  The complex multiply-add is kept as
+// source far away).  A thread holds kPkTargets targets and evaluates both sources of a pair
+// at once for each of them with packed FP32x2 arithmetic (fma.rn.f32x2 and friends), walking
+// every S-th pair; the S threads that share a target meet in shared memory.  The complex multiply-add is kept as
 // four real accumulators (Re s Re G, Im s Im G, Re s Im G, Im s Re G), so it needs no
 // negated operand.  Same kernel (cos, sinc polynomials in u = (kR)^2, hardware rsqrt) and
 // the same j != i rule as the staged kernel above.
 constexpr int kPkThreads = 128;
+constexpr int kPkTargets = 2;  // targets per thread
 constexpr float kPkPad = 64.0f;  // padding sources sit at (64, 64, 64) (scaled units): u stays finite
 
 __device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
@@ -352,6 +353,7 @@ __device__ __forceinline__ void pk_pair(const float4 xy, const float4 zr, float2
     D = __ffma2_rn(si, re, D);
 }
 
+template <int TPT>
 __global__ void __launch_bounds__(kPkThreads) k_p2p_packed(const int32_t* __restrict__ leaf_start,
                                                            const int4* __restrict__ leaf_ijk,
                                                            const int32_t* __restrict__ nbr_ptr,
@@ -362,7 +364,7 @@ __global__ void __launch_bounds__(kPkThreads) k_p2p_packed(const int32_t* __rest
     extern __shared__ float4 sq[];                                   // [2 cap_pairs]
     float2* sim = reinterpret_cast<float2*>(sq + 2 * cap_pairs);    // [cap_pairs]
     __shared__ NbrTable T;
-    __shared__ float2 s_red[kPkThreads];
+    __shared__ float2 s_red[TPT][kPkThreads];
     const int b = blockIdx.x, tid = threadIdx.x;
     if (tid < 32) build_nbr_table(b, leaf_start, leaf_ijk, nbr_ptr, nbr, shift, true, T);
     __syncthreads();
@@ -394,34 +396,69 @@ __global__ void __launch_bounds__(kPkThreads) k_p2p_packed(const int32_t* __rest
         sfi[2 * pq + h] = si;
     }
     __syncthreads();
-    const int TT = min(nself, kPkThreads);  // target slots per round
-    const int S = kPkThreads / max(TT, 1);  // threads sharing a target
+    // TPT targets per thread (slot, slot + TT, ...): every source pair read from shared memory
+    // serves all of them, so the loads and the loop's index work are shared
+    const int TT = min((nself + TPT - 1) / TPT, kPkThreads);  // target slots per round
+    const int S = kPkThreads / max(TT, 1);                     // threads sharing a slot
     const int slot = tid % max(TT, 1), sp = tid / max(TT, 1);
     const int i0 = __ldg(leaf_start + b);
-    for (int t0 = 0; t0 < nself; t0 += TT) {
-        const int it = t0 + slot;
-        float ar = 0.f, ai = 0.f;
-        if (sp < S && it < nself) {
-            const float* tr = sf + 8 * (it >> 1) + (it & 1);
-            const float2 ntx = f2(-tr[0]), nty = f2(-tr[2]), ntz = f2(-tr[4]);
-            float2 A = f2(0.f), B = f2(0.f), C = f2(0.f), D = f2(0.f);
-            int q = sp;
-            for (; q < qself; q += S) pk_pair<true>(sq[2 * q], sq[2 * q + 1], sim[q], ntx, nty, ntz, 2 * q - it, A, B, C, D);
-#pragma unroll 2
-            for (; q < npair; q += S) pk_pair<false>(sq[2 * q], sq[2 * q + 1], sim[q], ntx, nty, ntz, 0, A, B, C, D);
-            ar = (A.x + A.y) - (B.x + B.y);
-            ai = (C.x + C.y) + (D.x + D.y);
+    for (int t0 = 0; t0 < nself; t0 += TT * TPT) {
+        int it[TPT];
+        float ar[TPT], ai[TPT];
+#pragma unroll
+        for (int k = 0; k < TPT; ++k) {
+            it[k] = t0 + slot + k * TT;
+            ar[k] = ai[k] = 0.f;
         }
-        s_red[tid] = make_float2(ar, ai);
-        __syncthreads();
-        if (sp == 0 && it < nself) {
-            float2 acc = s_red[slot];
-            for (int r = 1; r < S; ++r) {
-                const float2 v = s_red[slot + r * TT];
-                acc.x += v.x;
-                acc.y += v.y;
+        if (sp < S && it[0] < nself) {
+            float2 ntx[TPT], nty[TPT], ntz[TPT], A[TPT], B[TPT], C[TPT], D[TPT];
+            int ik[TPT];  // staged index of each target (a missing one repeats the first)
+#pragma unroll
+            for (int k = 0; k < TPT; ++k) {
+                ik[k] = it[k] < nself ? it[k] : it[0];
+                const float* tr = sf + 8 * (ik[k] >> 1) + (ik[k] & 1);
+                ntx[k] = f2(-tr[0]);
+                nty[k] = f2(-tr[2]);
+                ntz[k] = f2(-tr[4]);
+                A[k] = B[k] = C[k] = D[k] = f2(0.f);
             }
-            phi[i0 + it] = acc;
+            int q = sp;
+            for (; q < qself; q += S) {
+                const float4 xy = sq[2 * q], zr = sq[2 * q + 1];
+                const float2 si = sim[q];
+#pragma unroll
+                for (int k = 0; k < TPT; ++k)
+                    pk_pair<true>(xy, zr, si, ntx[k], nty[k], ntz[k], 2 * q - ik[k], A[k], B[k], C[k], D[k]);
+            }
+#pragma unroll 2
+            for (; q < npair; q += S) {
+                const float4 xy = sq[2 * q], zr = sq[2 * q + 1];
+                const float2 si = sim[q];
+#pragma unroll
+                for (int k = 0; k < TPT; ++k)
+                    pk_pair<false>(xy, zr, si, ntx[k], nty[k], ntz[k], 0, A[k], B[k], C[k], D[k]);
+            }
+#pragma unroll
+            for (int k = 0; k < TPT; ++k) {
+                ar[k] = (A[k].x + A[k].y) - (B[k].x + B[k].y);
+                ai[k] = (C[k].x + C[k].y) + (D[k].x + D[k].y);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < TPT; ++k) s_red[k][tid] = make_float2(ar[k], ai[k]);
+        __syncthreads();
+        if (sp == 0) {
+#pragma unroll
+            for (int k = 0; k < TPT; ++k)
+                if (it[k] < nself) {
+                    float2 acc = s_red[k][slot];
+                    for (int r = 1; r < S; ++r) {
+                        const float2 v = s_red[k][slot + r * TT];
+                        acc.x += v.x;
+                        acc.y += v.y;
+                    }
+                    phi[i0 + it[k]] = acc;
+                }
         }
         __syncthreads();
     }
@@ -1507,7 +1544,7 @@ static void near_stage(hfmm_plan* P, int parts, cudaStream_t st) {
                              st>>>((int)P->nleaf, P->leaf_start.p, P->leaf_ijk.p, P->nbr_ptr.p, P->nbr.p, P->pts.p,
                                    P->sig.p, P->p2p_shift, cap_pairs, P->phi.p);
             } else if (P->poly_p2p && P->p2p_variant == 1) {
-                k_p2p_packed<<<(unsigned)P->nleaf, kPkThreads, pk_smem, st>>>(
+                k_p2p_packed<kPkTargets><<<(unsigned)P->nleaf, kPkThreads, pk_smem, st>>>(
                     P->leaf_start.p, P->leaf_ijk.p, P->nbr_ptr.p, P->nbr.p, P->pts.p, P->sig.p, P->p2p_shift,
                     cap_pairs, P->phi.p);
             } else if (P->poly_p2p)
@@ -1659,7 +1696,7 @@ void matvec_kernels_init() {
     };
     allow((const void*)k_p2p_staged<true>);
     allow((const void*)k_p2p_staged<false>);
-    allow((const void*)k_p2p_packed);
+    allow((const void*)k_p2p_packed<kPkTargets>);
     allow((const void*)k_p2p_pipe);
     allow((const void*)k_p2m);
     if (dev >= 0 && dev < 64) done[dev] = true;
