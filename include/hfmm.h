@@ -89,7 +89,7 @@ typedef struct {
                            leaf size, Sec. 3.2 / 6.2); hfmm_plan_tuning reports the result.
                            0: use the defaults (0) */
     int p2p_kernel;     /* near-field kernel: 0 staged (four lanes per target), 1 packed FP32x2
-                           (one lane per target, two sources per instruction), 2 the packed
+                           (two targets per lane, two sources per instruction), 2 the packed
                            arithmetic in persistent blocks that load the next leaf's sources
                            (cp.async) while evaluating the current one; -1 default/tuned (-1) */
     int m2l_kernel;     /* tensor-core M2L: 0 source-stationary work items (one offset's operator
