@@ -931,8 +931,9 @@ static void build_plan(hfmm_plan* P, const double* V, int64_t nv, const int32_t*
                     pairs += pb.size(g);
                 }
                 const int64_t mean = busy ? pairs / busy : 0;
-                // 16 columns measured faster than 8 at a mean of 11 (fewer operator re-reads)
-                width = mean <= 6 ? 8 : mean <= 28 ? 16 : HFMM_TRANS_NB;
+                // measured on the 1.97 M-point workload: 16 columns beat 8 at a mean of 11
+                // (order-16 level) and beat 64 at a mean of 39 (order-10 level)
+                width = mean <= 6 ? 8 : mean <= 48 ? 16 : HFMM_TRANS_NB;
             }
             lev_width[l] = width;
             if (ts_bxofs[l] >= 0)
